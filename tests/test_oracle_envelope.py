@@ -1,0 +1,96 @@
+"""Pins of the envelope oracle (Sec. 4.1-4.2) against closed forms and a library expm (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.special
+
+from oracle import envelope as ev
+from oracle import stencils as st
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_radial_laplacian_on_bessel(order):
+    # L_rho J0(k rho) = -k^2 J0(k rho) (m = 0, symmetric axis mirror), converging at order 2N
+    k = 2.0
+    errs = []
+    for Nr in (24, 48):
+        dr = 6.0 / Nr
+        L = ev.radial_laplacian(Nr, order, dr)
+        rho = (np.arange(Nr) + 0.5) * dr
+        f = scipy.special.j0(k * rho)
+        r = L @ f + k * k * f
+        win = rho < 3.5
+        errs.append(np.abs(r[win]).max())
+    assert math.log2(errs[0] / errs[1]) > order - 1.5, errs
+
+
+def test_radial_laplacian_m2_on_bessel():
+    k, order = 2.0, 8
+    errs = []
+    for Nr in (24, 48):
+        dr = 6.0 / Nr
+        L = ev.radial_laplacian(Nr, order, dr, m=2)
+        rho = (np.arange(Nr) + 0.5) * dr
+        f = scipy.special.jv(2, k * rho)
+        errs.append(np.abs((L @ f + k * k * f)[rho < 3.5]).max())
+    assert math.log2(errs[0] / errs[1]) > order - 2.5, errs
+
+
+def test_taylor_converges_to_expm():
+    rng = np.random.default_rng(5)
+    Nz, Nr, order, dz, dr = 8, 6, 4, 0.2, 0.25
+    a = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    at = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    chi = 0.5 + rng.random((Nz, Nr))
+    t = 0.05
+    ra, rt = ev.envelope_expm(a, at, chi, order, dz, dr, t)
+    sa, stt = ev.envelope_step(a, at, chi, order, 40, dz, dr, t / 8, nsteps=8)
+    s = max(np.abs(ra).max(), np.abs(rt).max())
+    assert np.abs(sa - ra).max() < 1e-12 * s and np.abs(stt - rt).max() < 1e-12 * s
+
+
+@pytest.mark.parametrize("NT", [1, 2, 4])
+def test_taylor_NT_is_the_truncated_series(NT):
+    # On tiny grids the oracle's N_T-term step equals sum_{n<=N_T} (dt A)^n/n! with A the
+    # assembled matrix (independent check of the term recursion and the dt/n scaling).
+    rng = np.random.default_rng(9)
+    Nz, Nr, order, dz, dr, dt = 6, 5, 4, 0.2, 0.25, 0.01
+    a = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    at = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    chi = rng.random((Nz, Nr))
+    A = ev.envelope_matrix(Nz, Nr, chi, order, dz, dr)
+    P = sum(np.linalg.matrix_power(dt * A, n) / math.factorial(n) for n in range(NT + 1))
+    x = P @ np.concatenate([a.ravel(), at.ravel()])
+    sa, stt = ev.envelope_step(a, at, chi, order, NT, dz, dr, dt)
+    n = Nz * Nr
+    np.testing.assert_allclose(sa.ravel(), x[:n], atol=1e-12)
+    np.testing.assert_allclose(stt.ravel(), x[n:], atol=1e-12)
+
+
+@pytest.mark.parametrize("q", [1, 3, 7])
+def test_separable_mode_closed_form(q):
+    # a = alpha v(rho) e^{i theta i}, a~ = beta v(rho) e^{i theta i} with L_rho v = -nu v and uniform chi:
+    # H_a reduces to [[0, 1], [-nu - K2 - chi0 - 2 k0 K1, 2 i k0]], K2, K1 the z-stencil symbols,
+    # so N_T Taylor terms act as the 2x2 polynomial (complex form of Eq. spatialAM_envelope_H).
+    Nz, Nr, order, dz, dr, dt, NT = 16, 10, 8, 0.2, 0.25, 0.05, 4
+    chi0, k0 = 0.7, 2 * np.pi
+    L = ev.radial_laplacian(Nr, order, dr)
+    w, V = np.linalg.eig(L)
+    j = int(np.argmax(w.real))
+    nu, v = -w[j].real, V[:, j].real
+    th = 2 * np.pi * q / Nz
+    e0, e = st.centred_d2_coeffs(order)
+    d = st.centred_d1_coeffs(order)
+    K2 = -(e0 + 2 * sum(e[n - 1] * np.cos(n * th) for n in range(1, len(e) + 1))) / dz ** 2
+    K1 = 2 * sum(d[n - 1] * np.sin(n * th) for n in range(1, len(d) + 1)) / dz
+    M = np.array([[0, 1], [-nu - K2 - chi0 - 2 * k0 * K1, 2j * k0]])
+    P = sum(np.linalg.matrix_power(dt * M, n) / math.factorial(n) for n in range(NT + 1))
+    alpha, beta = 0.3 - 0.2j, 1.1 + 0.4j
+    phase = np.exp(1j * th * np.arange(Nz))[:, None]
+    a, at = alpha * phase * v[None, :], beta * phase * v[None, :]
+    sa, stt = ev.envelope_step(a, at, np.full((Nz, Nr), chi0), order, NT, dz, dr, dt)
+    na, nb = P @ np.array([alpha, beta])
+    np.testing.assert_allclose(sa, na * phase * v[None, :], atol=1e-12)
+    np.testing.assert_allclose(stt, nb * phase * v[None, :], atol=1e-12)

@@ -1,0 +1,286 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: printed values,
+closed forms, library special functions, exact discrete identities, or a second
+independent evaluator.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle import diagnostics as dg
+from oracle import maxwell as mx
+from oracle import stencils as st
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dfact(k):
+    return math.prod(range(k, 0, -2)) if k > 0 else 1
+
+
+# ---------------------------------------------------------------- stencils
+
+def test_axis_coeffs_match_printed_order10():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "axis_coeffs_order10.txt")) if l.strip() and l[0] != "#"]
+    printed = [Fraction(int(a), int(b)) for a, b in rows]
+    assert st.axis_coeffs_exact(5) == printed
+
+
+def test_staggered_textbook_values():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "staggered_textbook.txt")) if l.strip() and l[0] != "#"]
+    for order, n, a, b in rows:
+        assert st.staggered_coeffs_exact(int(order))[int(n) - 1] == Fraction(int(a), int(b))
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 16, 24, 32])
+def test_staggered_closed_form(order):
+    # c_n = (-1)^(n+1) ((2N-1)!!)^2 / ((2n-1)^2 (N-n)! (N+n-1)! 2^(2N-2))
+    N = order // 2
+    c = st.staggered_coeffs_exact(order)
+    for n in range(1, N + 1):
+        ref = Fraction((-1) ** (n + 1) * _dfact(2 * N - 1) ** 2,
+                       (2 * n - 1) ** 2 * math.factorial(N - n) * math.factorial(N + n - 1) * 2 ** (2 * N - 2))
+        assert c[n - 1] == ref
+
+
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_centred_coeffs_exact_on_polynomials(order):
+    # centred D^(C) and D^2 of order 2N differentiate polynomials of degree <= 2N exactly
+    N = order // 2
+    d = st.centred_d1_coeffs_exact(order)
+    e0, e = st.centred_d2_coeffs_exact(order)
+    for deg in range(0, 2 * N + 1):
+        f = lambda x: Fraction(x) ** deg
+        d1 = sum(d[n - 1] * (f(3 + n) - f(3 - n)) for n in range(1, N + 1))
+        d2 = e0 * f(3) + sum(e[n - 1] * (f(3 + n) + f(3 - n)) for n in range(1, N + 1))
+        assert d1 == (deg * Fraction(3) ** (deg - 1) if deg >= 1 else 0)
+        assert d2 == (deg * (deg - 1) * Fraction(3) ** (deg - 2) if deg >= 2 else 0)
+
+
+def test_axis_coeffs_reproduce_even_polynomials():
+    # Lagrange in rho^2: exact for 1, rho^2, ..., rho^(2N-2)
+    for N in (2, 3, 5, 8):
+        c = st.axis_coeffs_exact(N)
+        for p in range(N):
+            val = sum(c[k - 1] * Fraction(k) ** (2 * p) for k in range(1, N + 1))
+            assert val == (1 if p == 0 else 0)
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_z_symbol_is_kappa(order):
+    # s+ s- = -kappa^2 with kappa = (2/dz) sum c_n sin((2n-1) k dz / 2), and kappa -> k at O((k dz)^order)
+    Nz, dz = 64, 0.1
+    sp, sm = mx.z_symbols(Nz, order, dz)
+    c = st.staggered_coeffs(order)
+    k = 2 * np.pi * np.fft.fftfreq(Nz, d=dz)
+    kappa = (2 / dz) * sum(c[n - 1] * np.sin((2 * n - 1) * k * dz / 2) for n in range(1, len(c) + 1))
+    np.testing.assert_allclose(sp * sm, -kappa ** 2, atol=1e-10)
+    np.testing.assert_allclose(sp, 1j * kappa * np.exp(1j * k * dz / 2), atol=1e-10)
+    errs = []
+    for q in (1, 2):
+        errs.append(abs(kappa[q] - k[q]))
+    # error ratio of doubling k is 2^(order+1)
+    assert abs(math.log2(errs[1] / errs[0]) - (order + 1)) < 0.2
+
+
+# ---------------------------------------------------------------- radial operators
+
+def _rows_clear(Nr, order, margin=2):
+    return slice(0, Nr - order // 2 - margin)
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+@pytest.mark.parametrize("order", [4, 8])
+def test_radial_derivative_convergence_near_axis(m, order):
+    # D^- on the parity-m function rho^m cos(rho) (extended by parity) converges at the stated order,
+    # including the rows that reach through the axis.
+    errs = []
+    kk = 3.0
+    for Nr in (20, 40):
+        dr = 4.0 / Nr
+        rad = mx.Radial(Nr, order, dr, m)
+        f = lambda r: r ** m * np.cos(kk * r) if m else np.cos(kk * r)
+        df = lambda r: (m * r ** (m - 1) * np.cos(kk * r) - kk * r ** m * np.sin(kk * r)) if m else -kk * np.sin(kk * r)
+        got = rad.Dm @ f(rad.rho)
+        rows = slice(1, Nr // 2)
+        errs.append(np.abs(got[rows] - df(rad.rhom[rows])).max())
+        g = f(rad.rhom)
+        got2 = rad.Dp @ g
+        errs_p = np.abs(got2[: Nr // 2] - df(rad.rho[: Nr // 2])).max()
+        errs[-1] = max(errs[-1], errs_p)
+    slope = math.log2(errs[0] / errs[1])
+    assert slope > order - 0.6, (errs, slope)
+
+
+def _check_orders(errs, order):
+    # interior rows (a fixed physical window) converge at the stated order 2N_D; the rows
+    # whose stencil reaches through the axis are multiplied by rho^-1 ~ 1/dr and, for the
+    # m = 0 B_z-type operator, use the O(dr^2N_D) axis extrapolation, so they may lose up
+    # to two orders - but they must still converge at high order.
+    (a0, b0), (a1, b1) = errs
+    assert math.log2(b0 / b1) > order - 0.5, errs
+    assert math.log2(a0 / a1) > order - 2.5, errs
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_L0_on_bessel(m):
+    # L0 = D_div^(+) D^(-) - m^2/rho^2 (primary grid) applied to J_m(k rho) -> -k^2 J_m(k rho)
+    order, k = 8, 2.0
+    errs = []
+    for Nr in (24, 48):
+        dr = 6.0 / Nr
+        rad = mx.Radial(Nr, order, dr, m)
+        L0 = rad.div_plus() @ rad.grad_r() - np.diag(m * m / rad.rho ** 2)
+        f = scipy.special.jv(m, k * rad.rho)
+        r = L0 @ f + k * k * f
+        win = (rad.rho > 2.0) & (rad.rho < 3.5)
+        errs.append((np.abs(r[:order]).max(), np.abs(r[win]).max()))
+    _check_orders(errs, order)
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_L2_on_bessel(m):
+    # L2 = D_div^(-) D^(+) - m^2/rho_-^2 on the staggered grid, B_z axis value from Sec. 2.4
+    order, k = 8, 2.0
+    errs = []
+    for Nr in (24, 48):
+        dr = 6.0 / Nr
+        rad = mx.Radial(Nr, order, dr, m)
+        L2 = rad.div_minus() @ rad.dplus_bz() - np.diag(m * m / rad.rhom[1:] ** 2)
+        f = scipy.special.jv(m, k * rad.rhom[1:])
+        r = L2 @ f + k * k * f
+        win = (rad.rhom[1:] > 2.0) & (rad.rhom[1:] < 3.5)
+        errs.append((np.abs(r[:order]).max(), np.abs(r[win]).max()))
+    _check_orders(errs, order)
+
+
+# ---------------------------------------------------------------- the operator and its exponential
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_spectrum_purely_imaginary(m):
+    Nz, Nr, order, dz, dr = 16, 24, 8, 1 / 16, 1 / 4
+    for q in (0, 1, 5, 8):
+        ev = mx.kz_spectrum(Nz, Nr, m, order, dz, dr, q)
+        assert np.abs(ev.real).max() < 1e-9 * np.abs(ev).max()
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_spectrum_factorises(m):
+    # The kz-block spectrum is {0} U {+-i sqrt(kappa^2 + lambda_j)} U {+-i sqrt(kappa^2 + mu_j)}
+    # with -lambda_j the eigenvalues of L0 and -mu_j those of L2 (plus, for m = 0, the
+    # radially uniform TE pair +-i kappa): the separable structure the GPU path relies on.
+    Nz, Nr, order, dz, dr = 16, 20, 8, 1 / 16, 1 / 4
+    rad = mx.Radial(Nr, order, dr, m)
+    L0 = rad.div_plus() @ rad.grad_r() - np.diag(m * m / rad.rho ** 2)
+    L2 = rad.div_minus() @ rad.dplus_bz() - np.diag(m * m / rad.rhom[1:] ** 2)
+    lam = -np.linalg.eigvals(L0).real
+    mu = -np.linalg.eigvals(L2).real
+    sp, sm = mx.z_symbols(Nz, order, dz)
+    for q in (1, 3, 8):
+        k2 = (-sp[q] * sm[q]).real
+        w = list(np.sqrt(k2 + lam[lam > 1e-9])) + list(np.sqrt(k2 + mu))
+        if m == 0:
+            w.append(np.sqrt(k2))          # radially uniform TE pair
+        expect = np.sort(np.concatenate([w, w]))
+        ev = mx.kz_spectrum(Nz, Nr, m, order, dz, dr, q)
+        got = np.sort(np.abs(ev.imag))
+        nz = got[got > 1e-8]
+        np.testing.assert_allclose(nz, expect, rtol=1e-9)
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_three_evaluators_agree(m):
+    rng = np.random.default_rng(7 + m)
+    Nz, Nr, order, dz, dr, dt = 8, 7, 4, 0.25, 0.3, 0.2
+    F = rng.standard_normal((6, Nz, Nr)) + 1j * rng.standard_normal((6, Nz, Nr))
+    J = rng.standard_normal((3, Nz, Nr)) + 1j * rng.standard_normal((3, Nz, Nr))
+    a = mx.step_spectral(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=3)
+    b = mx.step_expm_realspace(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=3)
+    c = mx.step_taylor(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=3)
+    s = np.abs(b).max()
+    assert np.abs(a - b).max() < 1e-12 * s
+    assert np.abs(c - b).max() < 1e-12 * s
+
+
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_eigenvector_advances_by_its_phase(m):
+    Nz, Nr, order, dz, dr, dt = 8, 9, 6, 0.25, 0.3, 0.17
+    q = 3
+    rad = mx.Radial(Nr, order, dr, m)
+    sp, sm = mx.z_symbols(Nz, order, dz)
+    w, V = np.linalg.eig(mx.kz_operator(rad, sp[q], sm[q]))
+    j = int(np.argmax(np.abs(w.imag)))
+    col = mx.scatter(V[:, j], Nr)
+    F = col[:, None, :] * np.exp(2j * np.pi * q * np.arange(Nz) / Nz)[None, :, None]
+    for step in (mx.step_expm_realspace, mx.step_taylor):
+        G = step(F, None, Nz, Nr, m, order, dz, dr, dt, nsteps=2)
+        G = mx._zero_axis_slots(G)
+        np.testing.assert_allclose(G, F * np.exp(2 * w[j] * dt), atol=1e-12 * np.abs(F).max())
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_divergence_invariants(m):
+    rng = np.random.default_rng(11 + m)
+    Nz, Nr, order, dz, dr, dt = 16, 12, 8, 1 / 16, 1 / 4, 1 / 16
+    rad = mx.Radial(Nr, order, dr, m)
+    F = mx.fill_axis(rng.standard_normal((6, Nz, Nr)) + 1j * rng.standard_normal((6, Nz, Nr)), rad)
+    J = rng.standard_normal((3, Nz, Nr)) + 1j * rng.standard_normal((3, Nz, Nr))
+    J[0, :, 0] = 0
+    n = 4
+    G0 = mx.step_spectral(F, None, Nz, Nr, m, order, dz, dr, dt, nsteps=n)
+    GJ = mx.step_spectral(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=n)
+    dE0, dB0 = dg.div_E(F, rad, order, dz), dg.div_B(F, rad, order, dz)
+    scale = np.abs(dE0).max()
+    assert np.abs(dg.div_E(G0, rad, order, dz) - dE0).max() < 1e-12 * scale
+    assert np.abs(dg.div_B(G0, rad, order, dz) - dB0).max() < 1e-12 * np.abs(dB0).max()
+    # Ampere with current: div E decreases by n dt div J exactly (div B unaffected)
+    dJ = dg.div_J(J, rad, order, dz)
+    assert np.abs(dg.div_E(GJ, rad, order, dz) - (dE0 - n * dt * dJ)).max() < 1e-12 * scale
+    assert np.abs(dg.div_B(GJ, rad, order, dz) - dB0).max() < 1e-12 * np.abs(dB0).max()
+
+
+def test_axis_output_values():
+    # Output slot 0: Bz extrapolated for m = 0; Er, Btheta extrapolated for m = 1; zero otherwise.
+    rng = np.random.default_rng(3)
+    Nz, Nr, order, dz, dr, dt = 8, 10, 8, 0.25, 0.3, 0.1
+    c = st.axis_coeffs(4)
+    for m in (0, 1, 2):
+        F = rng.standard_normal((6, Nz, Nr)) + 0j
+        G = mx.step_spectral(F, None, Nz, Nr, m, order, dz, dr, dt)
+        for f, const in ((0, m == 1), (4, m == 1), (5, m == 0)):
+            expect = G[f, :, 1:5] @ c if const else 0 * G[f, :, 0]
+            np.testing.assert_allclose(G[f, :, 0], expect, atol=1e-12)
+
+
+def test_vacuum_pulse_group_velocity():
+    # A Gaussian pulse in vacuum (m = 1, x-polarised, w0 = 3, tau = 2 wavelengths) moves at
+    # 1 - v_g = (lambda / (2 pi w0))^2 (Eq. test_am_vacuum_vg) within 5 %.  The initial fields
+    # are not divergence-free (no Poisson initialisation), so a small static remnant stays at
+    # the start; the centroid is measured beyond it, at two later times.
+    from paper_2605_12132_gb300.inputs import pulse_fields
+    Nz, Nr, order, dz, dr, dt = 384, 32, 16, 1 / 8, 1 / 4, 1 / 8
+    w0, tau, m, zc = 3.0, 2.0, 1, 8.0
+    rad = mx.Radial(Nr, order, dr, m)
+    F = mx.fill_axis(pulse_fields(Nz, Nr, dz, dr, w0, tau, zc=zc), rad)
+    z = np.arange(Nz) * dz
+    win = z > zc + 4 * tau
+
+    def dens(G):
+        return sum((np.abs(G[f]) ** 2 * (rad.rhom if f in (0, 4, 5) else rad.rho)).sum(axis=1) for f in range(6))
+
+    n1 = 120
+    G1, G2 = mx.step_spectral(F, None, Nz, Nr, m, order, dz, dr, dt, nsteps=[n1, 2 * n1])
+    d0, d1, d2 = dens(F), dens(G1), dens(G2)
+    c1 = (d1 * z)[win].sum() / d1[win].sum()
+    c2 = (d2 * z)[win].sum() / d2[win].sum()
+    delay = 1 - (c2 - c1) / (n1 * dt)
+    analytic = (1 / (2 * np.pi * w0)) ** 2
+    assert abs(delay - analytic) < 0.05 * analytic, (delay, analytic)
+    # the moving part carries all but a (lambda / w0)^2-small static fraction of the energy, and keeps it
+    assert 0.99 < d1[win].sum() / d0.sum() < 1.0
+    assert abs(d2[win].sum() / d1[win].sum() - 1) < 1e-3
