@@ -1,0 +1,312 @@
+"""Throughput benchmark of the exact exponential field step (cell*mode*steps/s).
+
+Default workload: the current-driven 2048 x 256 case (modes 0 and 1, order 16,
+seeded Gaussian pulse on m = 1 plus a seeded smooth random current on both
+modes), one real-space round trip per step (projection, z transform + exact
+rotation with the current, inverse transform, back-projection), inputs resident
+in HBM, L2 flushed (a 256 MiB write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16x6|fp32|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+N > 1 (torchrun, one process per GPU) runs independent replicas: the step has no
+data-path exchange, so each rank advances its own copy and `value` sums them.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell*mode*steps/s (exact exponential field step, one real-space round trip per step)"
+UNIT = "cell*mode*steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), float(p[4]), p[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        loaded = [r for r in rows if r[2] >= 30] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+def gemm_flops(w, hasJ):
+    """Algorithmic FLOPs of one step's radial transforms: each nonzero n x n block of the
+    (3n)^2 projection / back-projection matrices times a complex column, per z row and mode."""
+    n = w.Nr
+    fwd = (15 if hasJ else 10)
+    bwd = 10
+    per_block = 4.0 * n * n * w.Nz   # real matrix x complex vector = 2 real MACs per entry
+    return fwd * per_block * len(w.modes), bwd * per_block * len(w.modes)
+
+
+def spectral_bytes(w, hasJ, elt):
+    """Algorithmic bytes of the spectral stage: the coefficient arrays read once, written once."""
+    return ((9 if hasJ else 6) + 6) * w.Nz * w.Nr * len(w.modes) * elt
+
+
+def cpu_oracle_rate(w, F, J, kz_count):
+    """The FP64 oracle (per-kz dense eigendecomposition evaluator) on a bounded sample of kz columns."""
+    from oracle import maxwell as mx
+    rng = np.random.default_rng(123)
+    qs = list(rng.choice(w.Nz, size=kz_count, replace=False))
+    m_i = len(w.modes) - 1
+    t0 = time.perf_counter()
+    mx.step_spectral(F[m_i], None if J is None else J[m_i], w.Nz, w.Nr, w.modes[m_i], w.order, w.dz, w.dr, w.dt,
+                     nsteps=1, kz_subset=qs, method="eig")
+    dt = time.perf_counter() - t0
+    return kz_count * w.Nr / dt, dt
+
+
+def run_reference(args, w, rank, world):
+    """--impl reference: the oracle as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2605_12132_gb300 import inputs
+    F, J = inputs.workload_inputs(w)
+    kz_per_step = 1
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, F, J, kz_per_step)
+    tot, cells = 0.0, 0
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(w, F, J, kz_per_step)
+        tot += dt
+        cells += kz_per_step * w.Nr
+    value = cells / tot
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded pulse + smooth random current)",
+            "config": {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order,
+                       "precision": "fp64-oracle", "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one kz column ({w.Nr} cells) of mode {w.modes[-1]} per step, "
+                                       "per-kz dense eigendecomposition evaluator, FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--workload", default="lwfa_m01_2048x256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2605_12132_gb300 import inputs
+    w = inputs.workload(args.workload)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+
+    import torch
+    import paper_2605_12132_gb300 as fd
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prec = args.precision
+    if prec is None:
+        prec = "bf16x3"
+        try:
+            fd.fdetd_plan_modes(64, 16, [0], 4, 0.1, 0.1, 0.1, precision="bf16x3").close()
+        except fd.FdetdError:
+            prec = "fp32"
+
+    F, J = inputs.workload_inputs(w)
+    plan = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision=prec)
+    cdt = plan.complex_dtype
+    fields = torch.from_numpy(F).to(cdt).cuda()
+    Jd = torch.from_numpy(J).to(cdt).cuda() if J is not None else None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        fd.fdetd_step(plan, fields, Jd, 1)
+    barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    plan.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        fd.fdetd_step(plan, fields, Jd, 1)
+        evs[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ktimes = plan.kernel_times()
+    plan.set_profiling(False)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = w.Nz * w.Nr * len(w.modes)
+    value = cells * args.steps * world / (ms / 1e3)
+
+    # end-to-end through the host entry point: h2d of fields + J, the step, d2h of the fields
+    hf = torch.from_numpy(F).to(cdt).pin_memory()
+    hJ = torch.from_numpy(J).to(cdt).pin_memory() if J is not None else None
+    fd.fdetd_step_host(plan, hf, hJ, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        fd.fdetd_step_host(plan, hf, hJ, 1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    elt = hf.element_size()
+    h2d = hf.numel() * elt + (hJ.numel() * elt if hJ is not None else 0)
+    d2h = hf.numel() * elt
+    e2e_val = cells * args.e2e_steps * world / e2e_s
+
+    # FP64 single-instance path on the same workload (the plain baseline the split path must beat)
+    fp64_value = None
+    if not args.no_fp64 and prec != "fp64":
+        p64 = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision="fp64")
+        f64 = torch.from_numpy(F).cuda()
+        J64 = torch.from_numpy(J).cuda() if J is not None else None
+        fd.fdetd_step(p64, f64, J64, 1)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = 2
+        a.record(stream)
+        fd.fdetd_step(p64, f64, J64, n64)
+        b.record(stream)
+        barrier()
+        fp64_value = cells * n64 / (a.elapsed_time(b) / 1e3)
+        p64.close()
+        del f64, J64
+
+    # roofline of the dominant stage
+    peaks, src = _peaks()
+    hasJ = J is not None
+    fwd_flops, bwd_flops = gemm_flops(w, hasJ)
+    elt_c = 16 if prec == "fp64" else 8
+    stage = max(ktimes, key=lambda k: ktimes[k][0])
+    tms, calls = ktimes[stage]
+    per_launch_s = tms / 1e3 / max(calls, 1)
+    products = {"bf16x3": 3, "bf16x6": 6}.get(prec, 1)
+    if stage == "spectral":
+        algo = spectral_bytes(w, hasJ, elt_c)
+        roof = {"bound": "hbm", "achieved": algo / per_launch_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        algo = fwd_flops if stage == "projection" else bwd_flops
+        if prec in ("bf16x3", "bf16x6"):
+            roof = {"bound": "tensor", "achieved": algo * products / per_launch_s / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        else:
+            # CUDA-core FMA peak: 152 SMs x 128 FP32 lanes (FP64: nominal 1.25 TFLOP/s) x 2 flops x max clock
+            pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if prec == "fp32" else 1.25
+            roof = {"bound": "alu", "achieved": algo / per_launch_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = stage
+    roof["peak_source"] = src
+    roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in ktimes.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        kz = 4
+        rate, secs = cpu_oracle_rate(w, F, J, kz)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{kz} kz columns ({kz * w.Nr} cells) of mode {w.modes[-1]}, one step, per-kz dense "
+                         f"eigendecomposition evaluator, FP64 ({secs:.1f} s)"}
+
+    if rank == 0:
+        launches = plan.launches_per_step * args.steps
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec + "-split/f32-accumulate"),
+                "data": "synthetic (seeded Gaussian pulse + seeded smooth random current)",
+                "config": {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order,
+                           "precision": prec, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed between timed steps (256 MiB write)", "fp64_value": fp64_value,
+                           "wall_s": t_wall},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * fdetd.h - C ABI of the GB300-native exact exponential field solver for
+ * cylindrical (azimuthal-mode) particle-in-cell simulations, and of the
+ * exponential laser-envelope propagator.
+ *
+ * Method: "High-order exponential solver method for particle-in-cell simulations
+ * in cylindrical geometry" (Majorosi, Hafz, Lecz).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Units c = 1, lengths in laser wavelengths (Sec. 1, normalised units).
+ * - Complex azimuthal modes: F(rho, theta, z) = Re sum_m F_m(rho, z) exp(-i m theta),
+ *   the complex form of the real (2m, 2m+1) pairs of Sec. 2.1 (Eq. maxwellAM_dtheta).
+ * - Radial grids (Eqs. spatialAM_grid, spatialAM_gridR), k = 0..Nr-1:
+ *   primary rho_k = (k + 1/2) dr, staggered rho_(-),k = k dr (k = 0 is the axis).
+ * - Yee placement (Table tab:spatialAM_boundary): Er, Btheta, Bz on the staggered
+ *   radial grid; Etheta, Ez, Br on the primary grid; Ez, Br, Btheta sit at
+ *   z = (i - 1/2) dz, the others at z = i dz.  z is periodic with period Nz dz.
+ * - Field array of one call: [nmodes][6][Nz][Nr] interleaved complex, components
+ *   in the order (Er, Etheta, Ez, Br, Btheta, Bz), r fastest.  complex128 for
+ *   FDETD_PREC_FP64, complex64 for every other precision.  Slot k = 0 of Er,
+ *   Btheta, Bz is the axis: it is ignored on input and holds the axis value on
+ *   output (Sec. 2.4: extrapolated with the order-2N_D coefficients where the
+ *   field is constant on the axis - Bz for m = 0, Er and Btheta for m = 1 - and 0
+ *   elsewhere).
+ * - Current array: [nmodes][3][Nz][Nr] (Jr, Jtheta, Jz) on the Yee locations of
+ *   (Er, Etheta, Ez), same complex type as the fields; Jr slot 0 is ignored.
+ * - All device pointers must be 16-byte aligned.  A call never frees or keeps a
+ *   caller pointer.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *
+ * Error handling: every call returns FDETD_OK (0) or one of the FDETD_ERR_*
+ * codes; fdetd_last_error() copies a one-line message of the calling thread's
+ * last failure.  Argument errors are detected before any work is enqueued.
+ * Kernel launches are asynchronous; device-side failures surface at the next
+ * synchronising call as FDETD_ERR_CUDA.
+ */
+#ifndef FDETD_H_
+#define FDETD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FDETD_OK = 0,
+  FDETD_ERR_ARG = 1,         /* invalid argument (sizes, order, null pointer, misalignment) */
+  FDETD_ERR_OOM = 2,         /* device or host allocation failed */
+  FDETD_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  FDETD_ERR_EIG = 4,         /* radial eigen-decomposition failed (complex or singular spectrum) */
+  FDETD_ERR_UNSUPPORTED = 5, /* valid request this build does not implement (e.g. Nz not a power of 2) */
+  FDETD_ERR_TIMEOUT = 6      /* a kernel's bounded pipeline wait expired; it stopped early and freed its resources */
+};
+
+/* Arithmetic of the radial transforms (and storage type of the fields). */
+enum {
+  FDETD_PREC_FP64 = 0,   /* complex128 fields; FP64 everywhere */
+  FDETD_PREC_FP32 = 1,   /* complex64 fields; FP32 CUDA-core radial transforms */
+  FDETD_PREC_BF16X3 = 2, /* complex64 fields; tcgen05 BF16 2-piece split, 3 products, FP32 accumulate */
+  FDETD_PREC_BF16X6 = 3  /* complex64 fields; tcgen05 BF16 3-piece split, 6 products, FP32 accumulate */
+};
+
+typedef struct fdetd_plan_s* fdetd_plan_t;
+typedef struct envelope_plan_s* envelope_plan_t;
+
+/*
+ * fdetd_plan - build the exact exponential step of modes m = 0..M.
+ *
+ * Defines exp(dt H_m) of the discrete operator of Sec. 2.5 (Eqs.
+ * spatialAM_maxwell_Er ... _Bz): staggered finite differences of order `order`
+ * (even, 2..32) in z and rho (Eq. spatial_derivativeSt), the parity-dependent
+ * axis extensions of Eqs. spatialAM_derivativeS/A, the B_z axis value of
+ * Sec. 2.4, taps beyond the outer radius dropped (Sec. 2.2), periodic z.
+ * Nz >= 2 (this build: a power of two, 64..8192), Nr >= order/2 + 2, M >= 0.
+ * The radial eigen-decompositions, the omega table and the phase factors are
+ * computed in FP64 on the host; device tables are allocated here and owned by
+ * the plan.  Blocking; not stream-ordered.
+ */
+int fdetd_plan(fdetd_plan_t* out, int Nz, int Nr, int M, int order, double dz, double dr, double dt,
+               int precision, uint64_t flags);
+
+/* As fdetd_plan for an explicit list of mode numbers (each 0..64), e.g. {1}. */
+int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* modes, int nmodes, int order,
+                     double dz, double dr, double dt, int precision, uint64_t flags);
+
+/*
+ * fdetd_step - advance the fields in place by `nsteps` midpoint exponential steps
+ * (Eq. maxwellAM_solution2, with the dt factor of the current integral of
+ * Eq. maxwellAM_solution):
+ *     Psi <- exp(dt H) Psi - dt exp(dt H / 2) J.
+ * fields: device, in/out, layout above.  J: device or NULL (J = 0), constant over
+ * the nsteps steps and re-consumed in real space every step.  nsteps >= 0.
+ * Every step is one real-space round trip: radial projection, z-transform, exact
+ * per-(kz, j) rotation with the current term, inverse z-transform, radial
+ * back-projection.  Asynchronous on `stream`; uses the plan's scratch buffers,
+ * so calls on one plan must not overlap.
+ */
+int fdetd_step(fdetd_plan_t plan, void* fields, const void* J, int nsteps, void* stream);
+
+/* End-to-end variant with HOST arrays (same layouts): copies fields (and J) to the
+ * device, runs fdetd_step, copies the fields back; synchronises `stream`. */
+int fdetd_step_host(fdetd_plan_t plan, void* host_fields, const void* host_J, int nsteps, void* stream);
+
+/*
+ * fdetd_plan_status - synchronise `stream` and report device-side failures of earlier
+ * steps on this plan: FDETD_ERR_CUDA for a CUDA error, FDETD_ERR_TIMEOUT if a
+ * tensor-core kernel's bounded mbarrier wait expired (the kernel then skipped its
+ * remaining work, drained its own MMAs and released its tensor memory; the output
+ * of that step is undefined).  Clears the recorded timeout.
+ */
+int fdetd_plan_status(fdetd_plan_t plan, void* stream);
+
+/* Bytes of device memory the plan holds (tables + scratch). */
+size_t fdetd_plan_device_bytes(fdetd_plan_t plan);
+
+/* Number of kernels one fdetd_step step launches. */
+int fdetd_plan_launches_per_step(fdetd_plan_t plan);
+
+/*
+ * Per-kernel timing (instrumentation).  While profiling is on, fdetd_step records a
+ * CUDA event pair around each of its three kernel stages on the launch stream:
+ * 0 = radial projection, 1 = spectral (z transforms + rotation), 2 = radial
+ * back-projection.  fdetd_plan_kernel_times synchronises on the recorded events and
+ * returns the accumulated milliseconds and launch counts per stage (arrays of 3).
+ * Turning profiling on or off resets the accumulators.
+ */
+int fdetd_plan_set_profiling(fdetd_plan_t plan, int on);
+int fdetd_plan_kernel_times(fdetd_plan_t plan, double* ms, long* calls);
+
+int fdetd_plan_destroy(fdetd_plan_t plan);
+
+/*
+ * fdetd_host_tables - host-only (no GPU needed) export of the FP64 plan tables of
+ * one mode, for inspection and CPU tests.  Any output pointer may be NULL.
+ * PE, PB, QE, QB: (3 Nr)^2 row-major each.  Rows/cols of PE (cols) and QE (rows)
+ * are the field blocks (Er, tau Etheta, Ez), of PB (cols) and QB (rows) the blocks
+ * (Btheta, tau Br, tau Bz), tau = -i; the other index runs over the coefficient
+ * blocks (e, a, tau c) / (b, tau d, tau f).  lam, mu: Nr each; tm_live, te_live: Nr
+ * bytes; kappa2: Nz; sp, sm: 2 Nz (re, im) - the DFT symbols of D_z^(+), D_z^(-).
+ */
+int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, double dr, double dt, double* PE,
+                      double* PB, double* QE, double* QB, double* lam, double* mu, uint8_t* tm_live,
+                      uint8_t* te_live, double* kappa2, double* sp, double* sm);
+
+/* Host-only: staggered (kind 0), centred first (1), centred second (2, e0 first) derivative
+ * coefficients of `order`, or axis coefficients (3, N = order/2); returns the count written. */
+int fdetd_host_coeffs(int kind, int order, double* out);
+
+/*
+ * envelope_plan - exponential laser-envelope propagator of Sec. 4.2, mode m = 0:
+ *     da/dt = a~,  da~/dt = (L_rho + L_z - chi) a + 2 i k0 D_z^(C) a + 2 i k0 a~
+ * (complex form of Eq. spatialAM_envelope_H; L_rho = D^2_rho + rho^-1 D^(C)_rho with
+ * the symmetric axis mirror, Eq. spatialAM_laplaceR; centred differences of order
+ * `order` (even, 2..16); periodic z; primary radial grid).  One step applies the
+ * truncated Taylor series sum_{n <= taylor_order} (dt H_a)^n / n!
+ * (Eq. laserA_envelope_solution), taylor_order 1..16.  Nz >= 2*order, Nr >= order/2+1.
+ */
+int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, int taylor_order, double dz, double dr,
+                  double dt, double k0);
+
+/*
+ * envelope_step - advance psi_a = (a, a~) in place by nsteps Taylor steps.
+ * a: device [2][Nz][Nr] complex64 (a then a~).  chi: device [Nz][Nr] float32,
+ * frozen over the call (the mid-step value of Sec. 4.2).  Asynchronous on
+ * `stream`; uses the plan's scratch, so calls on one plan must not overlap.
+ */
+int envelope_step(envelope_plan_t plan, void* a, const float* chi, int nsteps, void* stream);
+
+/* Number of kernels one envelope step launches. */
+int envelope_plan_launches_per_step(envelope_plan_t plan);
+
+int envelope_plan_destroy(envelope_plan_t plan);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to len). */
+int fdetd_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDETD_H_ */

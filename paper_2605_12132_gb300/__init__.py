@@ -1,0 +1,28 @@
+"""GB300-native exact exponential field solver for cylindrical PIC (azimuthal modes).
+
+Thin Python binding over the C-ABI library ``lib/libfdetd.so`` (declared in
+``include/fdetd.h``): argument marshalling only; every step of the solver runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams.
+
+    from paper_2605_12132_gb300 import fdetd_plan, fdetd_step
+    plan = fdetd_plan(Nz, Nr, M, order, dz, dr, dt, precision="bf16x3")
+    fdetd_step(plan, fields, J, nsteps)      # fields: cuda complex64 [M+1][6][Nz][Nr]
+
+The library is loaded lazily on first use; importing this package does not need a GPU.
+"""
+from ._native import (  # noqa: F401
+    PRECISIONS,
+    EnvelopePlan,
+    FdetdError,
+    FdetdPlan,
+    envelope_plan,
+    envelope_step,
+    fdetd_host_coeffs,
+    fdetd_host_tables,
+    fdetd_plan,
+    fdetd_plan_modes,
+    fdetd_step,
+    fdetd_step_host,
+    lib,
+    lib_path,
+)

@@ -1,0 +1,231 @@
+"""ctypes binding of libfdetd.so (same names as the C-ABI; marshalling only)."""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
+
+
+class FdetdError(RuntimeError):
+    pass
+
+
+def lib_path():
+    return os.path.join(_HERE, "lib", "libfdetd.so")
+
+
+def lib():
+    """Load libfdetd.so (raises if it has not been built: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise FdetdError(f"{path} is missing; build it with `python {_HERE}/build.py` "
+                         "(or __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    c_int, c_dbl, c_vp, c_u64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    L.fdetd_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_int, c_u64]
+    L.fdetd_plan_modes.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, ctypes.POINTER(c_int), c_int, c_int,
+                                   c_dbl, c_dbl, c_dbl, c_int, c_u64]
+    L.fdetd_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.fdetd_step_host.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.fdetd_plan_device_bytes.argtypes = [c_vp]
+    L.fdetd_plan_device_bytes.restype = ctypes.c_size_t
+    L.fdetd_plan_launches_per_step.argtypes = [c_vp]
+    L.fdetd_plan_destroy.argtypes = [c_vp]
+    L.fdetd_plan_set_profiling.argtypes = [c_vp, c_int]
+    L.fdetd_plan_status.argtypes = [c_vp, c_vp]
+    L.fdetd_plan_kernel_times.argtypes = [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]
+    L.fdetd_host_tables.argtypes = [c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, dp, dp, dp, dp, dp, dp,
+                                    u8p, u8p, dp, dp, dp]
+    L.fdetd_host_coeffs.argtypes = [c_int, c_int, dp]
+    L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
+    L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.envelope_plan_launches_per_step.argtypes = [c_vp]
+    L.envelope_plan_destroy.argtypes = [c_vp]
+    L.fdetd_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    _LIB = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(512)
+        lib().fdetd_last_error(buf, 512)
+        raise FdetdError(f"fdetd error {rc}: {buf.value.decode(errors='replace')}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(arr):
+    return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if arr is not None else None
+
+
+class FdetdPlan:
+    def __init__(self, handle, Nz, Nr, modes, order, dz, dr, dt, precision):
+        self.handle = handle
+        self.Nz, self.Nr, self.modes, self.order = Nz, Nr, list(modes), order
+        self.dz, self.dr, self.dt, self.precision = dz, dr, dt, precision
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == "fp64" else torch.complex64
+
+    @property
+    def device_bytes(self):
+        return lib().fdetd_plan_device_bytes(self.handle)
+
+    @property
+    def launches_per_step(self):
+        return lib().fdetd_plan_launches_per_step(self.handle)
+
+    def status(self, stream=None):
+        """Synchronise and raise FdetdError if an earlier step failed on the device."""
+        _check(lib().fdetd_plan_status(self.handle, _stream_handle(stream)))
+
+    def set_profiling(self, on=True):
+        _check(lib().fdetd_plan_set_profiling(self.handle, int(on)))
+
+    def kernel_times(self):
+        """{stage: (total_ms, launches)} for stages projection / spectral / backprojection."""
+        ms = (ctypes.c_double * 3)()
+        calls = (ctypes.c_long * 3)()
+        _check(lib().fdetd_plan_kernel_times(self.handle, ms, calls))
+        return {name: (ms[i], calls[i]) for i, name in enumerate(("projection", "spectral", "backprojection"))}
+
+    def close(self):
+        if self.handle:
+            lib().fdetd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fdetd_plan_modes(Nz, Nr, modes, order, dz, dr, dt, precision="fp64", flags=0):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * len(modes))(*modes)
+    _check(lib().fdetd_plan_modes(ctypes.byref(h), Nz, Nr, arr, len(modes), order, dz, dr, dt,
+                                  PRECISIONS[precision], flags))
+    return FdetdPlan(h, Nz, Nr, modes, order, dz, dr, dt, precision)
+
+
+def fdetd_plan(Nz, Nr, M, order, dz, dr, dt, precision="fp64", flags=0):
+    return fdetd_plan_modes(Nz, Nr, list(range(M + 1)), order, dz, dr, dt, precision, flags)
+
+
+def _check_tensor(t, plan, ncomp, name):
+    shape = (len(plan.modes), ncomp, plan.Nz, plan.Nr)
+    if tuple(t.shape) != shape:
+        raise FdetdError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    if t.dtype != plan.complex_dtype:
+        raise FdetdError(f"{name} must be {plan.complex_dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise FdetdError(f"{name} must be contiguous")
+
+
+def fdetd_step(plan, fields, J=None, nsteps=1, stream=None):
+    """Advance device `fields` in place by nsteps exact midpoint steps (see include/fdetd.h)."""
+    if not fields.is_cuda:
+        raise FdetdError("fields must be a CUDA tensor (use fdetd_step_host for host arrays)")
+    _check_tensor(fields, plan, 6, "fields")
+    jp = None
+    if J is not None:
+        _check_tensor(J, plan, 3, "J")
+        jp = J.data_ptr()
+    _check(lib().fdetd_step(plan.handle, fields.data_ptr(), jp, nsteps, _stream_handle(stream)))
+    return fields
+
+
+def fdetd_step_host(plan, host_fields, host_J=None, nsteps=1, stream=None):
+    """End-to-end step on HOST tensors (pinned recommended): h2d, step, d2h inside the call."""
+    _check_tensor(host_fields, plan, 6, "fields")
+    jp = None
+    if host_J is not None:
+        _check_tensor(host_J, plan, 3, "J")
+        jp = host_J.data_ptr()
+    _check(lib().fdetd_step_host(plan.handle, host_fields.data_ptr(), jp, nsteps, _stream_handle(stream)))
+    return host_fields
+
+
+def fdetd_host_tables(Nz, Nr, m, order, dz, dr, dt):
+    """Host-only FP64 plan tables of one mode (no GPU needed)."""
+    N3 = 3 * Nr
+    out = {k: np.zeros((N3, N3)) for k in ("PE", "PB", "QE", "QB")}
+    out["lam"], out["mu"] = np.zeros(Nr), np.zeros(Nr)
+    out["tm_live"], out["te_live"] = np.zeros(Nr, np.uint8), np.zeros(Nr, np.uint8)
+    out["kappa2"] = np.zeros(Nz)
+    sp, sm = np.zeros(2 * Nz), np.zeros(2 * Nz)
+    u8 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    _check(lib().fdetd_host_tables(Nz, Nr, m, order, dz, dr, dt, _dptr(out["PE"]), _dptr(out["PB"]),
+                                   _dptr(out["QE"]), _dptr(out["QB"]), _dptr(out["lam"]), _dptr(out["mu"]),
+                                   u8(out["tm_live"]), u8(out["te_live"]), _dptr(out["kappa2"]), _dptr(sp),
+                                   _dptr(sm)))
+    out["sp"] = sp[0::2] + 1j * sp[1::2]
+    out["sm"] = sm[0::2] + 1j * sm[1::2]
+    return out
+
+
+def fdetd_host_coeffs(kind, order):
+    buf = np.zeros(64)
+    n = lib().fdetd_host_coeffs(kind, order, _dptr(buf))
+    if n < 0:
+        _check(n)
+    return buf[:n].copy()
+
+
+class EnvelopePlan:
+    def __init__(self, handle, Nz, Nr, order, taylor_order, dz, dr, dt, k0):
+        self.handle = handle
+        self.Nz, self.Nr, self.order, self.taylor_order = Nz, Nr, order, taylor_order
+        self.dz, self.dr, self.dt, self.k0 = dz, dr, dt, k0
+
+    @property
+    def launches_per_step(self):
+        return lib().envelope_plan_launches_per_step(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().envelope_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def envelope_plan(Nz, Nr, order, taylor_order, dz, dr, dt, k0=2 * np.pi):
+    h = ctypes.c_void_p()
+    _check(lib().envelope_plan(ctypes.byref(h), Nz, Nr, order, taylor_order, dz, dr, dt, k0))
+    return EnvelopePlan(h, Nz, Nr, order, taylor_order, dz, dr, dt, k0)
+
+
+def envelope_step(plan, a, chi, nsteps=1, stream=None):
+    """Advance psi_a = a[0] (a), a[1] (a~) in place: a cuda complex64 [2][Nz][Nr], chi float32 [Nz][Nr]."""
+    import torch
+    if not a.is_cuda or a.dtype != torch.complex64 or tuple(a.shape) != (2, plan.Nz, plan.Nr) or not a.is_contiguous():
+        raise FdetdError("a must be a contiguous cuda complex64 tensor of shape (2, Nz, Nr)")
+    if not chi.is_cuda or chi.dtype != torch.float32 or tuple(chi.shape) != (plan.Nz, plan.Nr) or not chi.is_contiguous():
+        raise FdetdError("chi must be a contiguous cuda float32 tensor of shape (Nz, Nr)")
+    _check(lib().envelope_step(plan.handle, a.data_ptr(), chi.data_ptr(), nsteps, _stream_handle(stream)))
+    return a

@@ -1,0 +1,54 @@
+// Shared device helpers and plan layout for the FDETD kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdetd {
+
+// ---------------------------------------------------------------- complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<double> { typedef double2 type; };
+template <> struct cplx<float> { typedef float2 type; };
+
+template <typename C> __device__ __forceinline__ C cmake(double r, double i) { C c; c.x = r; c.y = i; return c; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C c; c.x = a.x + b.x; c.y = a.y + b.y; return c; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C c; c.x = a.x - b.x; c.y = a.y - b.y; return c; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
+}
+template <typename C> __device__ __forceinline__ C cmulconj(C a, C b) {  // a * conj(b)
+  C c; c.x = a.x * b.x + a.y * b.y; c.y = a.y * b.x - a.x * b.y; return c;
+}
+// multiply by tau = -i (rotated variables) and by 1/tau = +i
+template <typename C> __device__ __forceinline__ C mul_tau(C a) { C c; c.x = a.y; c.y = -a.x; return c; }
+template <typename C> __device__ __forceinline__ C mul_itau(C a) { C c; c.x = -a.y; c.y = a.x; return c; }
+
+// ---------------------------------------------------------------- coefficient arithmetic
+// FP64 path: coefficients are doubles.  FP32 paths: coefficients are unevaluated
+// sums hi + lo of two floats, so that a coefficient rounded once to FP32 does not
+// bias every step the same way (a coherent phase error would grow linearly with
+// the number of steps); data stay FP32.
+struct df { float h, l; };
+
+__device__ __forceinline__ double rmul(double c, double x) { return c * x; }
+__device__ __forceinline__ float rmul(df c, float x) { return fmaf(c.h, x, c.l * x); }
+
+template <typename K, typename C> __device__ __forceinline__ C cscale(K c, C x) {
+  C r; r.x = rmul(c, x.x); r.y = rmul(c, x.y); return r;
+}
+// complex coefficient (re, im) times complex data
+template <typename K, typename C> __device__ __forceinline__ C ccoef(K re, K im, C x) {
+  C r; r.x = rmul(re, x.x) - rmul(im, x.y); r.y = rmul(re, x.y) + rmul(im, x.x); return r;
+}
+
+// Phase record per (family, j, q): exp(t M) = I + A1 M + A2 M^2 at t = dt (A) and dt/2 (B).
+struct PhaseD { double A1, A2, B1, B2; };
+struct PhaseF { df A1, A2; float B1, B2, pad0, pad1; };
+
+// z symbols per q: s+ and s- (complex), kappa^2
+struct ZSymD { double spr, spi, smr, smi, k2, pad0, pad1, pad2; };
+struct ZSymF { df spr, spi, smr, smi, k2; float pad0, pad1; };
+
+__device__ __forceinline__ unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
+
+}  // namespace fdetd

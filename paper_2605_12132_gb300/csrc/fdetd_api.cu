@@ -1,0 +1,547 @@
+// C-ABI of the FDETD solver: plan construction (host FP64 tables -> device),
+// the per-step launch sequence, the host-only table export, and the envelope
+// propagator.  See include/fdetd.h for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fdetd.h"
+#include "kernels.h"
+#include "plan_host.h"
+
+using namespace fdetd;
+
+static thread_local std::string g_err;
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+static df to_df(double x) {
+  df r;
+  r.h = (float)x;
+  r.l = (float)(x - (double)r.h);
+  return r;
+}
+
+struct fdetd_plan_s {
+  int Nz = 0, Nr = 0, nmodes = 0, order = 0, precision = 0, logNz = 0;
+  double dz = 0, dr = 0, dt = 0;
+  std::vector<int> modes;
+  void* d_P = nullptr;
+  void* d_Q = nullptr;
+  void* d_phase = nullptr;
+  void* d_zsym = nullptr;
+  void* d_lam = nullptr;
+  void* d_tw = nullptr;
+  void* d_coef = nullptr;
+  void* d_hostio = nullptr;  // staging for fdetd_step_host (lazy)
+  size_t hostio_bytes = 0;
+  TcPlan* tc = nullptr;
+  size_t bytes = 0;
+  // optional per-kernel timing: events recorded around each launch on the launch stream
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  double kern_ms[3] = {0, 0, 0};
+  long kern_calls[3] = {0, 0, 0};
+};
+
+static void prof_mark(fdetd_plan_s* p, int kind, bool begin, cudaStream_t st) {
+  if (!p->profiling) return;
+  if (begin) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    p->ev.push_back({kind, {a, b}});
+    cudaEventRecord(a, st);
+  } else {
+    cudaEventRecord(p->ev.back().second.second, st);
+  }
+}
+
+static void prof_collect(fdetd_plan_s* p) {
+  for (auto& e : p->ev) {
+    float ms = 0.f;
+    cudaEventSynchronize(e.second.second);
+    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+    p->kern_ms[e.first] += ms;
+    p->kern_calls[e.first] += 1;
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  p->ev.clear();
+}
+
+static void plan_free(fdetd_plan_s* p) {
+  if (!p) return;
+  prof_collect(p);
+  void* ptrs[] = {p->d_P, p->d_Q, p->d_phase, p->d_zsym, p->d_lam, p->d_tw, p->d_coef, p->d_hostio};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->tc) tc_destroy(p->tc);
+  delete p;
+}
+
+static cudaError_t upload(void** dst, const void* src, size_t bytes, size_t& total) {
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return e;
+  total += bytes;
+  return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+}
+
+static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* modes, int nmodes, int order,
+                                double dz, double dr, double dt, int precision, uint64_t flags) {
+  (void)flags;
+  if (!out) return fail(FDETD_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!modes || nmodes < 1 || nmodes > 64) return fail(FDETD_ERR_ARG, "need 1..64 modes");
+  if (precision < FDETD_PREC_FP64 || precision > FDETD_PREC_BF16X6) return fail(FDETD_ERR_ARG, "unknown precision");
+  if (!is_pow2(Nz) || Nz < 64 || Nz > 8192)
+    return fail(FDETD_ERR_UNSUPPORTED, "this build needs Nz a power of two in 64..8192");
+  const bool hasJ_max = true;
+  if (spectral_smem_bytes(Nz, precision, hasJ_max) > 227 * 1024)
+    return fail(FDETD_ERR_UNSUPPORTED, "Nz too long for the single-pass z transform at this precision");
+  HostPlan hp;
+  std::string msg;
+  int rc = build_host_plan(hp, Nz, Nr, modes, nmodes, order, dz, dr, dt, msg);
+  if (rc) return fail(rc == 4 ? FDETD_ERR_EIG : FDETD_ERR_ARG, msg);
+
+  fdetd_plan_s* p = new fdetd_plan_s();
+  p->Nz = Nz;
+  p->Nr = Nr;
+  p->nmodes = nmodes;
+  p->order = order;
+  p->precision = precision;
+  p->dz = dz;
+  p->dr = dr;
+  p->dt = dt;
+  p->modes.assign(modes, modes + nmodes);
+  while ((1 << p->logNz) < Nz) ++p->logNz;
+  const int n = Nr, N3 = 3 * Nr;
+  const bool fp64 = precision == FDETD_PREC_FP64;
+  const bool tc = precision == FDETD_PREC_BF16X3 || precision == FDETD_PREC_BF16X6;
+  cudaError_t e = cudaSuccess;
+
+  // projection matrices: [nmodes][2][3n][3n]
+  std::vector<double> P((size_t)nmodes * 2 * N3 * N3), Q(P.size());
+  for (int i = 0; i < nmodes; ++i) {
+    const size_t blk = (size_t)N3 * N3;
+    std::copy(hp.mp[i].PE.begin(), hp.mp[i].PE.end(), P.begin() + (2 * i) * blk);
+    std::copy(hp.mp[i].PB.begin(), hp.mp[i].PB.end(), P.begin() + (2 * i + 1) * blk);
+    std::copy(hp.mp[i].QE.begin(), hp.mp[i].QE.end(), Q.begin() + (2 * i) * blk);
+    std::copy(hp.mp[i].QB.begin(), hp.mp[i].QB.end(), Q.begin() + (2 * i + 1) * blk);
+  }
+  if (tc) {
+    char m2[256] = {0};
+    e = tc_create(&p->tc, Nz, n, nmodes, precision == FDETD_PREC_BF16X3 ? 2 : 3, P.data(), Q.data(), m2,
+                  sizeof(m2));
+    if (e != cudaSuccess) {
+      plan_free(p);
+      return fail(e == cudaErrorNotSupported ? FDETD_ERR_UNSUPPORTED : FDETD_ERR_CUDA,
+                  std::string("tensor-core plan: ") + m2 + " (" + cudaGetErrorString(e) + ")");
+    }
+    p->bytes += tc_device_bytes(p->tc);
+  } else if (fp64) {
+    if ((e = upload(&p->d_P, P.data(), P.size() * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
+    if ((e = upload(&p->d_Q, Q.data(), Q.size() * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
+  } else {
+    std::vector<float> Pf(P.begin(), P.end()), Qf(Q.begin(), Q.end());
+    if ((e = upload(&p->d_P, Pf.data(), Pf.size() * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
+    if ((e = upload(&p->d_Q, Qf.data(), Qf.size() * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
+  }
+  {
+    // phase tables [nmodes][2][n][Nz], eigenvalue tables [nmodes][2][n], z symbols [Nz], twiddles [Nz/2]
+    const size_t nph = (size_t)nmodes * 2 * n * Nz;
+    std::vector<PhaseD> phd;
+    std::vector<PhaseF> phf;
+    if (fp64) phd.resize(nph); else phf.resize(nph);
+    std::vector<double> lamd((size_t)nmodes * 2 * n);
+    std::vector<df> lamf(lamd.size());
+    for (int i = 0; i < nmodes; ++i)
+      for (int fam = 0; fam < 2; ++fam)
+        for (int j = 0; j < n; ++j) {
+          const ModePlan& mp = hp.mp[i];
+          const double lv = fam == 0 ? mp.lam[j] : mp.mu[j];
+          const bool live = fam == 0 ? mp.tm_live[j] : mp.te_live[j];
+          lamd[(size_t)(i * 2 + fam) * n + j] = lv;
+          lamf[(size_t)(i * 2 + fam) * n + j] = to_df(lv);
+          for (int q = 0; q < Nz; ++q) {
+            double A1 = 0, A2 = 0, B1 = 0, B2 = 0;
+            if (live) {
+              const double w = std::sqrt(hp.kappa2[q] + lv);
+              phase_coeffs(w, dt, &A1, &A2);
+              phase_coeffs(w, 0.5 * dt, &B1, &B2);
+            }
+            const size_t k = ((size_t)(i * 2 + fam) * n + j) * Nz + q;
+            if (fp64) {
+              phd[k] = PhaseD{A1, A2, B1, B2};
+            } else {
+              PhaseF f;
+              f.A1 = to_df(A1);
+              f.A2 = to_df(A2);
+              f.B1 = (float)B1;
+              f.B2 = (float)B2;
+              f.pad0 = f.pad1 = 0.f;
+              phf[k] = f;
+            }
+          }
+        }
+    if (fp64) {
+      if ((e = upload(&p->d_phase, phd.data(), nph * sizeof(PhaseD), p->bytes)) != cudaSuccess) goto cuda_fail;
+      if ((e = upload(&p->d_lam, lamd.data(), lamd.size() * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
+    } else {
+      if ((e = upload(&p->d_phase, phf.data(), nph * sizeof(PhaseF), p->bytes)) != cudaSuccess) goto cuda_fail;
+      if ((e = upload(&p->d_lam, lamf.data(), lamf.size() * sizeof(df), p->bytes)) != cudaSuccess) goto cuda_fail;
+    }
+    std::vector<ZSymD> zd(Nz);
+    std::vector<ZSymF> zf(Nz);
+    for (int q = 0; q < Nz; ++q) {
+      zd[q] = ZSymD{hp.sp_re[q], hp.sp_im[q], hp.sm_re[q], hp.sm_im[q], hp.kappa2[q], 0, 0, 0};
+      ZSymF f;
+      f.spr = to_df(hp.sp_re[q]);
+      f.spi = to_df(hp.sp_im[q]);
+      f.smr = to_df(hp.sm_re[q]);
+      f.smi = to_df(hp.sm_im[q]);
+      f.k2 = to_df(hp.kappa2[q]);
+      f.pad0 = f.pad1 = 0.f;
+      zf[q] = f;
+    }
+    if (fp64) {
+      if ((e = upload(&p->d_zsym, zd.data(), Nz * sizeof(ZSymD), p->bytes)) != cudaSuccess) goto cuda_fail;
+    } else {
+      if ((e = upload(&p->d_zsym, zf.data(), Nz * sizeof(ZSymF), p->bytes)) != cudaSuccess) goto cuda_fail;
+    }
+    const double pi = 3.14159265358979323846;
+    std::vector<double> twd(Nz);
+    std::vector<float> twf(Nz);
+    for (int k = 0; k < Nz / 2; ++k) {
+      const double ang = -2.0 * pi * (double)k / Nz;
+      twd[2 * k] = std::cos(ang);
+      twd[2 * k + 1] = std::sin(ang);
+      twf[2 * k] = (float)twd[2 * k];
+      twf[2 * k + 1] = (float)twd[2 * k + 1];
+    }
+    if (fp64) {
+      if ((e = upload(&p->d_tw, twd.data(), Nz * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
+    } else {
+      if ((e = upload(&p->d_tw, twf.data(), Nz * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
+    }
+    const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
+    if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
+    p->bytes += cbytes;
+  }
+  *out = p;
+  return FDETD_OK;
+cuda_fail:
+  plan_free(p);
+  return fail(e == cudaErrorMemoryAllocation ? FDETD_ERR_OOM : FDETD_ERR_CUDA,
+              std::string("plan upload: ") + cudaGetErrorString(e));
+}
+
+extern "C" int fdetd_plan(fdetd_plan_t* out, int Nz, int Nr, int M, int order, double dz, double dr, double dt,
+                          int precision, uint64_t flags) {
+  if (M < 0 || M > 63) return fail(FDETD_ERR_ARG, "M must be 0..63");
+  std::vector<int> modes(M + 1);
+  for (int m = 0; m <= M; ++m) modes[m] = m;
+  return fdetd_plan_modes(out, Nz, Nr, modes.data(), M + 1, order, dz, dr, dt, precision, flags);
+}
+
+extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nsteps, void* stream) {
+  if (!p) return fail(FDETD_ERR_ARG, "plan is null");
+  if (!fields) return fail(FDETD_ERR_ARG, "fields is null");
+  if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
+  if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
+  SpectralArgs sa;
+  sa.coef = p->d_coef;
+  sa.phase = p->d_phase;
+  sa.zsym = p->d_zsym;
+  sa.lam = p->d_lam;
+  sa.twiddle = p->d_tw;
+  sa.split_out = p->tc ? tc_split_buffer(p->tc) : nullptr;
+  sa.npieces = p->precision == FDETD_PREC_BF16X3 ? 2 : 3;
+  sa.split_rows = p->tc ? tc_split_rows(p->tc) : 0;
+  sa.Nz = p->Nz;
+  sa.logNz = p->logNz;
+  sa.n = p->Nr;
+  sa.dt = p->dt;
+  sa.hasJ = J != nullptr;
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e;
+    prof_mark(p, 0, true, st);
+    if (p->tc) {
+      e = tc_project(p->tc, fields, J, p->d_coef, st);
+    } else {
+      ProjArgs pa{fields, J, p->d_P, p->d_coef, p->Nz, p->Nr};
+      e = launch_project_simt(pa, p->nmodes, prec, st);
+    }
+    prof_mark(p, 0, false, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("projection: ") + cudaGetErrorString(e));
+    prof_mark(p, 1, true, st);
+    e = launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
+    prof_mark(p, 1, false, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("spectral: ") + cudaGetErrorString(e));
+    prof_mark(p, 2, true, st);
+    if (p->tc) {
+      e = tc_backproject(p->tc, fields, st);
+    } else {
+      BackArgs ba{fields, p->d_Q, p->d_coef, p->Nz, p->Nr};
+      e = launch_backproject_simt(ba, p->nmodes, prec, st);
+    }
+    prof_mark(p, 2, false, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("back-projection: ") + cudaGetErrorString(e));
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_step_host(fdetd_plan_t p, void* host_fields, const void* host_J, int nsteps, void* stream) {
+  if (!p || !host_fields) return fail(FDETD_ERR_ARG, "null argument");
+  const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
+  const size_t fb = (size_t)p->nmodes * 6 * p->Nz * p->Nr * elt, jb = (size_t)p->nmodes * 3 * p->Nz * p->Nr * elt;
+  const size_t need = fb + (host_J ? jb : 0);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->hostio_bytes < need) {
+    if (p->d_hostio) cudaFree(p->d_hostio);
+    p->d_hostio = nullptr;
+    p->hostio_bytes = 0;
+    if (cudaMalloc(&p->d_hostio, need) != cudaSuccess) return fail(FDETD_ERR_OOM, "staging allocation failed");
+    p->hostio_bytes = need;
+  }
+  char* dF = (char*)p->d_hostio;
+  char* dJ = host_J ? dF + fb : nullptr;
+  cudaError_t e = cudaMemcpyAsync(dF, host_fields, fb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && host_J) e = cudaMemcpyAsync(dJ, host_J, jb, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("h2d: ") + cudaGetErrorString(e));
+  int rc = fdetd_step(p, dF, dJ, nsteps, stream);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(host_fields, dF, fb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("d2h: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+extern "C" size_t fdetd_plan_device_bytes(fdetd_plan_t p) { return p ? p->bytes : 0; }
+
+extern "C" int fdetd_plan_launches_per_step(fdetd_plan_t p) {
+  if (!p) return 0;
+  return (p->tc ? tc_launches_per_step(p->tc) : 2) + 1;
+}
+
+extern "C" int fdetd_plan_status(fdetd_plan_t p, void* stream) {
+  if (!p) return fail(FDETD_ERR_ARG, "plan is null");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  if (p->tc) {
+    int flag = 0;
+    e = cudaMemcpy(&flag, tc_error_flag(p->tc), sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
+    if (flag) {
+      cudaMemset(tc_error_flag(p->tc), 0, sizeof(int));
+      return fail(FDETD_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (stage code " + std::to_string(flag) + ")");
+    }
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_set_profiling(fdetd_plan_t p, int on) {
+  if (!p) return fail(FDETD_ERR_ARG, "plan is null");
+  prof_collect(p);
+  p->profiling = on != 0;
+  for (int k = 0; k < 3; ++k) {
+    p->kern_ms[k] = 0;
+    p->kern_calls[k] = 0;
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_kernel_times(fdetd_plan_t p, double* ms, long* calls) {
+  if (!p || !ms || !calls) return fail(FDETD_ERR_ARG, "null argument");
+  prof_collect(p);
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = p->kern_ms[k];
+    calls[k] = p->kern_calls[k];
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_destroy(fdetd_plan_t p) {
+  plan_free(p);
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, double dr, double dt, double* PE,
+                                 double* PB, double* QE, double* QB, double* lam, double* mu, uint8_t* tm_live,
+                                 uint8_t* te_live, double* kappa2, double* sp, double* sm) {
+  HostPlan hp;
+  std::string msg;
+  int rc = build_host_plan(hp, Nz, Nr, &m, 1, order, dz, dr, dt, msg);
+  if (rc) return fail(rc == 4 ? FDETD_ERR_EIG : FDETD_ERR_ARG, msg);
+  const ModePlan& mp = hp.mp[0];
+  auto cp = [](double* dst, const std::vector<double>& v) {
+    if (dst) std::copy(v.begin(), v.end(), dst);
+  };
+  cp(PE, mp.PE);
+  cp(PB, mp.PB);
+  cp(QE, mp.QE);
+  cp(QB, mp.QB);
+  cp(lam, mp.lam);
+  cp(mu, mp.mu);
+  cp(kappa2, hp.kappa2);
+  if (tm_live) std::copy(mp.tm_live.begin(), mp.tm_live.end(), tm_live);
+  if (te_live) std::copy(mp.te_live.begin(), mp.te_live.end(), te_live);
+  for (int q = 0; q < Nz; ++q) {
+    if (sp) { sp[2 * q] = hp.sp_re[q]; sp[2 * q + 1] = hp.sp_im[q]; }
+    if (sm) { sm[2 * q] = hp.sm_re[q]; sm[2 * q + 1] = hp.sm_im[q]; }
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_host_coeffs(int kind, int order, double* out) {
+  if (order < 2 || order > 32 || (order & 1) || !out) return fail(FDETD_ERR_ARG, "bad order or null out");
+  std::vector<double> v;
+  if (kind == 0) v = staggered_coeffs(order);
+  else if (kind == 1) v = centred_d1_coeffs(order);
+  else if (kind == 2) {
+    double e0 = 0;
+    std::vector<double> e = centred_d2_coeffs(order, &e0);
+    v.push_back(e0);
+    v.insert(v.end(), e.begin(), e.end());
+  } else if (kind == 3) v = axis_coeffs(order / 2);
+  else return fail(FDETD_ERR_ARG, "unknown kind");
+  std::copy(v.begin(), v.end(), out);
+  return (int)v.size();
+}
+
+// ------------------------------------------------------------------ envelope
+
+struct envelope_plan_s {
+  int Nz = 0, Nr = 0, order = 0, NT = 0;
+  double dz = 0, dr = 0, dt = 0, k0 = 0;
+  float* d_lr = nullptr;
+  float2* d_buf = nullptr;  // T0 (a, a~), T1 (a, a~), ACC (a, a~)
+  EnvArgs base;
+};
+
+extern "C" int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, int taylor_order, double dz,
+                             double dr, double dt, double k0) {
+  if (!out) return fail(FDETD_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (order < 2 || order > 32 || (order & 1)) return fail(FDETD_ERR_ARG, "order must be even, 2..32");
+  const int N = order / 2;
+  if (taylor_order < 1 || taylor_order > 16) return fail(FDETD_ERR_ARG, "taylor_order must be 1..16");
+  if (Nz < 2 * order || Nr < N + 1 || !(dz > 0) || !(dr > 0) || !(dt > 0))
+    return fail(FDETD_ERR_ARG, "invalid sizes or spacings");
+  envelope_plan_s* p = new envelope_plan_s();
+  p->Nz = Nz; p->Nr = Nr; p->order = order; p->NT = taylor_order;
+  p->dz = dz; p->dr = dr; p->dt = dt; p->k0 = k0;
+  double e0 = 0;
+  const std::vector<double> e2 = centred_d2_coeffs(order, &e0), d1 = centred_d1_coeffs(order);
+  // radial Laplacian band (Eq. spatialAM_laplaceR), symmetric mirror j<0 -> -1-j (m = 0)
+  const int W = 2 * N + 1;
+  std::vector<double> band((size_t)Nr * W, 0.0);
+  for (int k = 0; k < Nr; ++k) {
+    const double rho = (k + 0.5) * dr;
+    band[(size_t)k * W + N] += e0 / (dr * dr);
+    for (int t = 1; t <= N; ++t) {
+      const int js[2] = {k + t, k - t};
+      const double ws[2] = {e2[t - 1] / (dr * dr) + d1[t - 1] / (dr * rho), e2[t - 1] / (dr * dr) - d1[t - 1] / (dr * rho)};
+      for (int s = 0; s < 2; ++s) {
+        int j = js[s];
+        if (j < 0) j = -1 - j;
+        if (j < Nr) band[(size_t)k * W + (j - k) + N] += ws[s];
+      }
+    }
+  }
+  std::vector<float> bandf((size_t)Nr * (W + 1));
+  for (int k = 0; k < Nr; ++k) {
+    double rs = 0.0;
+    for (int t = 0; t < W; ++t) {
+      bandf[(size_t)k * (W + 1) + t] = (float)band[(size_t)k * W + t];
+      rs += band[(size_t)k * W + t];
+    }
+    bandf[(size_t)k * (W + 1) + W] = (float)rs;
+  }
+  size_t tot = 0;
+  cudaError_t e = upload((void**)&p->d_lr, bandf.data(), bandf.size() * 4, tot);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_buf, (size_t)6 * Nz * Nr * sizeof(float2));
+  if (e != cudaSuccess) {
+    if (p->d_lr) cudaFree(p->d_lr);
+    delete p;
+    return fail(e == cudaErrorMemoryAllocation ? FDETD_ERR_OOM : FDETD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  EnvArgs& b = p->base;
+  memset(&b, 0, sizeof(b));
+  b.lr = p->d_lr;
+  b.Nz = Nz;
+  b.Nr = Nr;
+  b.N = N;
+  b.cz2[0] = (float)(e0 / (dz * dz));
+  for (int t = 1; t <= N; ++t) {
+    b.cz2[t] = (float)(e2[t - 1] / (dz * dz));
+    b.cz1[t] = (float)(d1[t - 1] / dz);
+  }
+  b.k2 = (float)(2.0 * k0);
+  *out = p;
+  return FDETD_OK;
+}
+
+extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int nsteps, void* stream) {
+  if (!p || !a || !chi) return fail(FDETD_ERR_ARG, "null argument");
+  if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
+  if (((uintptr_t)a & 15) || ((uintptr_t)chi & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t plane = (size_t)p->Nz * p->Nr;
+  float2* psi_a = (float2*)a;
+  float2* psi_t = psi_a + plane;
+  float2* T[2][2] = {{p->d_buf, p->d_buf + plane}, {p->d_buf + 2 * plane, p->d_buf + 3 * plane}};
+  float2* ACC[2] = {p->d_buf + 4 * plane, p->d_buf + 5 * plane};
+  EnvArgs g = p->base;
+  g.chi = chi;
+  for (int s = 0; s < nsteps; ++s) {
+    for (int n = 1; n <= p->NT; ++n) {
+      g.scale = (float)(p->dt / n);
+      if (n == 1) {
+        g.in_a = psi_a; g.in_t = psi_t;
+        g.accin_a = psi_a; g.accin_t = psi_t;
+      } else {
+        g.in_a = T[(n - 2) & 1][0]; g.in_t = T[(n - 2) & 1][1];
+        g.accin_a = ACC[0]; g.accin_t = ACC[1];
+      }
+      const bool last = n == p->NT;
+      g.out_a = last ? nullptr : T[(n - 1) & 1][0];
+      g.out_t = last ? nullptr : T[(n - 1) & 1][1];
+      const bool to_psi = last && n > 1;
+      g.accout_a = to_psi ? psi_a : ACC[0];
+      g.accout_t = to_psi ? psi_t : ACC[1];
+      cudaError_t e = launch_envelope_term(g, st);
+      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
+    }
+    if (p->NT == 1) {
+      cudaError_t e = cudaMemcpyAsync(psi_a, ACC[0], 2 * plane * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  return FDETD_OK;
+}
+
+extern "C" int envelope_plan_launches_per_step(envelope_plan_t p) { return p ? p->NT : 0; }
+
+extern "C" int envelope_plan_destroy(envelope_plan_t p) {
+  if (!p) return FDETD_OK;
+  if (p->d_lr) cudaFree(p->d_lr);
+  if (p->d_buf) cudaFree(p->d_buf);
+  delete p;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_last_error(char* buf, size_t len) {
+  if (!buf || !len) return FDETD_ERR_ARG;
+  snprintf(buf, len, "%s", g_err.c_str());
+  return FDETD_OK;
+}

@@ -1,0 +1,98 @@
+// Kernel argument records and launchers of the FDETD step (internal).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdetd {
+
+// ---------------------------------------------------------------- spectral kernel
+struct SpectralArgs {
+  void* coef;            // [nmodes][9][n][Nz] complex<T>; first 6 arrays updated in place
+  const void* phase;     // [nmodes][2][n][Nz] PhaseD / PhaseF
+  const void* zsym;      // [Nz] ZSymD / ZSymF
+  const void* lam;       // [nmodes][2][n] double / df (lambda for TM, mu for TE)
+  const void* twiddle;   // [Nz/2] complex<T>, exp(-2 pi i k / Nz)
+  __nv_bfloat16* split_out;  // tensor-core path: [nmodes][npieces][6][split_rows][2 Nz]
+  int npieces;
+  int split_rows;            // coefficient rows per block in split_out (n padded to the K tile)
+  int Nz, logNz, n;
+  double dt;
+  int hasJ;
+};
+
+cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);
+size_t spectral_smem_bytes(int Nz, int precision, bool hasJ);
+
+// bf16 split of an FP32 value into npieces (2 or 3) terms whose sum reproduces it to
+// 16 / 24 significant bits; piece p of coefficient array c goes to
+// out[((md * npieces + p) * 6 + c) * rows + j][2 z + part].
+__device__ __forceinline__ void split_store(__nv_bfloat16* out, int npieces, int md, int c, int j, int z, int rows,
+                                            int Nz, float vr, float vi) {
+  float r0 = vr, r1 = vi;
+  for (int p = 0; p < npieces; ++p) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(r0), h1 = __float2bfloat16_rn(r1);
+    __nv_bfloat162 pr;
+    pr.x = h0;
+    pr.y = h1;
+    const size_t row = ((size_t)(md * npieces + p) * 6 + c) * rows + j;
+    *reinterpret_cast<__nv_bfloat162*>(out + row * (size_t)(2 * Nz) + 2 * z) = pr;
+    r0 -= __bfloat162float(h0);
+    r1 -= __bfloat162float(h1);
+  }
+}
+
+// ---------------------------------------------------------------- CUDA-core projections
+struct ProjArgs {
+  const void* fields;  // [nmodes][6][Nz][Nr] complex<T>
+  const void* J;       // [nmodes][3][Nz][Nr] complex<T> or null
+  const void* P;       // [nmodes][2][3n][3n] T   (PE, PB)
+  void* coef;          // [nmodes][9][n][Nz] complex<T>
+  int Nz, n;
+};
+struct BackArgs {
+  void* fields;        // [nmodes][6][Nz][Nr] complex<T>
+  const void* Q;       // [nmodes][2][3n][3n] T   (QE, QB)
+  const void* coef;    // [nmodes][9][n][Nz] complex<T>
+  int Nz, n;
+};
+
+cudaError_t launch_project_simt(const ProjArgs& a, int nmodes, int precision, cudaStream_t st);
+cudaError_t launch_backproject_simt(const BackArgs& a, int nmodes, int precision, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor-core projections
+struct TcPlan;  // defined in k_tc.cu
+cudaError_t tc_create(TcPlan** out, int Nz, int n, int nmodes, int npieces, const double* P, const double* Q,
+                      char* msg, size_t msglen);
+void tc_destroy(TcPlan* p);
+size_t tc_device_bytes(const TcPlan* p);
+__nv_bfloat16* tc_split_buffer(TcPlan* p);
+int tc_split_rows(const TcPlan* p);
+int* tc_error_flag(TcPlan* p);
+cudaError_t tc_project(TcPlan* p, const void* fields, const void* J, void* coef, cudaStream_t st);
+cudaError_t tc_backproject(TcPlan* p, void* fields, cudaStream_t st);
+int tc_launches_per_step(const TcPlan* p);
+
+// ---------------------------------------------------------------- envelope
+struct EnvArgs {
+  // One Taylor term: out = scale * H_a(in); accout = accin + out.
+  const float2* in_a;   // [Nz][Nr] previous term, a part
+  const float2* in_t;   // [Nz][Nr] previous term, a~ part
+  float2* out_a;        // next term (may be null when not needed again)
+  float2* out_t;
+  const float2* accin_a;
+  const float2* accin_t;
+  float2* accout_a;     // running Taylor sum
+  float2* accout_t;
+  const float* chi;     // [Nz][Nr]
+  const float* lr;      // [Nr][2N+2] radial Laplacian band, axis mirror folded (column r + t at index t + N),
+                        // last entry of each row = the row sum (FP64-accumulated)
+  float scale;          // dt / n
+  int Nz, Nr, N;        // N = order / 2
+  float cz2[17];        // centred second derivative in z divided by dz^2: e0, e1..eN
+  float cz1[17];        // centred first derivative in z divided by dz: d1..dN at [1..N]
+  float k2;             // 2 k0
+};
+cudaError_t launch_envelope_term(const EnvArgs& a, cudaStream_t st);
+
+}  // namespace fdetd

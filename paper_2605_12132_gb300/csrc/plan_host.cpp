@@ -1,0 +1,530 @@
+// Host-side FP64 plan builder (see plan_host.h).
+#include "plan_host.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "eig.h"
+
+namespace fdetd {
+
+// --------------------------------------------------------------------------
+// Exact rational products for the stencil coefficients
+// --------------------------------------------------------------------------
+namespace {
+
+typedef __int128 i128;
+
+i128 gcd128(i128 a, i128 b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b) {
+    i128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+struct Rat {
+  i128 p = 0, q = 1;
+  Rat() {}
+  Rat(long long a, long long b = 1) : p(a), q(b) { norm(); }
+  void norm() {
+    if (q < 0) {
+      p = -p;
+      q = -q;
+    }
+    i128 g = gcd128(p, q);
+    if (g > 1) {
+      p /= g;
+      q /= g;
+    }
+  }
+  Rat mul(const Rat& o) const {
+    // cross-reduce before multiplying to keep the intermediates small
+    Rat a = *this, b = o;
+    i128 g1 = gcd128(a.p, b.q), g2 = gcd128(b.p, a.q);
+    if (g1 > 1) { a.p /= g1; b.q /= g1; }
+    if (g2 > 1) { b.p /= g2; a.q /= g2; }
+    Rat r;
+    r.p = a.p * b.p;
+    r.q = a.q * b.q;
+    r.norm();
+    return r;
+  }
+  Rat add(const Rat& o) const {
+    i128 g = gcd128(q, o.q);
+    Rat r;
+    r.p = p * (o.q / g) + o.p * (q / g);
+    r.q = (q / g) * o.q;
+    r.norm();
+    return r;
+  }
+  double val() const {
+    long double v = (long double)p / (long double)q;
+    return (double)v;
+  }
+};
+
+}  // namespace
+
+std::vector<double> staggered_coeffs(int order) {
+  // c_n = 1/(2n-1) prod_{k != n} (2k-1)^2 / ((2k-1)^2 - (2n-1)^2)
+  const int N = order / 2;
+  std::vector<double> c(N);
+  for (int n = 1; n <= N; ++n) {
+    Rat r(1, 2 * n - 1);
+    const long long on = (long long)(2 * n - 1) * (2 * n - 1);
+    for (int k = 1; k <= N; ++k) {
+      if (k == n) continue;
+      const long long ok = (long long)(2 * k - 1) * (2 * k - 1);
+      r = r.mul(Rat(ok, ok - on));
+    }
+    c[n - 1] = r.val();
+  }
+  return c;
+}
+
+static Rat centred_d1_rat(int N, int n) {
+  // d_n = (-1)^(n+1)/n prod_{k=1..n} (N-n+k)/(N+k)
+  Rat r((n % 2) ? 1 : -1, n);
+  for (int k = 1; k <= n; ++k) r = r.mul(Rat(N - n + k, N + k));
+  return r;
+}
+
+std::vector<double> centred_d1_coeffs(int order) {
+  const int N = order / 2;
+  std::vector<double> d(N);
+  for (int n = 1; n <= N; ++n) d[n - 1] = centred_d1_rat(N, n).val();
+  return d;
+}
+
+std::vector<double> centred_d2_coeffs(int order, double* e0) {
+  // e_n = (2/n) d_n, e_0 = -2 sum e_n
+  const int N = order / 2;
+  std::vector<double> e(N);
+  Rat s(0, 1);
+  for (int n = 1; n <= N; ++n) {
+    Rat en = centred_d1_rat(N, n).mul(Rat(2, n));
+    e[n - 1] = en.val();
+    s = s.add(en);
+  }
+  if (e0) *e0 = s.mul(Rat(-2, 1)).val();
+  return e;
+}
+
+std::vector<double> axis_coeffs(int N) {
+  // c_k = prod_{j != k} j^2 / (j^2 - k^2)   (Lagrange in rho^2 at rho = 0, Sec. 2.4)
+  std::vector<double> c(N);
+  for (int k = 1; k <= N; ++k) {
+    Rat r(1, 1);
+    for (int j = 1; j <= N; ++j) {
+      if (j == k) continue;
+      r = r.mul(Rat((long long)j * j, (long long)j * j - (long long)k * k));
+    }
+    c[k - 1] = r.val();
+  }
+  return c;
+}
+
+// --------------------------------------------------------------------------
+// Radial operators (Sec. 2.3-2.4)
+// --------------------------------------------------------------------------
+
+// D^(-): primary-grid operand -> staggered grid; mirror j<0 -> -1-j with sign (-1)^parity.
+static Mat d_minus(int n, const std::vector<double>& c, double dr, int parity) {
+  Mat D(n, n);
+  const double sg = (parity & 1) ? -1.0 : 1.0;
+  for (int k = 0; k < n; ++k)
+    for (int t = 1; t <= (int)c.size(); ++t) {
+      int js[2] = {k + t - 1, k - t};
+      double ws[2] = {c[t - 1], -c[t - 1]};
+      for (int s = 0; s < 2; ++s) {
+        int j = js[s];
+        double w = ws[s];
+        if (j < 0) {
+          j = -1 - j;
+          w *= sg;
+        }
+        if (j < n) D(k, j) += w / dr;
+      }
+    }
+  return D;
+}
+
+// D^(+): staggered-grid operand (slot 0 = axis) -> primary grid; mirror j<0 -> -j.
+static Mat d_plus(int n, const std::vector<double>& c, double dr, int parity) {
+  Mat D(n, n);
+  const double sg = (parity & 1) ? -1.0 : 1.0;
+  for (int k = 0; k < n; ++k)
+    for (int t = 1; t <= (int)c.size(); ++t) {
+      int js[2] = {k + t, k - t + 1};
+      double ws[2] = {c[t - 1], -c[t - 1]};
+      for (int s = 0; s < 2; ++s) {
+        int j = js[s];
+        double w = ws[s];
+        if (j < 0) {
+          j = -j;
+          w *= sg;
+        }
+        if (j < n) D(k, j) += w / dr;
+      }
+    }
+  return D;
+}
+
+// ---------------------------------------------------------------- double-double helpers
+namespace {
+struct DD {
+  double hi, lo;
+};
+inline DD quick_two_sum(double a, double b) {
+  const double s = a + b;
+  return {s, b - (s - a)};
+}
+inline DD two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+inline DD two_prod(double a, double b) {
+  const double p = a * b;
+  return {p, std::fma(a, b, -p)};
+}
+inline DD dd_add(DD a, DD b) {
+  DD s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, s.lo + a.lo + b.lo);
+}
+inline DD dd_mul_d(DD a, double b) {
+  DD p = two_prod(a.hi, b);
+  return quick_two_sum(p.hi, p.lo + a.lo * b);
+}
+inline DD dd_div_d(DD a, double b) {
+  const double q1 = a.hi / b;
+  DD p = two_prod(q1, b);
+  const double r = ((a.hi - p.hi) - p.lo + a.lo) / b;
+  return quick_two_sum(q1, r);
+}
+}  // namespace
+
+// Two-sided Rayleigh-quotient refinement of eigenvalues w_j of a matrix applied through
+// `apply` (double-double residual): w_j <- w_j + y_j.(A x_j - w_j x_j) / y_j.x_j with x_j the
+// right eigenvector (column j of V) and y_j the left one (row j of V^-1).  The residual of a
+// squared radial operator cancels to ~eps |A| in FP64, which is large relative to its small
+// eigenvalues; evaluating it in double-double restores their relative accuracy.
+template <typename F>
+static void refine_eigs(std::vector<double>& w, const Mat& V, const Mat& Vi, F apply) {
+  const int n = V.n;
+  std::vector<double> x(n);
+  std::vector<DD> ax(n);
+  for (int j = 0; j < n; ++j) {
+    for (int k = 0; k < n; ++k) x[k] = V(k, j);
+    apply(x, ax);
+    DD num = {0, 0}, den = {0, 0};
+    for (int k = 0; k < n; ++k) {
+      const DD r = dd_add(ax[k], two_prod(-w[j], x[k]));
+      num = dd_add(num, dd_mul_d(r, Vi(j, k)));
+      den = dd_add(den, two_prod(Vi(j, k), x[k]));
+    }
+    w[j] += (num.hi + num.lo) / (den.hi + den.lo);
+  }
+}
+
+void phase_coeffs(double w, double t, double* A1, double* A2) {
+  const double x = w * t;
+  if (x < 1e-3) {
+    const double x2 = x * x;
+    *A1 = t * (1.0 - x2 / 6.0 * (1.0 - x2 / 20.0));
+    *A2 = 0.5 * t * t * (1.0 - x2 / 12.0 * (1.0 - x2 / 30.0));
+  } else {
+    const double s = std::sin(0.5 * x);
+    *A1 = std::sin(x) / w;
+    *A2 = 2.0 * s * s / (w * w);
+  }
+}
+
+static int build_mode(ModePlan& P, int n, int order, double dr, int m, std::string& msg) {
+  P.m = m;
+  P.n = n;
+  const std::vector<double> c = staggered_coeffs(order);
+  const int ND = order / 2;
+  const int parity = m & 1;  // every radial derivative acts on a parity-m operand
+  Mat Dm = d_minus(n, c, dr, parity), Dp = d_plus(n, c, dr, parity);
+  std::vector<double> rho(n), rhom(n);
+  for (int k = 0; k < n; ++k) {
+    rho[k] = (k + 0.5) * dr;
+    rhom[k] = k * dr;
+  }
+  const std::vector<double> ax = axis_coeffs(ND);
+  std::vector<double> w_scalar(n - 1, 0.0), w_polar(n - 1, 0.0);
+  for (int k = 0; k < ND; ++k) {
+    if (m == 0) w_scalar[k] = ax[k];  // B_z-type constant on the axis for m = 0
+    if (m == 1) w_polar[k] = ax[k];   // E_rho / B_theta constant on the axis for m = 1
+  }
+  const int n1 = n - 1;
+  Mat DivP(n, n1), GradR(n1, n), DivM(n1, n), DpBz(n, n1);
+  for (int k = 0; k < n; ++k)
+    for (int j = 1; j < n; ++j) {
+      DivP(k, j - 1) = Dp(k, j) * rhom[j] / rho[k];
+      DpBz(k, j - 1) = Dp(k, j) + Dp(k, 0) * w_scalar[j - 1];
+    }
+  for (int k = 1; k < n; ++k)
+    for (int j = 0; j < n; ++j) {
+      GradR(k - 1, j) = Dm(k, j);
+      DivM(k - 1, j) = Dm(k, j) * rho[j] / rhom[k];
+    }
+  Mat L0 = matmul(DivP, GradR), L2 = matmul(DivM, DpBz);
+  for (int k = 0; k < n; ++k) L0(k, k) -= (double)m * m / (rho[k] * rho[k]);
+  for (int k = 0; k < n1; ++k) L2(k, k) -= (double)m * m / (rhom[k + 1] * rhom[k + 1]);
+
+  std::vector<double> w0, w2;
+  Mat U, Psi, Ui, Psii;
+  double im0 = 0, im2 = 0;
+  if (eig_real(L0, w0, U, 1e-8, &im0) != 0 || eig_real(L2, w2, Psi, 1e-8, &im2) != 0) {
+    msg = "radial eigen-decomposition failed (complex or non-convergent spectrum) for mode " + std::to_string(m);
+    return 4;
+  }
+  P.max_imag = std::max(im0, im2);
+  if (invert(U, Ui) != 0 || invert(Psi, Psii) != 0) {
+    msg = "singular radial eigenbasis for mode " + std::to_string(m);
+    return 4;
+  }
+  {
+    // L0 x = rho^-1 D^+ (rho_- (D^- x)) - m^2 x / rho^2 in factored form (double-double)
+    const double m2 = (double)m * m;
+    auto apply_L0 = [&](const std::vector<double>& x, std::vector<DD>& out) {
+      std::vector<DD> t(n, DD{0, 0});
+      for (int k = 1; k < n; ++k) {
+        DD acc = {0, 0};
+        for (int j = 0; j < n; ++j)
+          if (Dm(k, j) != 0.0) acc = dd_add(acc, two_prod(Dm(k, j), x[j]));
+        t[k] = dd_mul_d(acc, rhom[k]);
+      }
+      for (int k = 0; k < n; ++k) {
+        DD acc = {0, 0};
+        for (int j = 1; j < n; ++j)
+          if (Dp(k, j) != 0.0) acc = dd_add(acc, dd_mul_d(t[j], Dp(k, j)));
+        out[k] = dd_add(dd_div_d(acc, rho[k]), dd_div_d(dd_div_d(two_prod(-m2, x[k]), rho[k]), rho[k]));
+      }
+    };
+    // L2 psi = rho_-^-1 D^- (rho (D^+ X0 psi)) - m^2 psi / rho_-^2 (double-double)
+    auto apply_L2 = [&](const std::vector<double>& x, std::vector<DD>& out) {
+      std::vector<DD> g(n, DD{0, 0}), u(n, DD{0, 0});
+      for (int k = 1; k < n; ++k) g[k] = DD{x[k - 1], 0};
+      for (int k = 0; k < n1; ++k)
+        if (w_scalar[k] != 0.0) g[0] = dd_add(g[0], two_prod(w_scalar[k], x[k]));
+      for (int k = 0; k < n; ++k) {
+        DD acc = {0, 0};
+        for (int j = 0; j < n; ++j)
+          if (Dp(k, j) != 0.0) acc = dd_add(acc, dd_mul_d(g[j], Dp(k, j)));
+        u[k] = dd_mul_d(acc, rho[k]);
+      }
+      for (int k = 1; k < n; ++k) {
+        DD acc = {0, 0};
+        for (int j = 0; j < n; ++j)
+          if (Dm(k, j) != 0.0) acc = dd_add(acc, dd_mul_d(u[j], Dm(k, j)));
+        out[k - 1] = dd_add(dd_div_d(acc, rhom[k]),
+                            dd_div_d(dd_div_d(two_prod(-m2, x[k - 1]), rhom[k]), rhom[k]));
+      }
+    };
+    refine_eigs(w0, U, Ui, apply_L0);
+    refine_eigs(w2, Psi, Psii, apply_L2);
+  }
+  P.lam.assign(n, 0.0);
+  P.mu.assign(n, 0.0);
+  P.tm_live.assign(n, 1);
+  P.te_live.assign(n, 1);
+  double lmax = 0.0;
+  for (int j = 0; j < n; ++j) lmax = std::max(lmax, std::fabs(w0[j]));
+  int nzero = 0;
+  for (int j = 0; j < n; ++j) {
+    P.lam[j] = -w0[j];
+    if (std::fabs(w0[j]) < 1e-9 * lmax) {
+      P.tm_live[j] = 0;
+      P.lam[j] = 0.0;
+      ++nzero;
+    } else if (P.lam[j] <= 0.0) {
+      msg = "non-positive TM eigenvalue for mode " + std::to_string(m);
+      return 4;
+    }
+  }
+  if (nzero != (m == 0 ? 1 : 0)) {
+    msg = "unexpected TM null space for mode " + std::to_string(m);
+    return 4;
+  }
+  for (int j = 0; j < n1; ++j) {
+    P.mu[j] = -w2[j];
+    if (P.mu[j] <= 0.0) {
+      msg = "non-positive TE eigenvalue for mode " + std::to_string(m);
+      return 4;
+    }
+  }
+  P.mu[n1] = 0.0;
+  P.te_live[n1] = (m == 0) ? 1 : 0;
+
+  // projection pieces
+  Mat LiUi(n, n), MiPsii(n1, n1);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) LiUi(j, k) = P.tm_live[j] ? -Ui(j, k) / P.lam[j] : 0.0;
+  for (int j = 0; j < n1; ++j)
+    for (int k = 0; k < n1; ++k) MiPsii(j, k) = Psii(j, k) / P.mu[j];
+  Mat A_Er = matmul(LiUi, DivP);   // n x n1 (acts on Er slots 1..)
+  Mat C_Et = matmul(MiPsii, DivM);  // n1 x n
+  Mat GU = matmul(GradR, U);        // n1 x n
+  Mat DPsi = matmul(DpBz, Psi);     // n x n1
+
+  const int N3 = 3 * n;
+  P.PE.assign((size_t)N3 * N3, 0.0);
+  P.PB.assign((size_t)N3 * N3, 0.0);
+  P.QE.assign((size_t)N3 * N3, 0.0);
+  P.QB.assign((size_t)N3 * N3, 0.0);
+  auto at = [N3](std::vector<double>& M, int blk_r, int r, int blk_c, int cc) -> double& {
+    return M[(size_t)(blk_r * (N3 / 3) + r) * N3 + blk_c * (N3 / 3) + cc];
+  };
+  // E group forward: rows (e, a, c^), cols (Er, Et^, Ez)
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      at(P.PE, 0, j, 2, k) = Ui(j, k);
+      at(P.PE, 1, j, 1, k) = LiUi(j, k) * m / rho[k];
+      if (k >= 1) at(P.PE, 1, j, 0, k) = A_Er(j, k - 1);
+    }
+  for (int j = 0; j < n1; ++j)
+    for (int k = 0; k < n; ++k) {
+      at(P.PE, 2, j, 1, k) = C_Et(j, k);
+      if (k >= 1) at(P.PE, 2, j, 0, k) = MiPsii(j, k - 1) * m / rhom[k];
+    }
+  // B group forward: rows (b, d^, f^), cols (Bt, Br^, Bz^); same transverse map on w = (Bt, -Br^)
+  for (int r = 0; r < n; ++r)
+    for (int k = 0; k < n; ++k) {
+      at(P.PB, 0, r, 0, k) = at(P.PE, 1, r, 0, k);
+      at(P.PB, 0, r, 1, k) = -at(P.PE, 1, r, 1, k);
+      at(P.PB, 1, r, 0, k) = at(P.PE, 2, r, 0, k);
+      at(P.PB, 1, r, 1, k) = -at(P.PE, 2, r, 1, k);
+    }
+  for (int j = 0; j < n1; ++j)
+    for (int k = 1; k < n; ++k) at(P.PB, 2, j, 2, k) = Psii(j, k - 1);
+  // E group backward: rows (Er, Et^, Ez), cols (e, a, c^)
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j) {
+      at(P.QE, 2, k, 0, j) = U(k, j);
+      at(P.QE, 1, k, 1, j) = -(double)m / rho[k] * U(k, j);
+      if (k >= 1) at(P.QE, 0, k, 1, j) = GU(k - 1, j);
+    }
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n1; ++j) {
+      at(P.QE, 1, k, 2, j) = -DPsi(k, j);
+      if (k >= 1) at(P.QE, 0, k, 2, j) = (double)m / rhom[k] * Psi(k - 1, j);
+    }
+  if (m == 0) {
+    // radially uniform TE pair (curl- and divergence-free E_theta / B_rho component):
+    // h spans ker D_div^(-), l spans the left null space of D^(+) with the axis fill, l.h = 1.
+    std::vector<double> h(n, 0.0), l(n, 0.0), x, b(n1);
+    Mat A(n1, n1);
+    for (int i = 0; i < n1; ++i) {
+      for (int j = 0; j < n1; ++j) A(i, j) = DivM(i, j + 1);
+      b[i] = -DivM(i, 0);
+    }
+    if (solve(A, x, b) != 0) {
+      msg = "null vector of D_div^(-) not found";
+      return 4;
+    }
+    h[0] = 1.0;
+    for (int i = 0; i < n1; ++i) h[i + 1] = x[i];
+    for (int i = 0; i < n1; ++i) {
+      for (int j = 0; j < n1; ++j) A(i, j) = DpBz(j + 1, i);
+      b[i] = -DpBz(0, i);
+    }
+    if (solve(A, x, b) != 0) {
+      msg = "left null vector of D^(+) not found";
+      return 4;
+    }
+    l[0] = 1.0;
+    for (int i = 0; i < n1; ++i) l[i + 1] = x[i];
+    double lh = 0.0;
+    for (int i = 0; i < n; ++i) lh += l[i] * h[i];
+    for (int i = 0; i < n; ++i) {
+      at(P.PE, 2, n1, 1, i) = l[i] / lh;
+      at(P.QE, 1, i, 2, n1) = h[i];
+    }
+  }
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j) {
+      at(P.QB, 0, k, 0, j) = at(P.QE, 0, k, 1, j);
+      at(P.QB, 0, k, 1, j) = at(P.QE, 0, k, 2, j);
+      at(P.QB, 1, k, 0, j) = -at(P.QE, 1, k, 1, j);
+      at(P.QB, 1, k, 1, j) = -at(P.QE, 1, k, 2, j);
+    }
+  for (int r = 0; r < n; ++r)
+    for (int k = 0; k < n; ++k) at(P.PB, 1, r, 1, k) = -at(P.PE, 2, r, 1, k);  // includes -l^T row
+  for (int k = 1; k < n; ++k)
+    for (int j = 0; j < n1; ++j) at(P.QB, 2, k, 2, j) = Psi(k - 1, j);
+  // axis rows (Sec. 2.4): slot 0 of the staggered-grid fields from their interior slots
+  for (int col = 0; col < N3; ++col) {
+    double se = 0, sb = 0, sz = 0;
+    for (int k = 1; k <= ND && k < n; ++k) {
+      se += w_polar[k - 1] * P.QE[(size_t)k * N3 + col];
+      sb += w_polar[k - 1] * P.QB[(size_t)k * N3 + col];
+      sz += w_scalar[k - 1] * P.QB[(size_t)(2 * n + k) * N3 + col];
+    }
+    P.QE[(size_t)0 * N3 + col] = se;
+    P.QB[(size_t)0 * N3 + col] = sb;
+    P.QB[(size_t)(2 * n) * N3 + col] = sz;
+  }
+  return 0;
+}
+
+int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
+                    double dr, double dt, std::string& msg) {
+  if (order < 2 || order > 32 || (order & 1)) {
+    msg = "order must be even, 2..32";
+    return 1;
+  }
+  if (Nr < order / 2 + 2 || Nz < 2 || nmodes < 1 || !(dz > 0) || !(dr > 0) || !(dt > 0)) {
+    msg = "invalid sizes or spacings";
+    return 1;
+  }
+  hp.Nz = Nz;
+  hp.Nr = Nr;
+  hp.order = order;
+  hp.dz = dz;
+  hp.dr = dr;
+  hp.dt = dt;
+  hp.modes.assign(modes, modes + nmodes);
+  hp.mp.resize(nmodes);
+  for (int i = 0; i < nmodes; ++i) {
+    if (modes[i] < 0 || modes[i] > 64) {
+      msg = "mode numbers must be 0..64";
+      return 1;
+    }
+    int rc = build_mode(hp.mp[i], Nr, order, dr, modes[i], msg);
+    if (rc) return rc;
+  }
+  // z symbols of the periodic staggered stencil: s+ = i kappa e^{+i th/2}, s- = i kappa e^{-i th/2},
+  // kappa = (2/dz) sum_n c_n sin((2n-1) th / 2), th = 2 pi q / Nz.
+  const std::vector<double> c = staggered_coeffs(order);
+  hp.sp_re.resize(Nz);
+  hp.sp_im.resize(Nz);
+  hp.sm_re.resize(Nz);
+  hp.sm_im.resize(Nz);
+  hp.kappa2.resize(Nz);
+  const double pi = 3.14159265358979323846;
+  for (int q = 0; q < Nz; ++q) {
+    double kap = 0.0;
+    for (int t = 1; t <= (int)c.size(); ++t) {
+      const long long num = ((long long)q * (2 * t - 1)) % (2LL * Nz);  // angle = pi * num / Nz
+      kap += c[t - 1] * std::sin(pi * (double)num / Nz);
+    }
+    kap *= 2.0 / dz;
+    const double half = pi * (double)q / Nz;
+    const double ch = std::cos(half), sh = std::sin(half);
+    hp.kappa2[q] = kap * kap;
+    hp.sp_re[q] = -kap * sh;
+    hp.sp_im[q] = kap * ch;
+    hp.sm_re[q] = kap * sh;
+    hp.sm_im[q] = kap * ch;
+  }
+  return 0;
+}
+
+}  // namespace fdetd

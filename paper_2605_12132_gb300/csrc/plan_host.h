@@ -1,0 +1,59 @@
+// Host-side (FP64) plan construction for the exact exponential field step.
+//
+// For every azimuthal mode m the discrete operator of Sec. 2.5 (Eqs.
+// spatialAM_maxwell_Er ... _Bz) separates, after a DFT along periodic z, into
+// two radial families per kz:
+//   TM: (E_z, grad part of E_perp, grad part of w)   with w = (B_theta, -B_rho)
+//   TE: (curl part of E_perp, curl part of w, B_z)
+// Each family is diagonalised by one kz-independent real radial basis
+// (eigenvectors of L0 = D_div^(+) D^(-) - m^2/rho^2 on the primary grid and of
+// L2 = D_div^(-) D^(+) - m^2/rho_-^2 on the staggered grid), leaving a 3x3 block
+// per (kz, j) with eigenvalues {0, +-i omega}, omega^2 = kappa(kz)^2 + lambda_j.
+// The radial divergence/curl stencils are folded into dense projection (P) and
+// back-projection (Q) matrices; the axis rule of Sec. 2.4 is folded into Q's
+// axis rows.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace fdetd {
+
+// Coefficient closed forms (Sec. 2.3): staggered first derivative of order 2N,
+// centred first and second derivatives, axis extrapolation of Sec. 2.4.
+std::vector<double> staggered_coeffs(int order);
+std::vector<double> centred_d1_coeffs(int order);
+std::vector<double> centred_d2_coeffs(int order, double* e0);
+std::vector<double> axis_coeffs(int N);
+
+// Per-mode radial tables.  All matrices are row-major (3n x 3n), n = Nr.
+//  Field blocks (columns of P, rows of Q), E group: (Er, Et^, Ez); B group: (Bt, Br^, Bz^)
+//  Coefficient blocks, E group: (e, a, c^); B group: (b, d^, f^).
+//  ^ marks the rotated variable tau*F with tau = i*sigma = -i (sigma = -1 mode sign),
+//  which makes every radial matrix real.
+struct ModePlan {
+  int m = 0, n = 0;
+  std::vector<double> lam, mu;          // n each; lam = TM eigenvalues, mu = TE (slot n-1 special)
+  std::vector<uint8_t> tm_live, te_live;  // 1 where the 3x3 rotation applies, 0 = identity
+  std::vector<double> PE, PB, QE, QB;   // (3n)^2 each
+  double max_imag = 0.0;                // largest |Im| met in the eigen-solves
+};
+
+struct HostPlan {
+  int Nz = 0, Nr = 0, order = 0;
+  double dz = 0, dr = 0, dt = 0;
+  std::vector<int> modes;
+  std::vector<ModePlan> mp;
+  std::vector<double> sp_re, sp_im, sm_re, sm_im, kappa2;  // z symbols, Nz each
+};
+
+// Builds the full host plan.  Returns 0 on success; nonzero with msg set otherwise
+// (1 = bad argument, 4 = eigen-solve failure).
+int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
+                    double dr, double dt, std::string& msg);
+
+// Phase coefficients of exp(t M) = I + A1 M + A2 M^2 for a 3x3 block with eigenvalues {0, +-i w}:
+// A1 = sin(w t)/w, A2 = (1 - cos(w t))/w^2 (limits at w = 0).
+void phase_coeffs(double w, double t, double* A1, double* A2);
+
+}  // namespace fdetd

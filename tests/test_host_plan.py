@@ -1,0 +1,135 @@
+"""Host-side checks of the C-ABI library (no GPU): symbol exports, stencil coefficients and the
+FP64 plan tables (radial eigenbases folded into projection matrices) against the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import maxwell as mx
+from oracle import stencils as st
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+native = pytest.importorskip("paper_2605_12132_gb300._native")
+
+
+def _lib_or_skip():
+    try:
+        return native.lib()
+    except native.FdetdError as e:
+        pytest.skip(str(e))
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib_or_skip()
+    hdr = open(os.path.join(ROOT, "include", "fdetd.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"^\s*(?:int|size_t)\s+(\w+)\s*\(", hdr, flags=re.M))
+    assert {"fdetd_plan", "fdetd_step", "envelope_step", "envelope_plan"} <= names
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
+        assert ctypes.cast(getattr(L, nm), ctypes.c_void_p).value
+
+
+@pytest.mark.parametrize("order", [2, 4, 8, 16, 24, 32])
+def test_host_coefficients_match_oracle(order):
+    _lib_or_skip()
+    np.testing.assert_allclose(native.fdetd_host_coeffs(0, order), st.staggered_coeffs(order), rtol=2e-16, atol=0)
+    np.testing.assert_allclose(native.fdetd_host_coeffs(1, order), st.centred_d1_coeffs(order), rtol=2e-16, atol=0)
+    e0, e = st.centred_d2_coeffs(order)
+    np.testing.assert_allclose(native.fdetd_host_coeffs(2, order), np.concatenate([[e0], e]), rtol=4e-16, atol=0)
+    np.testing.assert_allclose(native.fdetd_host_coeffs(3, order), st.axis_coeffs(order // 2), rtol=2e-16, atol=0)
+
+
+TAU = -1j
+
+
+def _phase(w, t):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        A1 = np.where(w * t > 1e-3, np.sin(w * t) / w, t * (1 - (w * t) ** 2 / 6))
+        A2 = np.where(w * t > 1e-3, 2 * np.sin(w * t / 2) ** 2 / w ** 2, t * t / 2 * (1 - (w * t) ** 2 / 12))
+    return A1, A2
+
+
+def factorised_step(F, J, T, dt, nsteps):
+    """The factorised exact step, written with the exported host tables (what the kernels compute)."""
+    n = F.shape[2]
+    G = F.copy()
+    for f in (1, 3, 5):
+        G[f] = TAU * G[f]
+    JJ = J.copy()
+    JJ[1] = TAU * JJ[1]
+    sp, sm, k2 = T["sp"][:, None], T["sm"][:, None], T["kappa2"][:, None]
+    for _ in range(nsteps):
+        cE = np.concatenate([G[0], G[1], G[2]], axis=1) @ T["PE"].T
+        cB = np.concatenate([G[4], G[3], G[5]], axis=1) @ T["PB"].T
+        cJ = np.concatenate([JJ[0], JJ[1], JJ[2]], axis=1) @ T["PE"].T
+        cE, cB, cJ = (np.fft.fft(c, axis=0) for c in (cE, cB, cJ))
+        e, a, c = cE[:, :n], cE[:, n:2 * n], cE[:, 2 * n:]
+        b, d, f = cB[:, :n], cB[:, n:2 * n], cB[:, 2 * n:]
+        eJ, aJ, cJ_ = cJ[:, :n], cJ[:, n:2 * n], cJ[:, 2 * n:]
+        lam = T["lam"][None, :]
+        w = np.sqrt(k2 + lam)
+        A1, A2 = _phase(w, dt)
+        B1, B2 = _phase(w, dt / 2)
+        live = T["tm_live"][None, :] > 0
+        A1, A2, B1, B2 = (np.where(live, x, 0) for x in (A1, A2, B1, B2))
+        Mtm = lambda x: (-lam * x[2], -sp * x[2], x[0] - sm * x[1])
+
+        def upd(x, xJ, M):
+            y, z, yJ, zJ = M(x), M(M(x)), M(xJ), M(M(xJ))
+            return tuple(x[i] + A1 * y[i] + A2 * z[i] - dt * (xJ[i] + B1 * yJ[i] + B2 * zJ[i]) for i in range(3))
+
+        e, a, b = upd((e, a, b), (eJ, aJ, 0 * eJ), Mtm)
+        mu = T["mu"][None, :]
+        w = np.sqrt(k2 + mu)
+        A1, A2 = _phase(w, dt)
+        B1, B2 = _phase(w, dt / 2)
+        live = T["te_live"][None, :] > 0
+        A1, A2, B1, B2 = (np.where(live, x, 0) for x in (A1, A2, B1, B2))
+        Mte = lambda x: (-sp * x[1] + x[2], -sm * x[0], -mu * x[0])
+        c, d, f = upd((c, d, f), (cJ_, 0 * cJ_, 0 * cJ_), Mte)
+        XE = np.fft.ifft(np.concatenate([e, a, c], axis=1), axis=0) @ T["QE"].T
+        XB = np.fft.ifft(np.concatenate([b, d, f], axis=1), axis=0) @ T["QB"].T
+        G = np.zeros_like(G)
+        G[0], G[1], G[2] = XE[:, :n], XE[:, n:2 * n], XE[:, 2 * n:]
+        G[4], G[3], G[5] = XB[:, :n], XB[:, n:2 * n], XB[:, 2 * n:]
+    for f in (1, 3, 5):
+        G[f] = G[f] / TAU
+    return G
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+@pytest.mark.parametrize("order", [4, 8])
+def test_host_tables_reproduce_oracle_step(m, order):
+    _lib_or_skip()
+    rng = np.random.default_rng(20 + m + order)
+    Nz, Nr, dz, dr, dt = 16, 13, 1 / 16, 1 / 4, 1 / 16
+    F = rng.standard_normal((6, Nz, Nr)) + 1j * rng.standard_normal((6, Nz, Nr))
+    J = rng.standard_normal((3, Nz, Nr)) + 1j * rng.standard_normal((3, Nz, Nr))
+    T = native.fdetd_host_tables(Nz, Nr, m, order, dz, dr, dt)
+    got = factorised_step(F, J, T, dt, 3)
+    ref = mx.step_spectral(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=3)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_host_tables_full_size_structure():
+    # order 16, Nr = 256 (the 2048 x 256 workload): real spectra, bounded tables
+    _lib_or_skip()
+    for m in (0, 1):
+        T = native.fdetd_host_tables(64, 256, m, 16, 1 / 16, 1 / 4, 1 / 16)
+        assert (T["lam"] >= 0).all() and (T["mu"] >= 0).all()
+        assert T["tm_live"].sum() == 256 - (m == 0)
+        assert T["te_live"].sum() == 255 + (m == 0)
+        for k in ("PE", "PB", "QE", "QB"):
+            assert np.isfinite(T[k]).all() and np.abs(T[k]).max() < 100
+
+
+def test_plan_errors_are_reported():
+    _lib_or_skip()
+    with pytest.raises(native.FdetdError, match="order"):
+        native.fdetd_host_tables(16, 8, 0, 7, 0.1, 0.1, 0.1)
+    with pytest.raises(native.FdetdError):
+        native.fdetd_host_tables(16, 3, 0, 8, 0.1, 0.1, 0.1)
