@@ -43,11 +43,11 @@ template <typename K, typename C> __device__ __forceinline__ C ccoef(K re, K im,
 
 // Phase record per (family, j, q): exp(t M) = I + A1 M + A2 M^2 at t = dt (A) and dt/2 (B).
 struct PhaseD { double A1, A2, B1, B2; };
-struct PhaseF { df A1, A2; float B1, B2, pad0, pad1; };
+struct PhaseF { df A1, A2; };  // B1, B2 follow from A1, A2 (half-angle identities) in the kernel
 
-// z symbols per q: s+ and s- (complex), kappa^2
-struct ZSymD { double spr, spi, smr, smi, k2, pad0, pad1, pad2; };
-struct ZSymF { df spr, spi, smr, smi, k2; float pad0, pad1; };
+// z symbol per q: s+ = i kappa e^{+i th/2} (complex); s- = i kappa e^{-i th/2} = (-Re s+, Im s+)
+struct ZSymD { double spr, spi; };
+struct ZSymF { df spr, spi; };
 
 __device__ __forceinline__ unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
 

@@ -38,6 +38,7 @@ struct fdetd_plan_s {
   void* d_lam = nullptr;
   void* d_tw = nullptr;
   void* d_coef = nullptr;
+  int* d_err = nullptr;      // device-side failure code (bounded waits that expired)
   void* d_hostio = nullptr;  // staging for fdetd_step_host (lazy)
   size_t hostio_bytes = 0;
   TcPlan* tc = nullptr;
@@ -78,7 +79,7 @@ static void prof_collect(fdetd_plan_s* p) {
 static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
-  void* ptrs[] = {p->d_P, p->d_Q, p->d_phase, p->d_zsym, p->d_lam, p->d_tw, p->d_coef, p->d_hostio};
+  void* ptrs[] = {p->d_P, p->d_Q, p->d_phase, p->d_zsym, p->d_lam, p->d_tw, p->d_coef, p->d_hostio, p->d_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -125,7 +126,12 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   const int n = Nr, N3 = 3 * Nr;
   const bool fp64 = precision == FDETD_PREC_FP64;
   const bool tc = precision == FDETD_PREC_BF16X3 || precision == FDETD_PREC_BF16X6;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)&p->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    plan_free(p);
+    return fail(FDETD_ERR_CUDA, std::string("plan: ") + cudaGetErrorString(e));
+  }
 
   // projection matrices: [nmodes][2][3n][3n]
   std::vector<double> P((size_t)nmodes * 2 * N3 * N3), Q(P.size());
@@ -138,7 +144,7 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   }
   if (tc) {
     char m2[256] = {0};
-    e = tc_create(&p->tc, Nz, n, nmodes, precision == FDETD_PREC_BF16X3 ? 2 : 3, P.data(), Q.data(), m2,
+    e = tc_create(&p->tc, Nz, n, nmodes, precision == FDETD_PREC_BF16X3 ? 2 : 3, P.data(), Q.data(), p->d_err, m2,
                   sizeof(m2));
     if (e != cudaSuccess) {
       plan_free(p);
@@ -184,9 +190,6 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
               PhaseF f;
               f.A1 = to_df(A1);
               f.A2 = to_df(A2);
-              f.B1 = (float)B1;
-              f.B2 = (float)B2;
-              f.pad0 = f.pad1 = 0.f;
               phf[k] = f;
             }
           }
@@ -201,14 +204,10 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     std::vector<ZSymD> zd(Nz);
     std::vector<ZSymF> zf(Nz);
     for (int q = 0; q < Nz; ++q) {
-      zd[q] = ZSymD{hp.sp_re[q], hp.sp_im[q], hp.sm_re[q], hp.sm_im[q], hp.kappa2[q], 0, 0, 0};
+      zd[q] = ZSymD{hp.sp_re[q], hp.sp_im[q]};
       ZSymF f;
       f.spr = to_df(hp.sp_re[q]);
       f.spi = to_df(hp.sp_im[q]);
-      f.smr = to_df(hp.sm_re[q]);
-      f.smi = to_df(hp.sm_im[q]);
-      f.k2 = to_df(hp.kappa2[q]);
-      f.pad0 = f.pad1 = 0.f;
       zf[q] = f;
     }
     if (fp64) {
@@ -217,9 +216,9 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
       if ((e = upload(&p->d_zsym, zf.data(), Nz * sizeof(ZSymF), p->bytes)) != cudaSuccess) goto cuda_fail;
     }
     const double pi = 3.14159265358979323846;
-    std::vector<double> twd(Nz);
-    std::vector<float> twf(Nz);
-    for (int k = 0; k < Nz / 2; ++k) {
+    std::vector<double> twd(2 * Nz);
+    std::vector<float> twf(2 * Nz);
+    for (int k = 0; k < Nz; ++k) {
       const double ang = -2.0 * pi * (double)k / Nz;
       twd[2 * k] = std::cos(ang);
       twd[2 * k + 1] = std::sin(ang);
@@ -227,9 +226,9 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
       twf[2 * k + 1] = (float)twd[2 * k + 1];
     }
     if (fp64) {
-      if ((e = upload(&p->d_tw, twd.data(), Nz * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
+      if ((e = upload(&p->d_tw, twd.data(), 2 * Nz * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
     } else {
-      if ((e = upload(&p->d_tw, twf.data(), Nz * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
+      if ((e = upload(&p->d_tw, twf.data(), 2 * Nz * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
     }
     const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
     if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
@@ -267,6 +266,7 @@ extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nstep
   sa.split_out = p->tc ? tc_split_buffer(p->tc) : nullptr;
   sa.npieces = p->precision == FDETD_PREC_BF16X3 ? 2 : 3;
   sa.split_rows = p->tc ? tc_split_rows(p->tc) : 0;
+  sa.err = p->d_err;
   sa.Nz = p->Nz;
   sa.logNz = p->logNz;
   sa.n = p->Nr;
@@ -337,14 +337,12 @@ extern "C" int fdetd_plan_status(fdetd_plan_t p, void* stream) {
   if (!p) return fail(FDETD_ERR_ARG, "plan is null");
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
-  if (p->tc) {
-    int flag = 0;
-    e = cudaMemcpy(&flag, tc_error_flag(p->tc), sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
-    if (flag) {
-      cudaMemset(tc_error_flag(p->tc), 0, sizeof(int));
-      return fail(FDETD_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (stage code " + std::to_string(flag) + ")");
-    }
+  int flag = 0;
+  e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
+  if (flag) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return fail(FDETD_ERR_TIMEOUT, "a kernel's bounded wait expired (stage code " + std::to_string(flag) + ")");
   }
   return FDETD_OK;
 }

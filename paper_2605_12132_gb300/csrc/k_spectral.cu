@@ -14,9 +14,11 @@
 // Ampere equations only).  s+/s- are the DFT symbols of the periodic staggered
 // z stencil D_z^(+/-) (Eq. spatial_derivativeSt along z).
 //
-// The z transform is an in-shared-memory radix-2 FFT (decimation in time after a
-// bit-reversed load, decimation in frequency for the inverse), all arrays of the
-// family advancing through each stage together.
+// The z transform is a mixed-radix Stockham FFT in shared memory: each pass loads
+// every butterfly of every array of the family into registers, twiddles and
+// transforms it there (radix 8 for FP32, radix 4 for FP64, one radix-2/4 pass
+// first when log2 Nz is not a multiple), and writes it back in place after one
+// barrier.  The rotation runs between the forward and inverse transforms.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -49,16 +51,58 @@ __device__ __forceinline__ void apply_te(const C& c, const C& d, const C& f, C& 
 }
 
 __device__ __forceinline__ void phase_unpack(const PhaseD& p, double& A1, double& A2, double& B1, double& B2) {
-  A1 = p.A1; A2 = p.A2; B1 = p.B1; B2 = p.B2;
+  A1 = p.A1;
+  A2 = p.A2;
+  B1 = p.B1;
+  B2 = p.B2;
 }
+// FP32 record holds A1, A2 as double-float; the half-step pair follows from half-angle identities:
+// sin(th/2) = w sqrt(A2/2) -> B1 = sqrt(A2/2);  cos(th/2) = A1 / (2 B1);  B2 = B1^2 / (1 + cos(th/2)).
 __device__ __forceinline__ void phase_unpack(const PhaseF& p, df& A1, df& A2, float& B1, float& B2) {
-  A1 = p.A1; A2 = p.A2; B1 = p.B1; B2 = p.B2;
+  A1 = p.A1;
+  A2 = p.A2;
+  const float a2 = p.A2.h + p.A2.l;
+  B1 = sqrtf(0.5f * fmaxf(a2, 0.f));
+  const float c = B1 > 0.f ? (p.A1.h + p.A1.l) / (2.f * B1) : 1.f;
+  B2 = B1 > 0.f ? B1 * B1 / (1.f + c) : 0.f;
 }
+// s- = (-Re s+, Im s+)
 __device__ __forceinline__ void zsym_unpack(const ZSymD& z, double& spr, double& spi, double& smr, double& smi) {
-  spr = z.spr; spi = z.spi; smr = z.smr; smi = z.smi;
+  spr = z.spr;
+  spi = z.spi;
+  smr = -z.spr;
+  smi = z.spi;
 }
 __device__ __forceinline__ void zsym_unpack(const ZSymF& z, df& spr, df& spi, df& smr, df& smi) {
-  spr = z.spr; spi = z.spi; smr = z.smr; smi = z.smi;
+  spr = z.spr;
+  spi = z.spi;
+  smr.h = -z.spr.h;
+  smr.l = -z.spr.l;
+  smi = z.spi;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// bulk asynchronous copy of `bytes` (multiple of 16) from global to shared, completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"((uint64_t)src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  for (long it = 0; it < (1L << 26); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 template <typename C, typename Kc, typename Tb>
@@ -73,13 +117,128 @@ __device__ __forceinline__ C combine(C x, C y, C z, Kc A1, Kc A2, C xJ, C yJ, C 
   return r;
 }
 
+// multiply by -i (forward) / +i (inverse)
+template <bool INV, typename C>
+__device__ __forceinline__ C rot90(C a) {
+  C r;
+  if (INV) {
+    r.x = -a.y;
+    r.y = a.x;
+  } else {
+    r.x = a.y;
+    r.y = -a.x;
+  }
+  return r;
+}
+
+// In-register DFT of RR points, natural order in and out (W = exp(-+2 pi i / RR)).
+template <int RR, bool INV, typename C>
+__device__ __forceinline__ void dft_small(C* v) {
+  if (RR == 2) {
+    const C t = v[1];
+    v[1] = csub(v[0], t);
+    v[0] = cadd(v[0], t);
+  } else if (RR == 4) {
+    const C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), a2 = cadd(v[1], v[3]);
+    const C a3 = rot90<INV>(csub(v[1], v[3]));
+    v[0] = cadd(a0, a2);
+    v[2] = csub(a0, a2);
+    v[1] = cadd(a1, a3);
+    v[3] = csub(a1, a3);
+  } else {  // 8: two 4-point DFTs (even / odd samples) and one radix-2 stage
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft_small<4, INV>(e);
+    dft_small<4, INV>(o);
+    typedef decltype(e[0].x) R;
+    const R h = (R)0.70710678118654752440;
+    C w1, w3;  // W8^1, W8^3 (forward), conjugates for the inverse
+    w1.x = h;
+    w1.y = INV ? h : -h;
+    w3.x = -h;
+    w3.y = INV ? h : -h;
+    const C t0 = o[0], t1 = cmul(w1, o[1]), t2 = rot90<INV>(o[2]), t3 = cmul(w3, o[3]);
+    v[0] = cadd(e[0], t0);
+    v[4] = csub(e[0], t0);
+    v[1] = cadd(e[1], t1);
+    v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2);
+    v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3);
+    v[7] = csub(e[3], t3);
+  }
+}
+
+// One in-place Stockham pass of radix RR over narr arrays of length N stored back to back
+// (sub-sequence length Ns before the pass).  MAXB bounds the butterflies per thread.
+template <int RR, bool INV, int NT, int MAXB, typename C>
+__device__ __forceinline__ void stockham_pass(C* s, int narr, int N, int Ns, const C* tw) {
+  const int nbf = N / RR;
+  const int total = narr * nbf;
+  const int stride = N / (Ns * RR);
+  C v[MAXB][RR];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int a = b / nbf, j = b - a * nbf;
+      const C* x = s + (size_t)a * N;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) v[i][r] = x[j + r * nbf];
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < RR; ++r) {
+          const C w = tw[(r * k) * stride];
+          v[i][r] = INV ? cmulconj(v[i][r], w) : cmul(v[i][r], w);
+        }
+      }
+      dft_small<RR, INV>(v[i]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int a = b / nbf, j = b - a * nbf;
+      const int k = j & (Ns - 1);
+      C* x = s + (size_t)a * N + (j - k) * RR + k;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) x[r * Ns] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full FFT of narr arrays (forward or inverse, unnormalised): one small-radix pass first
+// when log2 N is not a multiple of log2 R, then radix-R passes.
+template <int R, bool INV, int NT, int MAXB, typename C>
+__device__ void fft_all(C* s, int narr, int N, int logN, const C* tw) {
+  const int lr = R == 8 ? 3 : 2;
+  int Ns = 1;
+  const int rem = logN % lr;
+  if (rem == 1) {
+    stockham_pass<2, INV, NT, MAXB * (R / 2)>(s, narr, N, Ns, tw);
+    Ns *= 2;
+  } else if (rem == 2) {
+    stockham_pass<4, INV, NT, MAXB * (R / 4)>(s, narr, N, Ns, tw);
+    Ns *= 4;
+  }
+  for (int p = 0; p < logN / lr; ++p) {
+    stockham_pass<R, INV, NT, MAXB>(s, narr, N, Ns, tw);
+    Ns *= R;
+  }
+}
+
 }  // namespace
 
-// T: data real type; K: coefficient type (double or df); PH / ZS: table records.
-template <typename T, typename K, typename PH, typename ZS, bool SPLIT_OUT>
-__global__ void __launch_bounds__(256) spectral_kernel(SpectralArgs args) {
+// T: data real type; K: coefficient type (double or df); PH / ZS: table records;
+// R: FFT radix; NT: threads; MAXB: radix-R butterflies per thread per pass.
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, int MAXB, bool SPLIT_OUT>
+__global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs args) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t load_bar;
   C* s = reinterpret_cast<C*>(smem_raw);
   const int Nz = args.Nz, L = args.logNz, n = args.n;
   const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
@@ -96,38 +255,38 @@ __global__ void __launch_bounds__(256) spectral_kernel(SpectralArgs args) {
   }
   const C* coef = reinterpret_cast<const C*>(args.coef);
   const C* tw = reinterpret_cast<const C*>(args.twiddle);
-  for (int a = 0; a < narr; ++a) {
-    const C* src = coef + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
-    C* dst = s + (size_t)a * Nz;
-    for (int z = threadIdx.x; z < Nz; z += blockDim.x) dst[bitrev(z, L)] = src[z];
+  // the family's coefficient columns and its phase column are contiguous in global memory:
+  // one bulk copy each into shared memory, completing on one mbarrier
+  PH* phase = reinterpret_cast<PH*>(s + (size_t)narr * Nz);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&load_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const uint32_t col = (uint32_t)(Nz * sizeof(C)), pcol = (uint32_t)(Nz * sizeof(PH));
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                     smem_addr(&load_bar)),
+                 "r"(narr * col + pcol)
+                 : "memory");
+    for (int a = 0; a < narr; ++a)
+      bulk_g2s(s + (size_t)a * Nz, coef + ((size_t)(md * 9 + idx[a]) * n + j) * Nz, col, &load_bar);
+    bulk_g2s(phase, reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz, pcol,
+             &load_bar);
   }
   __syncthreads();
-  const int half_total = Nz >> 1;
-  for (int st = 0; st < L; ++st) {
-    const int half = 1 << st;
-    for (int b = threadIdx.x; b < narr * half_total; b += blockDim.x) {
-      const int a = b / half_total, bb = b - a * half_total;
-      const int grp = bb >> st, pos = bb & (half - 1);
-      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-      C* x = s + (size_t)a * Nz;
-      const C w = tw[pos << (L - 1 - st)];
-      const C t = cmul(w, x[i1]);
-      const C u = x[i0];
-      x[i0] = cadd(u, t);
-      x[i1] = csub(u, t);
-    }
-    __syncthreads();
+  if (!bar_wait(&load_bar, 0)) {
+    if (threadIdx.x == 0 && args.err) atomicCAS(args.err, 0, 8);
+    return;
   }
-  // exact rotation per kz
-  const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
+  fft_all<R, false, NT, MAXB>(s, narr, Nz, L, tw);
+  // exact rotation per kz (the 1/Nz of the inverse transform folded in)
   const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
   const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
   const T dt = (T)args.dt;
-  for (int q = threadIdx.x; q < Nz; q += blockDim.x) {
+  const T inv = (T)1 / (T)Nz;
+  for (int q = threadIdx.x; q < Nz; q += NT) {
     K spr, spi, smr, smi, A1, A2;
     T B1, B2;
     zsym_unpack(zs[q], spr, spi, smr, smi);
-    phase_unpack(phase[q], A1, A2, B1, B2);
+    phase_unpack(phase[q], A1, A2, B1, B2);  // from shared memory
     C x0 = s[q], x1 = s[Nz + q], x2 = s[2 * Nz + q];
     C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
     if (hasJ) {
@@ -146,71 +305,70 @@ __global__ void __launch_bounds__(256) spectral_kernel(SpectralArgs args) {
       apply_te(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
       apply_te(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
     }
-    s[q] = combine(x0, y0, z0, A1, A2, j0, yj0, zj0, B1, B2, dt, hasJ);
-    s[Nz + q] = combine(x1, y1, z1, A1, A2, j1, yj1, zj1, B1, B2, dt, hasJ);
-    s[2 * Nz + q] = combine(x2, y2, z2, A1, A2, j2, yj2, zj2, B1, B2, dt, hasJ);
+    C r0 = combine(x0, y0, z0, A1, A2, j0, yj0, zj0, B1, B2, dt, hasJ);
+    C r1 = combine(x1, y1, z1, A1, A2, j1, yj1, zj1, B1, B2, dt, hasJ);
+    C r2 = combine(x2, y2, z2, A1, A2, j2, yj2, zj2, B1, B2, dt, hasJ);
+    r0.x *= inv; r0.y *= inv;
+    r1.x *= inv; r1.y *= inv;
+    r2.x *= inv; r2.y *= inv;
+    s[q] = r0;
+    s[Nz + q] = r1;
+    s[2 * Nz + q] = r2;
   }
   __syncthreads();
-  for (int st = L - 1; st >= 0; --st) {
-    const int half = 1 << st;
-    for (int b = threadIdx.x; b < 3 * half_total; b += blockDim.x) {
-      const int a = b / half_total, bb = b - a * half_total;
-      const int grp = bb >> st, pos = bb & (half - 1);
-      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-      C* x = s + (size_t)a * Nz;
-      const C w = tw[pos << (L - 1 - st)];
-      const C u = x[i0], v = x[i1];
-      x[i0] = cadd(u, v);
-      x[i1] = cmulconj(csub(u, v), w);
-    }
-    __syncthreads();
-  }
-  const T inv = (T)1 / (T)Nz;
+  fft_all<R, true, NT, MAXB>(s, 3, Nz, L, tw);
   if (!SPLIT_OUT) {
     C* out = reinterpret_cast<C*>(args.coef);
     for (int a = 0; a < 3; ++a) {
       C* dst = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
       const C* x = s + (size_t)a * Nz;
-      for (int z = threadIdx.x; z < Nz; z += blockDim.x) {
-        C v = x[bitrev(z, L)];
-        v.x *= inv;
-        v.y *= inv;
-        dst[z] = v;
-      }
+      for (int z = threadIdx.x; z < Nz; z += NT) dst[z] = x[z];
     }
   } else {
-    // bf16 split pieces for the tensor-core back-projection: [md][piece][6][n][Nz*2] (re, im interleaved)
+    // bf16 split pieces for the tensor-core back-projection (re, im interleaved along z)
     for (int a = 0; a < 3; ++a) {
       const C* x = s + (size_t)a * Nz;
-      for (int z = threadIdx.x; z < Nz; z += blockDim.x) {
-        C v = x[bitrev(z, L)];
-        const float vr = (float)(v.x * inv), vi = (float)(v.y * inv);
-        split_store(args.split_out, args.npieces, md, idx[a], j, z, args.split_rows, Nz, vr, vi);
+      for (int z = threadIdx.x; z < Nz; z += NT) {
+        const C v = x[z];
+        split_store(args.split_out, args.npieces, md, idx[a], j, z, args.split_rows, Nz, (float)v.x, (float)v.y);
       }
     }
   }
 }
 
-template <typename T, typename K, typename PH, typename ZS, bool SPLIT>
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
-  const size_t smem = (size_t)(a.hasJ ? 5 : 3) * a.Nz * sizeof(C);
-  auto k = spectral_kernel<T, K, PH, ZS, SPLIT>;
+  constexpr int MAXB = 5;  // radix-R butterflies per thread per pass (5 arrays, NT >= Nz / R)
+  const size_t smem = spectral_smem_bytes(a.Nz, sizeof(T) == 8 ? 0 : 1, a.hasJ);
+  auto k = spectral_kernel<T, K, PH, ZS, R, NT, MAXB, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.n, 2, nmodes);
-  k<<<grid, 256, smem, st>>>(a);
+  k<<<grid, NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st) {
-  if (precision == 0) return launch_one<double, double, PhaseD, ZSymD, false>(a, nmodes, st);
-  if (split_out) return launch_one<float, df, PhaseF, ZSymF, true>(a, nmodes, st);
-  return launch_one<float, df, PhaseF, ZSymF, false>(a, nmodes, st);
+// Threads per block: NT = max(128, 5 Nz / (R * MAXB)) with MAXB = 5 butterflies per thread.
+template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT>
+static cudaError_t launch_sized(const SpectralArgs& a, int nmodes, cudaStream_t st) {
+  const int need = a.Nz / R;  // threads for MAXB = 5 with 5 arrays
+  if (need <= 128) return launch_one<T, K, PH, ZS, R, 128, SPLIT>(a, nmodes, st);
+  if (need <= 256) return launch_one<T, K, PH, ZS, R, 256, SPLIT>(a, nmodes, st);
+  if (need <= 512) return launch_one<T, K, PH, ZS, R, 512, SPLIT>(a, nmodes, st);
+  return cudaErrorNotSupported;  // plans reject such Nz (shared-memory capacity)
 }
 
+cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st) {
+  if (precision == 0) return launch_sized<double, double, PhaseD, ZSymD, 4, false>(a, nmodes, st);
+  if (split_out) return launch_sized<float, df, PhaseF, ZSymF, 8, true>(a, nmodes, st);
+  return launch_sized<float, df, PhaseF, ZSymF, 8, false>(a, nmodes, st);
+}
+
+// coefficient columns of the family (5 with a current, else 3) plus its phase column
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ) {
-  return (size_t)(hasJ ? 5 : 3) * Nz * (precision == 0 ? 16 : 8);
+  return (size_t)(hasJ ? 5 : 3) * Nz * (precision == 0 ? 16 : 8) +
+         (size_t)Nz * (precision == 0 ? sizeof(PhaseD) : sizeof(PhaseF));
 }
 
 }  // namespace fdetd

@@ -7,14 +7,15 @@
 // significant bits per operand) and 6 for 3 pieces (BF16x6, ~24 bits).
 //
 // Projection  (per mode, group, output block):  D[(z,part), j] = sum_r X[(z,part), r] P[j, r]
-//   A = field rows (64 z x re/im, r contiguous), converted from FP32 complex to swizzled
-//       bf16 pieces by four producer warps (the rotated components tau*F are formed here);
-//   B = P pieces [j][r], K-major, loaded by TMA (128B swizzle);
-//   M = 128, N = 128, K = 64 per pipeline stage; D in TMEM (128 lanes x 128 fp32 columns).
+//   A = field rows (64 z x re/im, r contiguous): TMA stages the FP32 complex tile in shared
+//       memory, four converter warps split it into swizzled bf16 pieces (forming the rotated
+//       components tau*F on the way);
+//   B = P pieces [j][r], K-major, loaded by TMA (64B swizzle);
+//   M = 128, N = 256, K = 32 per pipeline stage; D in TMEM (128 lanes x 256 fp32 columns).
 // Back-projection (per mode, group, output field): D[r, (z,part)] = sum_j Q[r, j] C[j, (z,part)]
 //   A = Q pieces [r][j], K-major, TMA;  B = coefficient pieces [j][(z,part)], MN-major, TMA
 //   (written pre-split by the spectral kernel).
-// Warp roles: warps 0-3 produce (projection) and run the epilogue (TMEM -> registers ->
+// Warp roles: warps 0-3 convert (projection) and run the epilogue (TMEM -> registers ->
 // global); warp 4 issues TMA; warp 5 issues tcgen05.mma (one elected thread) and commits
 // to the stage's "empty" mbarrier.  Every mbarrier wait is bounded; on timeout the kernel
 // records an error code, drains its own MMAs and frees TMEM before returning.
@@ -119,7 +120,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 struct TcSmem {
-  uint64_t fullA[4], fullB[4], empty[4], done;
+  uint64_t fullA[4], fullB[4], fullS[4], empty[4], done;
   uint32_t tmem_base;
 };
 
@@ -163,15 +164,46 @@ struct TcBackArgs {
   int Nz, n, npad, kpad;
 };
 
+// Projection pipeline geometry: K tile of 32 (64-byte rows, 64B swizzle), N tile of 256.
+constexpr int PBK = 32, PBN = 256;
+constexpr uint32_t kPA = 128 * PBK * 2;      // one bf16 piece of the A tile (8 KB)
+constexpr uint32_t kPB = PBN * PBK * 2;      // one bf16 piece of the B tile (16 KB)
+constexpr uint32_t kPS = 64 * PBK * 8;       // FP32 complex staging tile: 64 z x 32 r (16 KB)
+
 template <int NP>
-__global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constant__ CUtensorMap tmP, TcProjArgs a) {
+struct PCfg {
+  static constexpr int S = NP == 2 ? 3 : 2;
+  static constexpr uint32_t kStage = kPS + NP * kPA + NP * kPB;
+  static constexpr size_t kSmem = (size_t)S * kStage + 1024 + sizeof(TcSmem) + 64;
+};
+
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void* p) {
+  // K-major, 64-byte rows, SWIZZLE_64B (4): 8-row groups 512 B apart
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16_n(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constant__ CUtensorMap tmP,
+                                                             const __grid_constant__ CUtensorMap tmF,
+                                                             const __grid_constant__ CUtensorMap tmJ,
+                                                             TcProjArgs a) {
   extern __shared__ __align__(1024) unsigned char raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
-  typedef Cfg<NP> C;
+  typedef PCfg<NP> C;
   TcSmem* sm = reinterpret_cast<TcSmem*>(base + C::S * C::kStage);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, Nz = a.Nz;
-  const int z0 = blockIdx.x * 64, j0 = blockIdx.y * BN;
+  const int z0 = blockIdx.x * 64, j0 = blockIdx.y * PBN;
   const int md = blockIdx.z / (3 * a.ngroups), rem = blockIdx.z % (3 * a.ngroups);
   const int g = rem / 3, ob = rem % 3;
   const int gp = (g == 1) ? 1 : 0;
@@ -185,8 +217,12 @@ __global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constan
     blist[1] = 1;
     nb = 2;
   }
-  const int ksteps = a.kpad / BK;
+  const int ksteps = a.kpad / PBK;
   const int T = nb * ksteps;
+  // stage layout: [staging FP32][A pieces][B pieces]
+  auto stage_S = [&](int s) { return base + s * C::kStage; };
+  auto stage_A = [&](int s) { return base + s * C::kStage + kPS; };
+  auto stage_B = [&](int s) { return base + s * C::kStage + kPS + NP * kPA; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::S; ++s) {
@@ -194,61 +230,75 @@ __global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constan
       mbar_init(&sm->fullB[s], 1);
       mbar_init(&sm->empty[s], 1);
     }
+    for (int s = 0; s < C::S; ++s) mbar_init(&sm->fullS[s], 1);
     mbar_init(&sm->done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
-                 "r"(BN));
+                 "r"(PBN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm->tmem_base;
-  bool ok = true;
 
   if (warp < 4) {
-    // ---- A producer: fields (FP32 complex) -> swizzled bf16 pieces, rows (z, part) interleaved
-    const float2* X = g == 2 ? a.J + (size_t)md * 3 * Nz * n : a.fields + (size_t)md * 6 * Nz * n;
-    for (int t = 0; t < T && ok; ++t) {
+    // ---- converters: staged FP32 complex [64 z][32 r] -> A pieces, rows (z, re/im), K = r
+    for (int t = 0; t < T; ++t) {
       const int s = t % C::S;
       const uint32_t ph = (uint32_t)(t / C::S) & 1u;
-      if (!mbar_wait(&sm->empty[s], ph ^ 1u)) {
-        ok = false;
+      if (!mbar_wait(&sm->fullS[s], ph)) {
         record_error(a.err, 1);
         break;
       }
       const int ib = blist[t / ksteps];
-      const int r0 = (t % ksteps) * BK;
-      const int field = (g == 1) ? (ib == 0 ? 4 : (ib == 1 ? 3 : 5)) : ib;
       const bool rot = (g == 1) ? (ib >= 1) : (ib == 1);
-      const float2* Xf = X + (size_t)field * Nz * n;
-      unsigned char* As = base + s * C::kStage;
-      const int r = r0 + 2 * lane;
-      for (int zl = warp * 16; zl < warp * 16 + 16; ++zl) {
-        const float2* rowp = Xf + (size_t)(z0 + zl) * n;
-        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-        if (r < n) v0 = rowp[r];
-        if (r + 1 < n) v1 = rowp[r + 1];
-        if (rot) {  // tau = -i: (x, y) -> (y, -x)
-          v0 = make_float2(v0.y, -v0.x);
-          v1 = make_float2(v1.y, -v1.x);
+      const float* stg = reinterpret_cast<const float*>(stage_S(s));
+      unsigned char* A = stage_A(s);
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int item = threadIdx.x + it * 128;  // 64 z x 4 chunks of 8 r
+        const int zl = item >> 2, c = item & 3;
+        const float4* src = reinterpret_cast<const float4*>(stg + zl * 64 + c * 16);
+        float re[8], im[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = src[q];
+          re[2 * q] = v.x;
+          im[2 * q] = v.y;
+          re[2 * q + 1] = v.z;
+          im[2 * q + 1] = v.w;
         }
-        float re0 = v0.x, re1 = v1.x, im0 = v0.y, im1 = v1.y;
-        const int k = 2 * lane;
-        const uint32_t chunk = (uint32_t)(k >> 3), within = (uint32_t)(k & 7) * 2;
+        if (rot) {  // tau = -i: (x, y) -> (y, -x)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float x = re[q];
+            re[q] = im[q];
+            im[q] = -x;
+          }
+        }
+        const int row_re = 2 * zl, row_im = 2 * zl + 1;
+        const uint32_t off_re = row_re * 64 + ((c ^ ((row_re >> 1) & 3)) << 4);
+        const uint32_t off_im = row_im * 64 + ((c ^ ((row_im >> 1) & 3)) << 4);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          const __nv_bfloat162 hre = __floats2bfloat162_rn(re0, re1), him = __floats2bfloat162_rn(im0, im1);
-          const int row_re = 2 * zl, row_im = 2 * zl + 1;
-          unsigned char* P = As + p * kTileBytes;
-          *reinterpret_cast<__nv_bfloat162*>(P + row_re * 128 + ((chunk ^ (row_re & 7)) << 4) + within) = hre;
-          *reinterpret_cast<__nv_bfloat162*>(P + row_im * 128 + ((chunk ^ (row_im & 7)) << 4) + within) = him;
-          re0 -= __low2float(hre);
-          re1 -= __high2float(hre);
-          im0 -= __low2float(him);
-          im1 -= __high2float(him);
+          uint32_t wr[4], wi[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 hr = __floats2bfloat162_rn(re[2 * q], re[2 * q + 1]);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(im[2 * q], im[2 * q + 1]);
+            wr[q] = *reinterpret_cast<const uint32_t*>(&hr);
+            wi[q] = *reinterpret_cast<const uint32_t*>(&hi);
+            re[2 * q] -= __low2float(hr);
+            re[2 * q + 1] -= __high2float(hr);
+            im[2 * q] -= __low2float(hi);
+            im[2 * q + 1] -= __high2float(hi);
+          }
+          unsigned char* P = A + p * kPA;
+          *reinterpret_cast<uint4*>(P + off_re) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+          *reinterpret_cast<uint4*>(P + off_im) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -265,18 +315,25 @@ __global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constan
           break;
         }
         const int ib = blist[t / ksteps];
-        const int x = ib * a.kpad + (t % ksteps) * BK;
-        unsigned char* Bs = base + s * C::kStage + NP * kTileBytes;
-        mbar_expect_tx(&sm->fullB[s], NP * kTileBytes);
+        const int r0 = (t % ksteps) * PBK;
+        // FP32 field tile: 64 z rows x 32 complex (64 floats)
+        mbar_expect_tx(&sm->fullS[s], kPS);
+        if (g == 2) {
+          tma_load_2d(stage_S(s), &tmJ, &sm->fullS[s], 2 * r0, (md * 3 + ib) * Nz + z0);
+        } else {
+          const int field = (g == 1) ? (ib == 0 ? 4 : (ib == 1 ? 3 : 5)) : ib;
+          tma_load_2d(stage_S(s), &tmF, &sm->fullS[s], 2 * r0, (md * 6 + field) * Nz + z0);
+        }
+        mbar_expect_tx(&sm->fullB[s], NP * kPB);
         for (int p = 0; p < NP; ++p) {
           const int y = (((md * 2 + gp) * NP + p) * 3 + ob) * a.npad + j0;
-          tma_load_2d(Bs + p * kTileBytes, &tmP, &sm->fullB[s], x, y);
+          tma_load_2d(stage_B(s) + p * kPB, &tmP, &sm->fullB[s], ib * a.kpad + r0, y);
         }
       }
     }
   } else {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(false);
+      const uint32_t idesc = idesc_bf16_n(PBN);
       for (int t = 0; t < T; ++t) {
         const int s = t % C::S;
         const uint32_t ph = (uint32_t)(t / C::S) & 1u;
@@ -285,16 +342,16 @@ __global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constan
           break;
         }
         tc_fence_after();
-        unsigned char* As = base + s * C::kStage;
-        unsigned char* Bs = As + NP * kTileBytes;
+        unsigned char* As = stage_A(s);
+        unsigned char* Bs = stage_B(s);
 #pragma unroll
-        for (int k16 = 0; k16 < BK / 16; ++k16) {
+        for (int k16 = 0; k16 < PBK / 16; ++k16) {
 #pragma unroll
           for (int pr = 0; pr < (NP == 2 ? 3 : 6); ++pr) {
             int ia, ib;
             product<NP>(pr, ia, ib);
-            const uint64_t ad = smem_desc(As + ia * kTileBytes + k16 * 32, 16, 1024);
-            const uint64_t bd = smem_desc(Bs + ib * kTileBytes + k16 * 32, 16, 1024);
+            const uint64_t ad = smem_desc_sw64(As + ia * kPA + k16 * 32);
+            const uint64_t bd = smem_desc_sw64(Bs + ib * kPB + k16 * 32);
             mma_bf16(tmem, ad, bd, idesc, (t | k16 | pr) != 0);
           }
         }
@@ -313,7 +370,8 @@ __global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constan
       const int row = warp * 32 + lane;
       const int z = z0 + (row >> 1), part = row & 1;
       float* out = a.coef + (size_t)(md * 9 + g * 3 + ob) * n * 2 * Nz;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < PBN; c0 += 32) {
+        if (j0 + c0 >= n) break;
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
 #pragma unroll
@@ -328,7 +386,7 @@ __global__ void __launch_bounds__(192, 1) tc_project_kernel(const __grid_constan
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PBN));
   }
 }
 
@@ -463,12 +521,17 @@ __global__ void __launch_bounds__(192, 1) tc_backproject_kernel(const __grid_con
 // ------------------------------------------------------------------ host side
 
 struct TcPlan {
-  int Nz = 0, n = 0, nmodes = 0, np = 0, npad = 0, kpad = 0;
+  int Nz = 0, n = 0, nmodes = 0, np = 0;
+  int npadP = 0;  // projection: rows (j) of each coefficient block padded to the N tile (256)
+  int npadQ = 0;  // back-projection: rows (r) of each field block padded to the M tile (128)
+  int kpad = 0;   // columns of each block padded to 64
   __nv_bfloat16* d_P = nullptr;
   __nv_bfloat16* d_Q = nullptr;
   __nv_bfloat16* d_split = nullptr;
-  int* d_err = nullptr;
-  CUtensorMap tmP, tmQ, tmS;
+  int* d_err = nullptr;  // owned by the caller's plan
+  CUtensorMap tmP, tmQ, tmS, tmF, tmJ;
+  const void* mapped_fields = nullptr;
+  const void* mapped_J = nullptr;
   size_t bytes = 0;
 };
 
@@ -485,17 +548,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-static bool make_map(CUtensorMap* m, void* ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                     uint32_t box_outer) {
+static bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                     uint32_t box_outer, CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B,
+                     CUtensorMapDataType ty = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   auto enc = get_encode();
   if (!enc) return false;
+  const uint64_t esz = ty == CU_TENSOR_MAP_DATA_TYPE_FLOAT32 ? 4 : 2;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {inner * 2};
+  cuuint64_t strides[1] = {inner * esz};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return enc(m, ty, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static void split_bf16(double x, int np, uint16_t* out) {
@@ -528,8 +592,8 @@ static std::vector<uint16_t> pack(const double* M, int nmodes, int n, int np, in
   return out;
 }
 
-cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const double* P, const double* Q, char* msg,
-                      size_t msglen) {
+cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const double* P, const double* Q, int* err,
+                      char* msg, size_t msglen) {
   *outp = nullptr;
   if (np != 2 && np != 3) {
     snprintf(msg, msglen, "npieces must be 2 or 3");
@@ -537,6 +601,10 @@ cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const do
   }
   if (Nz % 64) {
     snprintf(msg, msglen, "Nz must be a multiple of 64");
+    return cudaErrorNotSupported;
+  }
+  if (n % 2) {
+    snprintf(msg, msglen, "the tensor-core path needs an even Nr (16-byte field row stride for TMA)");
     return cudaErrorNotSupported;
   }
   int dev = 0, cc_major = 0, cc_minor = 0;
@@ -556,27 +624,29 @@ cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const do
   t->n = n;
   t->nmodes = nmodes;
   t->np = np;
-  t->npad = (n + BN - 1) / BN * BN;
+  t->npadP = (n + PBN - 1) / PBN * PBN;
+  t->npadQ = (n + BM - 1) / BM * BM;
   t->kpad = (n + BK - 1) / BK * BK;
-  std::vector<uint16_t> hp = pack(P, nmodes, n, np, t->npad, t->kpad);
-  std::vector<uint16_t> hq = pack(Q, nmodes, n, np, t->npad, t->kpad);
+  std::vector<uint16_t> hp = pack(P, nmodes, n, np, t->npadP, t->kpad);
+  std::vector<uint16_t> hq = pack(Q, nmodes, n, np, t->npadQ, t->kpad);
   const size_t split_elems = (size_t)nmodes * np * 6 * t->kpad * 2 * Nz;
   cudaError_t e = cudaMalloc(&t->d_P, hp.size() * 2);
   if (e == cudaSuccess) e = cudaMalloc(&t->d_Q, hq.size() * 2);
   if (e == cudaSuccess) e = cudaMalloc(&t->d_split, split_elems * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&t->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(t->d_P, hp.data(), hp.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(t->d_Q, hq.data(), hq.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(t->d_split, 0, split_elems * 2);
-  if (e == cudaSuccess) e = cudaMemset(t->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     snprintf(msg, msglen, "allocation/upload failed");
     tc_destroy(t);
     return e;
   }
-  t->bytes = hp.size() * 2 + hq.size() * 2 + split_elems * 2 + 4;
-  const uint64_t cols = (uint64_t)3 * t->kpad, rows = (uint64_t)nmodes * 2 * np * 3 * t->npad;
-  bool ok = make_map(&t->tmP, t->d_P, cols, rows, BK, BN) && make_map(&t->tmQ, t->d_Q, cols, rows, BK, BM) &&
+  t->d_err = err;
+  t->bytes = hp.size() * 2 + hq.size() * 2 + split_elems * 2;
+  const uint64_t cols = (uint64_t)3 * t->kpad;
+  bool ok = make_map(&t->tmP, t->d_P, cols, (uint64_t)nmodes * 2 * np * 3 * t->npadP, PBK, PBN,
+                     CU_TENSOR_MAP_SWIZZLE_64B) &&
+            make_map(&t->tmQ, t->d_Q, cols, (uint64_t)nmodes * 2 * np * 3 * t->npadQ, BK, BM) &&
             make_map(&t->tmS, t->d_split, (uint64_t)2 * Nz, (uint64_t)nmodes * np * 6 * t->kpad, 64, BK);
   if (!ok) {
     snprintf(msg, msglen, "tensor map encoding failed");
@@ -585,11 +655,11 @@ cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const do
   }
   cudaError_t e1, e2;
   if (np == 2) {
-    e1 = cudaFuncSetAttribute(tc_project_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<2>::kSmem);
+    e1 = cudaFuncSetAttribute(tc_project_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCfg<2>::kSmem);
     e2 = cudaFuncSetAttribute(tc_backproject_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Cfg<2>::kSmem);
   } else {
-    e1 = cudaFuncSetAttribute(tc_project_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::kSmem);
+    e1 = cudaFuncSetAttribute(tc_project_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCfg<3>::kSmem);
     e2 = cudaFuncSetAttribute(tc_backproject_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Cfg<3>::kSmem);
   }
@@ -607,16 +677,27 @@ void tc_destroy(TcPlan* t) {
   if (t->d_P) cudaFree(t->d_P);
   if (t->d_Q) cudaFree(t->d_Q);
   if (t->d_split) cudaFree(t->d_split);
-  if (t->d_err) cudaFree(t->d_err);
   delete t;
 }
 
 size_t tc_device_bytes(const TcPlan* t) { return t ? t->bytes : 0; }
 __nv_bfloat16* tc_split_buffer(TcPlan* t) { return t->d_split; }
 int tc_split_rows(const TcPlan* t) { return t->kpad; }
-int* tc_error_flag(TcPlan* t) { return t->d_err; }
 
 cudaError_t tc_project(TcPlan* t, const void* fields, const void* J, void* coef, cudaStream_t st) {
+  // FP32 views of the caller's field and current arrays for the staging TMA: rows of 2 Nr floats
+  if (fields != t->mapped_fields) {
+    if (!make_map(&t->tmF, fields, (uint64_t)2 * t->n, (uint64_t)t->nmodes * 6 * t->Nz, 2 * PBK, 64,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_DATA_TYPE_FLOAT32))
+      return cudaErrorInvalidValue;
+    t->mapped_fields = fields;
+  }
+  if (J && J != t->mapped_J) {
+    if (!make_map(&t->tmJ, J, (uint64_t)2 * t->n, (uint64_t)t->nmodes * 3 * t->Nz, 2 * PBK, 64,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_DATA_TYPE_FLOAT32))
+      return cudaErrorInvalidValue;
+    t->mapped_J = J;
+  }
   TcProjArgs a;
   a.fields = (const float2*)fields;
   a.J = (const float2*)J;
@@ -624,14 +705,15 @@ cudaError_t tc_project(TcPlan* t, const void* fields, const void* J, void* coef,
   a.err = t->d_err;
   a.Nz = t->Nz;
   a.n = t->n;
-  a.npad = t->npad;
+  a.npad = t->npadP;
   a.kpad = t->kpad;
   a.ngroups = J ? 3 : 2;
-  dim3 grid(t->Nz / 64, t->npad / BN, t->nmodes * a.ngroups * 3);
+  const CUtensorMap& mJ = J ? t->tmJ : t->tmF;
+  dim3 grid(t->Nz / 64, t->npadP / PBN, t->nmodes * a.ngroups * 3);
   if (t->np == 2)
-    tc_project_kernel<2><<<grid, 192, Cfg<2>::kSmem, st>>>(t->tmP, a);
+    tc_project_kernel<2><<<grid, 192, PCfg<2>::kSmem, st>>>(t->tmP, t->tmF, mJ, a);
   else
-    tc_project_kernel<3><<<grid, 192, Cfg<3>::kSmem, st>>>(t->tmP, a);
+    tc_project_kernel<3><<<grid, 192, PCfg<3>::kSmem, st>>>(t->tmP, t->tmF, mJ, a);
   return cudaGetLastError();
 }
 
@@ -641,9 +723,9 @@ cudaError_t tc_backproject(TcPlan* t, void* fields, cudaStream_t st) {
   a.err = t->d_err;
   a.Nz = t->Nz;
   a.n = t->n;
-  a.npad = t->npad;
+  a.npad = t->npadQ;
   a.kpad = t->kpad;
-  dim3 grid(t->Nz / 64, t->npad / BM, t->nmodes * 6);
+  dim3 grid(t->Nz / 64, t->npadQ / BM, t->nmodes * 6);
   if (t->np == 2)
     tc_backproject_kernel<2><<<grid, 192, Cfg<2>::kSmem, st>>>(t->tmQ, t->tmS, a);
   else

@@ -12,13 +12,14 @@ struct SpectralArgs {
   const void* phase;     // [nmodes][2][n][Nz] PhaseD / PhaseF
   const void* zsym;      // [Nz] ZSymD / ZSymF
   const void* lam;       // [nmodes][2][n] double / df (lambda for TM, mu for TE)
-  const void* twiddle;   // [Nz/2] complex<T>, exp(-2 pi i k / Nz)
+  const void* twiddle;   // [Nz] complex<T>, exp(-2 pi i k / Nz)
   __nv_bfloat16* split_out;  // tensor-core path: [nmodes][npieces][6][split_rows][2 Nz]
   int npieces;
   int split_rows;            // coefficient rows per block in split_out (n padded to the K tile)
   int Nz, logNz, n;
   double dt;
   int hasJ;
+  int* err;              // device failure flag (bounded waits)
 };
 
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);
@@ -63,12 +64,11 @@ cudaError_t launch_backproject_simt(const BackArgs& a, int nmodes, int precision
 // ---------------------------------------------------------------- tensor-core projections
 struct TcPlan;  // defined in k_tc.cu
 cudaError_t tc_create(TcPlan** out, int Nz, int n, int nmodes, int npieces, const double* P, const double* Q,
-                      char* msg, size_t msglen);
+                      int* err, char* msg, size_t msglen);
 void tc_destroy(TcPlan* p);
 size_t tc_device_bytes(const TcPlan* p);
 __nv_bfloat16* tc_split_buffer(TcPlan* p);
 int tc_split_rows(const TcPlan* p);
-int* tc_error_flag(TcPlan* p);
 cudaError_t tc_project(TcPlan* p, const void* fields, const void* J, void* coef, cudaStream_t st);
 cudaError_t tc_backproject(TcPlan* p, void* fields, cudaStream_t st);
 int tc_launches_per_step(const TcPlan* p);

@@ -5,7 +5,7 @@ import pytest
 from oracle import diagnostics as dg
 from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
-from tests.gpu_util import field_errors, zero_axis
+from tests.gpu_util import field_errors, floor_for, zero_axis
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,7 @@ def test_parity_small_ragged(prec):
     got = _run(prec, F, J, Nz, Nr, modes, order, dz, dr, dt, 3)
     ref = _oracle(F, J, Nz, Nr, modes, order, dz, dr, dt, 3)
     for i in range(len(modes)):
-        err = field_errors(got[i], ref[i])
+        err = field_errors(got[i], ref[i], floor_for(prec))
         assert err.max() < TOL[prec] * 3, (modes[i], err)
 
 
@@ -69,9 +69,11 @@ def test_parity_vacuum_pulse_256x64(prec, vacuum_ref):
     # the 256 x 64 vacuum pulse (m = 1, order 8, dt = dz): after 1 step and after 200 steps
     w, F, r1, r200 = vacuum_ref
     g1 = _run(prec, F, None, w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, 1)
-    assert field_errors(g1[0], r1).max() < TOL[prec]
+    e1 = field_errors(g1[0], r1, floor_for(prec))
+    rel = [np.linalg.norm(r1[f]) / np.linalg.norm(r1) for f in range(6)]
+    assert e1.max() < TOL[prec], (e1, rel)
     g200 = _run(prec, F, None, w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, w.steps)
-    err = field_errors(g200[0], r200)
+    err = field_errors(g200[0], r200, floor_for(prec))
     assert err.max() < TOL[prec] * (0.25 if prec == "fp64" else 1) * w.steps, err
 
 
