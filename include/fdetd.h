@@ -168,6 +168,31 @@ int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, int taylor_or
  */
 int envelope_step(envelope_plan_t plan, void* a, const float* chi, int nsteps, void* stream);
 
+/*
+ * envelope_step_static - the envelope step for callers that cannot allocate device memory
+ * (no counterpart in the paper; same mathematics and layouts as envelope_step).
+ *
+ * Who needs it: code running while its stream is captured into a CUDA graph (cudaMalloc is
+ * not allowed during capture), applications whose device memory is entirely pre-reserved by
+ * their own pool or arena, and plugins whose host framework owns every allocation.  It takes
+ * no plan and allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * a: device [2][Nz][Nr] complex64 (a, a~), advanced in place; chi: device [Nz][Nr] float32.
+ * order (even, 2..32), taylor_order (1..16), dz, dr, dt, k0 as in envelope_plan.
+ * Limit: Nz * Nr <= 1048576 (2^20 cells); larger grids return FDETD_ERR_ARG.
+ * Scratch: one file-scope device array of 4 * 2^20 complex64 values (32 MiB), held by every
+ * GPU that loads the library until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device current) and caches it;
+ * make that first call before any stream capture.  All calls share the array and each call
+ * overwrites it before reading it (no state carries over, nothing needs clearing), so calls
+ * whose kernels overlap on the GPU - on different streams, or on one device from several
+ * threads without ordering - race on it and must be serialised by the caller.
+ * Asynchronous on `stream`; returns FDETD_OK, FDETD_ERR_ARG or FDETD_ERR_CUDA (this entry
+ * point does not set fdetd_last_error).
+ */
+int envelope_step_static(void* a, const float* chi, int Nz, int Nr, int order, int taylor_order, double dz,
+                         double dr, double dt, double k0, int nsteps, void* stream);
+
 /* Number of kernels one envelope step launches. */
 int envelope_plan_launches_per_step(envelope_plan_t plan);
 

@@ -17,6 +17,7 @@ from ._native import (  # noqa: F401
     FdetdPlan,
     envelope_plan,
     envelope_step,
+    envelope_step_static,
     fdetd_host_coeffs,
     fdetd_host_tables,
     fdetd_plan,

@@ -49,6 +49,8 @@ def lib():
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_plan_launches_per_step.argtypes = [c_vp]
+    L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
+                                       c_vp]
     L.envelope_plan_destroy.argtypes = [c_vp]
     L.fdetd_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     _LIB = L
@@ -228,4 +230,19 @@ def envelope_step(plan, a, chi, nsteps=1, stream=None):
     if not chi.is_cuda or chi.dtype != torch.float32 or tuple(chi.shape) != (plan.Nz, plan.Nr) or not chi.is_contiguous():
         raise FdetdError("chi must be a contiguous cuda float32 tensor of shape (Nz, Nr)")
     _check(lib().envelope_step(plan.handle, a.data_ptr(), chi.data_ptr(), nsteps, _stream_handle(stream)))
+    return a
+
+
+def envelope_step_static(a, chi, order, taylor_order, dz, dr, dt, k0=2 * np.pi, nsteps=1, stream=None):
+    """Allocation-free envelope step (see include/fdetd.h): same arguments as a plan plus step."""
+    import torch
+    if not a.is_cuda or a.dtype != torch.complex64 or a.dim() != 3 or a.shape[0] != 2 or not a.is_contiguous():
+        raise FdetdError("a must be a contiguous cuda complex64 tensor of shape (2, Nz, Nr)")
+    Nz, Nr = a.shape[1], a.shape[2]
+    if not chi.is_cuda or chi.dtype != torch.float32 or tuple(chi.shape) != (Nz, Nr) or not chi.is_contiguous():
+        raise FdetdError("chi must be a contiguous cuda float32 tensor of shape (Nz, Nr)")
+    rc = lib().envelope_step_static(a.data_ptr(), chi.data_ptr(), Nz, Nr, order, taylor_order, dz, dr, dt, k0,
+                                    nsteps, _stream_handle(stream))
+    if rc != 0:
+        raise FdetdError(f"envelope_step_static error {rc}")
     return a

@@ -115,6 +115,21 @@ std::vector<double> centred_d2_coeffs(int order, double* e0) {
   return e;
 }
 
+int centred_coeffs_fixed(int order, double* d1, double* e2, double* e0) {
+  if (order < 2 || order > 32 || (order & 1)) return -1;
+  const int N = order / 2;
+  Rat s(0, 1);
+  for (int n = 1; n <= N; ++n) {
+    const Rat d = centred_d1_rat(N, n);
+    const Rat en = d.mul(Rat(2, n));
+    d1[n - 1] = d.val();
+    e2[n - 1] = en.val();
+    s = s.add(en);
+  }
+  *e0 = s.mul(Rat(-2, 1)).val();
+  return N;
+}
+
 std::vector<double> axis_coeffs(int N) {
   // c_k = prod_{j != k} j^2 / (j^2 - k^2)   (Lagrange in rho^2 at rho = 0, Sec. 2.4)
   std::vector<double> c(N);

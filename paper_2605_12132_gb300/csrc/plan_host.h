@@ -25,6 +25,9 @@ std::vector<double> staggered_coeffs(int order);
 std::vector<double> centred_d1_coeffs(int order);
 std::vector<double> centred_d2_coeffs(int order, double* e0);
 std::vector<double> axis_coeffs(int N);
+// Centred first (d1[0..N-1]) and second (e2[0..N-1], e0) derivative coefficients written into
+// caller arrays (no allocation); returns N = order/2 or -1 for an invalid order.
+int centred_coeffs_fixed(int order, double* d1, double* e2, double* e0);
 
 // Per-mode radial tables.  All matrices are row-major (3n x 3n), n = Nr.
 //  Field blocks (columns of P, rows of Q), E group: (Er, Et^, Ez); B group: (Bt, Br^, Bz^)
