@@ -63,6 +63,7 @@ enum {
 };
 
 typedef struct fdetd_plan_s* fdetd_plan_t;
+typedef struct fdetd_batch_s* fdetd_batch_t;
 typedef struct envelope_plan_s* envelope_plan_t;
 
 /*
@@ -130,6 +131,24 @@ int fdetd_plan_set_profiling(fdetd_plan_t plan, int on);
 int fdetd_plan_kernel_times(fdetd_plan_t plan, double* ms, long* calls);
 
 int fdetd_plan_destroy(fdetd_plan_t plan);
+
+/*
+ * Batches of uneven instances advanced by one CUDA graph.
+ *
+ * fdetd_batch_add registers an instance (a plan with its own device fields and optional J;
+ * each plan at most once per batch because its scratch buffers are private to it) and writes
+ * its index to *index (may be NULL).
+ * fdetd_batch_capture records `nsteps` steps of every instance into one CUDA graph, each
+ * instance on its own branch (forked from and joined back into `stream`), so independent
+ * instances run concurrently on the GPU; fdetd_batch_launch replays it on `stream`.
+ * Re-capture after adding instances.  The pointers registered must stay valid while the
+ * graph is launched.  Host-side, capture uses only stream-ordered calls (no allocation).
+ */
+int fdetd_batch_create(fdetd_batch_t* out);
+int fdetd_batch_add(fdetd_batch_t batch, fdetd_plan_t plan, void* fields, const void* J, int* index);
+int fdetd_batch_capture(fdetd_batch_t batch, int nsteps, void* stream);
+int fdetd_batch_launch(fdetd_batch_t batch, void* stream);
+int fdetd_batch_destroy(fdetd_batch_t batch);
 
 /*
  * fdetd_host_tables - host-only (no GPU needed) export of the FP64 plan tables of

@@ -13,6 +13,7 @@ The library is loaded lazily on first use; importing this package does not need 
 from ._native import (  # noqa: F401
     PRECISIONS,
     EnvelopePlan,
+    FdetdBatch,
     FdetdError,
     FdetdPlan,
     envelope_plan,

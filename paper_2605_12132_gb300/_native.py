@@ -49,6 +49,11 @@ def lib():
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_plan_launches_per_step.argtypes = [c_vp]
+    L.fdetd_batch_create.argtypes = [ctypes.POINTER(c_vp)]
+    L.fdetd_batch_add.argtypes = [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_int)]
+    L.fdetd_batch_capture.argtypes = [c_vp, c_int, c_vp]
+    L.fdetd_batch_launch.argtypes = [c_vp, c_vp]
+    L.fdetd_batch_destroy.argtypes = [c_vp]
     L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
                                        c_vp]
     L.envelope_plan_destroy.argtypes = [c_vp]
@@ -246,3 +251,41 @@ def envelope_step_static(a, chi, order, taylor_order, dz, dr, dt, k0=2 * np.pi, 
     if rc != 0:
         raise FdetdError(f"envelope_step_static error {rc}")
     return a
+
+
+class FdetdBatch:
+    """Uneven instances advanced together by one captured CUDA graph (see include/fdetd.h)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().fdetd_batch_create(ctypes.byref(h)))
+        self.handle = h
+        self._keep = []
+
+    def add(self, plan, fields, J=None):
+        _check_tensor(fields, plan, 6, "fields")
+        jp = None
+        if J is not None:
+            _check_tensor(J, plan, 3, "J")
+            jp = J.data_ptr()
+        idx = ctypes.c_int(-1)
+        _check(lib().fdetd_batch_add(self.handle, plan.handle, fields.data_ptr(), jp, ctypes.byref(idx)))
+        self._keep.append((plan, fields, J))
+        return idx.value
+
+    def capture(self, nsteps=1, stream=None):
+        _check(lib().fdetd_batch_capture(self.handle, nsteps, _stream_handle(stream)))
+
+    def launch(self, stream=None):
+        _check(lib().fdetd_batch_launch(self.handle, _stream_handle(stream)))
+
+    def close(self):
+        if self.handle:
+            lib().fdetd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -416,6 +416,121 @@ extern "C" int fdetd_host_coeffs(int kind, int order, double* out) {
   return (int)v.size();
 }
 
+// ------------------------------------------------------------------ batches of instances
+
+struct fdetd_batch_s {
+  struct Inst {
+    fdetd_plan_s* plan;
+    void* fields;
+    const void* J;
+  };
+  std::vector<Inst> inst;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int steps = 0;
+};
+
+static void batch_release_graph(fdetd_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+extern "C" int fdetd_batch_create(fdetd_batch_t* out) {
+  if (!out) return fail(FDETD_ERR_ARG, "out is null");
+  fdetd_batch_s* b = new fdetd_batch_s();
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return fail(FDETD_ERR_CUDA, "event creation failed");
+  }
+  *out = b;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_add(fdetd_batch_t b, fdetd_plan_t plan, void* fields, const void* J, int* index) {
+  if (!b || !plan || !fields) return fail(FDETD_ERR_ARG, "null argument");
+  if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  for (auto& i : b->inst)
+    if (i.plan == plan) return fail(FDETD_ERR_ARG, "a plan may appear once per batch (its scratch is not shared)");
+  cudaStream_t s;
+  cudaEvent_t e;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(FDETD_ERR_CUDA, "stream");
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return fail(FDETD_ERR_CUDA, "event");
+  }
+  b->inst.push_back({plan, fields, J});
+  b->side.push_back(s);
+  b->join.push_back(e);
+  batch_release_graph(b);
+  if (index) *index = (int)b->inst.size() - 1;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
+  if (!b || nsteps < 1) return fail(FDETD_ERR_ARG, "bad batch or nsteps");
+  if (b->inst.empty()) return fail(FDETD_ERR_ARG, "empty batch");
+  for (auto& i : b->inst)
+    if (i.plan->profiling) return fail(FDETD_ERR_ARG, "turn profiling off before capturing");
+  batch_release_graph(b);
+  cudaStream_t s0 = (cudaStream_t)stream;
+  cudaStream_t cap = s0;
+  cudaStream_t own = nullptr;
+  if (!cap) {  // the legacy default stream cannot be captured
+    if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return fail(FDETD_ERR_CUDA, "stream");
+    cap = own;
+  }
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  int rc = FDETD_OK;
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
+  for (size_t k = 0; e == cudaSuccess && k < b->inst.size(); ++k) {
+    e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+    if (e != cudaSuccess) break;
+    rc = fdetd_step(b->inst[k].plan, b->inst[k].fields, b->inst[k].J, nsteps, b->side[k]);
+    if (rc != FDETD_OK) break;
+    e = cudaEventRecord(b->join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, b->join[k], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+  if (own) cudaStreamDestroy(own);
+  if (rc != FDETD_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    b->exec = nullptr;
+    return fail(FDETD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  b->graph = g;
+  b->steps = nsteps;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_launch(fdetd_batch_t b, void* stream) {
+  if (!b || !b->exec) return fail(FDETD_ERR_ARG, "batch has no captured graph");
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_destroy(fdetd_batch_t b) {
+  if (!b) return FDETD_OK;
+  batch_release_graph(b);
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+  return FDETD_OK;
+}
+
 // ------------------------------------------------------------------ envelope
 
 struct envelope_plan_s {

@@ -168,27 +168,43 @@ __device__ __forceinline__ void dft_small(C* v) {
   }
 }
 
-// One in-place Stockham pass of radix RR over narr arrays of length N stored back to back
-// (sub-sequence length Ns before the pass).  MAXB bounds the butterflies per thread.
-template <int RR, bool INV, int NT, int MAXB, typename C>
-__device__ __forceinline__ void stockham_pass(C* s, int narr, int N, int Ns, const C* tw) {
+// Shared-memory layout of one array: logical element i at physical i + i/8 (one pad slot per
+// 8 elements), which keeps every Stockham pass at most 2-way bank-conflicted.
+__device__ __forceinline__ int padx(int i) { return i + (i >> 3); }
+
+// Twiddle exp(-2 pi i m / N) from two small shared tables: lo[m & 63] * hi[m >> 6].
+template <typename C>
+__device__ __forceinline__ C twiddle(const C* lo, const C* hi, int m) {
+  return cmul(hi[m >> 6], lo[m & 63]);
+}
+
+// One in-place Stockham pass of radix RR over arrays a0 .. a0+na-1 of length N (sub-sequence
+// length Ns before the pass).  Every butterfly of the group is read into registers before the
+// barrier and written after it, so source and destination layouts may differ: SRC_PAD = false reads
+// the unpadded arrays left by the bulk copy (array a at a*N), otherwise arrays sit at a*(N + N/8)
+// in the padded layout.  MAXB bounds the butterflies per thread.
+template <int RR, bool INV, int NT, int MAXB, bool SRC_PAD, typename C>
+__device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int N, int Ns, const C* lo, const C* hi) {
   const int nbf = N / RR;
-  const int total = narr * nbf;
+  const int total = na * nbf;
   const int stride = N / (Ns * RR);
+  const int P = N + (N >> 3);
   C v[MAXB][RR];
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
     const int b = threadIdx.x + i * NT;
     if (b < total) {
-      const int a = b / nbf, j = b - a * nbf;
-      const C* x = s + (size_t)a * N;
+      const int a = a0 + b / nbf, j = b % nbf;
 #pragma unroll
-      for (int r = 0; r < RR; ++r) v[i][r] = x[j + r * nbf];
+      for (int r = 0; r < RR; ++r) {
+        const int li = j + r * nbf;
+        v[i][r] = SRC_PAD ? s[a * P + padx(li)] : s[a * N + li];
+      }
       const int k = j & (Ns - 1);
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < RR; ++r) {
-          const C w = tw[(r * k) * stride];
+          const C w = twiddle(lo, hi, (r * k) * stride);
           v[i][r] = INV ? cmulconj(v[i][r], w) : cmul(v[i][r], w);
         }
       }
@@ -200,32 +216,60 @@ __device__ __forceinline__ void stockham_pass(C* s, int narr, int N, int Ns, con
   for (int i = 0; i < MAXB; ++i) {
     const int b = threadIdx.x + i * NT;
     if (b < total) {
-      const int a = b / nbf, j = b - a * nbf;
+      const int a = a0 + b / nbf, j = b % nbf;
       const int k = j & (Ns - 1);
-      C* x = s + (size_t)a * N + (j - k) * RR + k;
+      C* x = s + a * P;
+      const int base = (j - k) * RR + k;
 #pragma unroll
-      for (int r = 0; r < RR; ++r) x[r * Ns] = v[i][r];
+      for (int r = 0; r < RR; ++r) x[padx(base + r * Ns)] = v[i][r];
     }
   }
   __syncthreads();
 }
 
-// Full FFT of narr arrays (forward or inverse, unnormalised): one small-radix pass first
-// when log2 N is not a multiple of log2 R, then radix-R passes.
-template <int R, bool INV, int NT, int MAXB, typename C>
-__device__ void fft_all(C* s, int narr, int N, int logN, const C* tw) {
+// One pass over all narr arrays in groups of at most G.  A pass that reads the unpadded layout walks
+// the groups last-first: group g's padded destination [g0 P, g1 P) then never overlaps the unpadded
+// source [0, g0 N) of the groups still to be read (P > N).
+template <int RR, bool INV, int NT, int MAXB, int G, bool SRC_PAD, typename C>
+__device__ __forceinline__ void pass_all(C* s, int narr, int N, int Ns, const C* lo, const C* hi) {
+  const int ng = (narr + G - 1) / G;
+  for (int gi = 0; gi < ng; ++gi) {
+    const int g = SRC_PAD ? gi : ng - 1 - gi;
+    const int a0 = g * G, na = min(G, narr - a0);
+    stockham_pass<RR, INV, NT, MAXB, SRC_PAD>(s, a0, na, N, Ns, lo, hi);
+  }
+}
+
+// Full FFT of narr arrays (forward or inverse, unnormalised), result in the padded layout:
+// one small-radix pass first when log2 N is not a multiple of log2 R, then radix-R passes.
+// MAXB = G butterflies of radix R per thread (NT >= N / R).
+template <int R, bool INV, int NT, int G, bool SRC_PAD, typename C>
+__device__ void fft_all(C* s, int narr, int N, int logN, const C* lo, const C* hi) {
   const int lr = R == 8 ? 3 : 2;
   int Ns = 1;
   const int rem = logN % lr;
+  bool from_pad = SRC_PAD;
   if (rem == 1) {
-    stockham_pass<2, INV, NT, MAXB * (R / 2)>(s, narr, N, Ns, tw);
+    if (from_pad)
+      pass_all<2, INV, NT, G*(R / 2), G, true>(s, narr, N, Ns, lo, hi);
+    else
+      pass_all<2, INV, NT, G*(R / 2), G, false>(s, narr, N, Ns, lo, hi);
     Ns *= 2;
+    from_pad = true;
   } else if (rem == 2) {
-    stockham_pass<4, INV, NT, MAXB * (R / 4)>(s, narr, N, Ns, tw);
+    if (from_pad)
+      pass_all<4, INV, NT, G*(R / 4), G, true>(s, narr, N, Ns, lo, hi);
+    else
+      pass_all<4, INV, NT, G*(R / 4), G, false>(s, narr, N, Ns, lo, hi);
     Ns *= 4;
+    from_pad = true;
   }
   for (int p = 0; p < logN / lr; ++p) {
-    stockham_pass<R, INV, NT, MAXB>(s, narr, N, Ns, tw);
+    if (from_pad)
+      pass_all<R, INV, NT, G, G, true>(s, narr, N, Ns, lo, hi);
+    else
+      pass_all<R, INV, NT, G, G, false>(s, narr, N, Ns, lo, hi);
+    from_pad = true;
     Ns *= R;
   }
 }
@@ -235,10 +279,11 @@ __device__ void fft_all(C* s, int narr, int N, int logN, const C* tw) {
 // T: data real type; K: coefficient type (double or df); PH / ZS: table records;
 // R: FFT radix; NT: threads; MAXB: radix-R butterflies per thread per pass.
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, int MAXB, bool SPLIT_OUT>
-__global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs args) {
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(SpectralArgs args) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t load_bar;
+  __shared__ C tw_lo[64], tw_hi[64];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int Nz = args.Nz, L = args.logNz, n = args.n;
   const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
@@ -255,43 +300,48 @@ __global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs args) {
   }
   const C* coef = reinterpret_cast<const C*>(args.coef);
   const C* tw = reinterpret_cast<const C*>(args.twiddle);
-  // the family's coefficient columns and its phase column are contiguous in global memory:
-  // one bulk copy each into shared memory, completing on one mbarrier
-  PH* phase = reinterpret_cast<PH*>(s + (size_t)narr * Nz);
+  // the family's coefficient columns are contiguous in global memory: one bulk copy each into
+  // shared memory (unpadded), completing on one mbarrier; the first FFT pass re-lays them out padded
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&load_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const uint32_t col = (uint32_t)(Nz * sizeof(C)), pcol = (uint32_t)(Nz * sizeof(PH));
+    const uint32_t col = (uint32_t)(Nz * sizeof(C));
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
                      smem_addr(&load_bar)),
-                 "r"(narr * col + pcol)
+                 "r"(narr * col)
                  : "memory");
     for (int a = 0; a < narr; ++a)
       bulk_g2s(s + (size_t)a * Nz, coef + ((size_t)(md * 9 + idx[a]) * n + j) * Nz, col, &load_bar);
-    bulk_g2s(phase, reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz, pcol,
-             &load_bar);
+  }
+  // two-level twiddle tables: lo[m] = W^m (m < 64), hi[m] = W^(64 m) (m < Nz / 64)
+  for (int m = threadIdx.x; m < 64; m += NT) {
+    tw_lo[m] = tw[m & (Nz - 1)];
+    tw_hi[m] = tw[(64 * m) & (Nz - 1)];
   }
   __syncthreads();
   if (!bar_wait(&load_bar, 0)) {
     if (threadIdx.x == 0 && args.err) atomicCAS(args.err, 0, 8);
     return;
   }
-  fft_all<R, false, NT, MAXB>(s, narr, Nz, L, tw);
+  const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
+  fft_all<R, false, NT, MAXB, false>(s, narr, Nz, L, tw_lo, tw_hi);  // MAXB = array group size
   // exact rotation per kz (the 1/Nz of the inverse transform folded in)
   const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
   const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
   const T dt = (T)args.dt;
   const T inv = (T)1 / (T)Nz;
+  const int PS = Nz + (Nz >> 3);
   for (int q = threadIdx.x; q < Nz; q += NT) {
+    const int pq = padx(q);
     K spr, spi, smr, smi, A1, A2;
     T B1, B2;
     zsym_unpack(zs[q], spr, spi, smr, smi);
-    phase_unpack(phase[q], A1, A2, B1, B2);  // from shared memory
-    C x0 = s[q], x1 = s[Nz + q], x2 = s[2 * Nz + q];
+    phase_unpack(phase[q], A1, A2, B1, B2);
+    C x0 = s[pq], x1 = s[PS + pq], x2 = s[2 * PS + pq];
     C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
     if (hasJ) {
-      j0 = s[3 * Nz + q];
-      if (fam == 0) j1 = s[4 * Nz + q];
+      j0 = s[3 * PS + pq];
+      if (fam == 0) j1 = s[4 * PS + pq];
     }
     C y0, y1, y2, z0, z1, z2, yj0, yj1, yj2, zj0, zj1, zj2;
     if (fam == 0) {
@@ -311,25 +361,25 @@ __global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs args) {
     r0.x *= inv; r0.y *= inv;
     r1.x *= inv; r1.y *= inv;
     r2.x *= inv; r2.y *= inv;
-    s[q] = r0;
-    s[Nz + q] = r1;
-    s[2 * Nz + q] = r2;
+    s[pq] = r0;
+    s[PS + pq] = r1;
+    s[2 * PS + pq] = r2;
   }
   __syncthreads();
-  fft_all<R, true, NT, MAXB>(s, 3, Nz, L, tw);
+  fft_all<R, true, NT, MAXB, true>(s, 3, Nz, L, tw_lo, tw_hi);
   if (!SPLIT_OUT) {
     C* out = reinterpret_cast<C*>(args.coef);
     for (int a = 0; a < 3; ++a) {
       C* dst = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
-      const C* x = s + (size_t)a * Nz;
-      for (int z = threadIdx.x; z < Nz; z += NT) dst[z] = x[z];
+      const C* x = s + (size_t)a * PS;
+      for (int z = threadIdx.x; z < Nz; z += NT) dst[z] = x[padx(z)];
     }
   } else {
     // bf16 split pieces for the tensor-core back-projection (re, im interleaved along z)
     for (int a = 0; a < 3; ++a) {
-      const C* x = s + (size_t)a * Nz;
+      const C* x = s + (size_t)a * PS;
       for (int z = threadIdx.x; z < Nz; z += NT) {
-        const C v = x[z];
+        const C v = x[padx(z)];
         split_store(args.split_out, args.npieces, md, idx[a], j, z, args.split_rows, Nz, (float)v.x, (float)v.y);
       }
     }
@@ -339,7 +389,7 @@ __global__ void __launch_bounds__(NT) spectral_kernel(SpectralArgs args) {
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
-  constexpr int MAXB = 5;  // radix-R butterflies per thread per pass (5 arrays, NT >= Nz / R)
+  constexpr int MAXB = 3;  // arrays per FFT pass group = radix-R butterflies per thread (NT >= Nz / R)
   const size_t smem = spectral_smem_bytes(a.Nz, sizeof(T) == 8 ? 0 : 1, a.hasJ);
   auto k = spectral_kernel<T, K, PH, ZS, R, NT, MAXB, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -365,10 +415,9 @@ cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bo
   return launch_sized<float, df, PhaseF, ZSymF, 8, false>(a, nmodes, st);
 }
 
-// coefficient columns of the family (5 with a current, else 3) plus its phase column
+// coefficient columns of the family (5 with a current, else 3) in the padded layout (9/8)
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ) {
-  return (size_t)(hasJ ? 5 : 3) * Nz * (precision == 0 ? 16 : 8) +
-         (size_t)Nz * (precision == 0 ? sizeof(PhaseD) : sizeof(PhaseF));
+  return (size_t)(hasJ ? 5 : 3) * (Nz + Nz / 8) * (precision == 0 ? 16 : 8);
 }
 
 }  // namespace fdetd
