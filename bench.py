@@ -8,6 +8,8 @@ in HBM, L2 flushed (a 256 MiB write) between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16x6|fp32|fp64]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+    python bench.py --mode batch ...       # 64 seeded uneven instances under one captured CUDA graph
+    python bench.py --mode serve ...       # Poisson request stream through the continuous-batching server
 
 N > 1 (torchrun, one process per GPU) runs independent replicas: the step has no
 data-path exchange, so each rank advances its own copy and `value` sums them.
@@ -143,6 +145,117 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def uneven_instances(count, seed=0):
+    """The uneven-instance mix: Nz in {512, 1024, 2048, 4096} (powers of two: this build's z transform),
+    even Nr in [64, 512], M in {1, 2, 3}, order 8 or 16, m = 1 pulse with waist 10-40 dr, seeded current."""
+    from paper_2605_12132_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        Nz = int(rng.choice([512, 1024, 2048, 4096]))
+        Nr = 2 * int(rng.integers(32, 257))
+        M = int(rng.integers(1, 4))
+        order = int(rng.choice([8, 16]))
+        waist = float(rng.uniform(10, 40)) * 0.25
+        out.append(dict(Nz=Nz, Nr=Nr, M=M, order=order, waist=waist, seed=seed * 1000 + k))
+    return out
+
+
+def _instance_arrays(c):
+    from paper_2605_12132_gb300 import inputs
+    Nz, Nr, M = c["Nz"], c["Nr"], c["M"]
+    F = np.zeros((M + 1, 6, Nz, Nr), np.complex64)
+    F[1] = inputs.pulse_fields(Nz, Nr, 1 / 16, 1 / 4, c["waist"], 8.0)
+    for f in (0, 4, 5):
+        F[:, f, :, 0] = 0
+    J = np.stack([inputs.random_current(Nz, Nr, m, 8.0, 1e-2, c["seed"]) for m in range(M + 1)]).astype(np.complex64)
+    return F, J
+
+
+def run_batch(args):
+    """Uneven instances advanced by one captured CUDA graph; value = total cell*mode*steps/s."""
+    import concurrent.futures as cf
+    import torch
+    import paper_2605_12132_gb300 as fd
+    prec = args.precision or "bf16x3"
+    cfgs = uneven_instances(args.instances)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        plans = list(ex.map(lambda c: fd.fdetd_plan(c["Nz"], c["Nr"], c["M"], c["order"], 1 / 16, 1 / 4, 1 / 16,
+                                                     precision=prec), cfgs))
+    plan_s = time.perf_counter() - t0
+    batch = fd.FdetdBatch()
+    keep = []
+    cells = 0
+    for c, p in zip(cfgs, plans):
+        F, J = _instance_arrays(c)
+        f, j = torch.from_numpy(F).cuda(), torch.from_numpy(J).cuda()
+        keep.append((f, j))
+        batch.add(p, f, j)
+        cells += c["Nz"] * c["Nr"] * (c["M"] + 1)
+    stream = torch.cuda.current_stream()
+    batch.capture(1)
+    for _ in range(max(args.warmup, 3)):
+        batch.launch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        batch.launch()
+    b.record(stream)
+    torch.cuda.synchronize()
+    for p in plans:
+        p.status()
+    ms = a.elapsed_time(b)
+    line = {"metric": METRIC + " [uneven instances, one CUDA graph]", "value": cells * args.steps / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": prec + "-split/f32-accumulate" if prec.startswith("bf16") else prec,
+            "data": "synthetic (seeded uneven instances)",
+            "config": {"workload": f"{len(cfgs)} uneven instances", "cells_modes": cells, "precision": prec,
+                       "plan_build_s": plan_s, "graph": "one capture of one step per instance, replayed"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson stream of field- and envelope-advance requests through the continuous-batching server."""
+    import torch
+    from paper_2605_12132_gb300 import inputs, serve
+    prec = args.precision or "bf16x3"
+    cfgs = uneven_instances(2000, seed=5)
+    ew = inputs.envelope_workload("envelope_4096x256")
+    ea, eat, echi = inputs.envelope_inputs(ew)
+
+    def make(i, rng):
+        if rng.random() < 0.5:
+            c = cfgs[i % len(cfgs)]
+            F, J = _instance_arrays(c)
+            return serve.FieldRequest(c["Nz"], c["Nr"], list(range(c["M"] + 1)), c["order"], 1 / 16, 1 / 4, 1 / 16,
+                                      int(rng.integers(10, 501)), F, J, prec)
+        return serve.EnvelopeRequest(ew.Nz, ew.Nr, ew.order, ew.taylor_order, ew.dz, ew.dr, ew.dt,
+                                     int(rng.integers(10, 501)), np.stack([ea, eat]), echi)
+
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    srv = serve.Server(budget, chunk_steps=32)
+    t0 = time.perf_counter()
+    tickets = serve.run_poisson(srv, make, args.rate, args.duration, seed=11)
+    wall = time.perf_counter() - t0
+    srv.close()
+    cell_steps = 0
+    for t in tickets:
+        r = t.request
+        cell_steps += r.Nz * r.Nr * (len(r.modes) if r.kind == "field" else 1) * r.steps
+    st = serve.latency_stats(tickets)
+    line = {"metric": "served cell*mode*steps/s and request latency (continuous batching)",
+            "value": cell_steps / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "latency": st, "requests": len(tickets), "rate_hz": args.rate, "duration_s": args.duration,
+            "wall_s": wall, "hbm_budget_bytes": budget, "peak_admitted_bytes": srv.peak_used,
+            "config": {"workload": "Poisson mix of field (uneven sizes, 10-500 steps) and 4096x256 envelope requests",
+                       "precision": prec}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +267,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--duration", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -165,6 +282,10 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import torch
     import paper_2605_12132_gb300 as fd

@@ -185,6 +185,11 @@ def gather(cols):
     return np.concatenate([c[1:] if s else c for c, s in zip(cols, STAGGERED_R)])
 
 
+def gather_field(col, f):
+    """Unknowns of field f (0..5) of a [6][Nr] column (drops the axis slot of staggered-grid fields)."""
+    return col[f][1:] if STAGGERED_R[f] else col[f]
+
+
 def scatter(x, Nr):
     out = np.zeros((6, Nr), complex)
     o = 0

@@ -28,7 +28,7 @@ static df to_df(double x) {
 }
 
 struct fdetd_plan_s {
-  int Nz = 0, Nr = 0, nmodes = 0, order = 0, precision = 0, logNz = 0;
+  int Nz = 0, Nr = 0, nmodes = 0, order = 0, precision = 0, logNz = 0, tw_count = 0;
   double dz = 0, dr = 0, dt = 0;
   std::vector<int> modes;
   void* d_P = nullptr;
@@ -38,6 +38,7 @@ struct fdetd_plan_s {
   void* d_lam = nullptr;
   void* d_tw = nullptr;
   void* d_coef = nullptr;
+  void* d_src = nullptr;     // kz-space source term of the two-kernel spectral path (long Nz)
   int* d_err = nullptr;      // device-side failure code (bounded waits that expired)
   void* d_hostio = nullptr;  // staging for fdetd_step_host (lazy)
   size_t hostio_bytes = 0;
@@ -79,7 +80,8 @@ static void prof_collect(fdetd_plan_s* p) {
 static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
-  void* ptrs[] = {p->d_P, p->d_Q, p->d_phase, p->d_zsym, p->d_lam, p->d_tw, p->d_coef, p->d_hostio, p->d_err};
+  void* ptrs[] = {p->d_P,    p->d_Q,      p->d_phase, p->d_zsym, p->d_lam,
+                  p->d_tw,   p->d_coef,   p->d_src,   p->d_hostio, p->d_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -215,24 +217,31 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     } else {
       if ((e = upload(&p->d_zsym, zf.data(), Nz * sizeof(ZSymF), p->bytes)) != cudaSuccess) goto cuda_fail;
     }
-    const double pi = 3.14159265358979323846;
-    std::vector<double> twd(2 * Nz);
-    std::vector<float> twf(2 * Nz);
-    for (int k = 0; k < Nz; ++k) {
-      const double ang = -2.0 * pi * (double)k / Nz;
-      twd[2 * k] = std::cos(ang);
-      twd[2 * k + 1] = std::sin(ang);
-      twf[2 * k] = (float)twd[2 * k];
-      twf[2 * k + 1] = (float)twd[2 * k + 1];
+    const int prec_k = fp64 ? 0 : 1;
+    p->tw_count = spectral_twiddles(Nz, prec_k, nullptr, nullptr);
+    std::vector<double> tre(p->tw_count + 1), tim(p->tw_count + 1);
+    spectral_twiddles(Nz, prec_k, tre.data(), tim.data());
+    std::vector<double> twd(2 * (p->tw_count + 1));
+    std::vector<float> twf(2 * (p->tw_count + 1));
+    for (int k = 0; k < p->tw_count; ++k) {
+      twd[2 * k] = tre[k];
+      twd[2 * k + 1] = tim[k];
+      twf[2 * k] = (float)tre[k];
+      twf[2 * k + 1] = (float)tim[k];
     }
     if (fp64) {
-      if ((e = upload(&p->d_tw, twd.data(), 2 * Nz * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
+      if ((e = upload(&p->d_tw, twd.data(), twd.size() * 8, p->bytes)) != cudaSuccess) goto cuda_fail;
     } else {
-      if ((e = upload(&p->d_tw, twf.data(), 2 * Nz * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
+      if ((e = upload(&p->d_tw, twf.data(), twf.size() * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
     }
     const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
     if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
     p->bytes += cbytes;
+    if (spectral_needs_source(Nz, prec_k, p->tw_count)) {
+      const size_t sbytes = (size_t)nmodes * 2 * 3 * n * Nz * (fp64 ? 16 : 8);
+      if ((e = cudaMalloc(&p->d_src, sbytes)) != cudaSuccess) goto cuda_fail;
+      p->bytes += sbytes;
+    }
   }
   *out = p;
   return FDETD_OK;
@@ -263,10 +272,12 @@ extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nstep
   sa.zsym = p->d_zsym;
   sa.lam = p->d_lam;
   sa.twiddle = p->d_tw;
+  sa.tw_count = p->tw_count;
   sa.split_out = p->tc ? tc_split_buffer(p->tc) : nullptr;
   sa.npieces = p->precision == FDETD_PREC_BF16X3 ? 2 : 3;
   sa.split_rows = p->tc ? tc_split_rows(p->tc) : 0;
   sa.err = p->d_err;
+  sa.src = p->d_src;
   sa.Nz = p->Nz;
   sa.logNz = p->logNz;
   sa.n = p->Nr;
@@ -330,7 +341,7 @@ extern "C" size_t fdetd_plan_device_bytes(fdetd_plan_t p) { return p ? p->bytes 
 
 extern "C" int fdetd_plan_launches_per_step(fdetd_plan_t p) {
   if (!p) return 0;
-  return (p->tc ? tc_launches_per_step(p->tc) : 2) + 1;
+  return (p->tc ? tc_launches_per_step(p->tc) : 2) + (p->d_src ? 2 : 1);  // + source kernel when split
 }
 
 extern "C" int fdetd_plan_status(fdetd_plan_t p, void* stream) {

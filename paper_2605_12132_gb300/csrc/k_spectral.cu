@@ -172,41 +172,35 @@ __device__ __forceinline__ void dft_small(C* v) {
 // 8 elements), which keeps every Stockham pass at most 2-way bank-conflicted.
 __device__ __forceinline__ int padx(int i) { return i + (i >> 3); }
 
-// Twiddle exp(-2 pi i m / N) from two small shared tables: lo[m & 63] * hi[m >> 6].
-template <typename C>
-__device__ __forceinline__ C twiddle(const C* lo, const C* hi, int m) {
-  return cmul(hi[m >> 6], lo[m & 63]);
-}
 
-// One in-place Stockham pass of radix RR over arrays a0 .. a0+na-1 of length N (sub-sequence
+// One in-place Stockham pass of radix RR over arrays a0 .. a0+na-1 of length N = 2^logN (sub-sequence
 // length Ns before the pass).  Every butterfly of the group is read into registers before the
 // barrier and written after it, so source and destination layouts may differ: SRC_PAD = false reads
 // the unpadded arrays left by the bulk copy (array a at a*N), otherwise arrays sit at a*(N + N/8)
-// in the padded layout.  MAXB bounds the butterflies per thread.
+// in the padded layout.  tw points at this pass's twiddle table: entry k*(RR-1) + r-1 holds
+// exp(-2 pi i r k / (Ns RR)) for k < Ns.  MAXB bounds the butterflies per thread.
 template <int RR, bool INV, int NT, int MAXB, bool SRC_PAD, typename C>
-__device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int N, int Ns, const C* lo, const C* hi) {
-  const int nbf = N / RR;
-  const int total = na * nbf;
-  const int stride = N / (Ns * RR);
+__device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int logN, int Ns, const C* tw) {
+  constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
+  const int N = 1 << logN;
+  const int lnbf = logN - LR, nbf = 1 << lnbf;
+  const int total = na << lnbf;
   const int P = N + (N >> 3);
   C v[MAXB][RR];
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
     const int b = threadIdx.x + i * NT;
     if (b < total) {
-      const int a = a0 + b / nbf, j = b % nbf;
+      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
 #pragma unroll
       for (int r = 0; r < RR; ++r) {
-        const int li = j + r * nbf;
+        const int li = j + (r << lnbf);
         v[i][r] = SRC_PAD ? s[a * P + padx(li)] : s[a * N + li];
       }
-      const int k = j & (Ns - 1);
       if (Ns > 1) {
+        const C* t = tw + (j & (Ns - 1)) * (RR - 1);
 #pragma unroll
-        for (int r = 1; r < RR; ++r) {
-          const C w = twiddle(lo, hi, (r * k) * stride);
-          v[i][r] = INV ? cmulconj(v[i][r], w) : cmul(v[i][r], w);
-        }
+        for (int r = 1; r < RR; ++r) v[i][r] = INV ? cmulconj(v[i][r], t[r - 1]) : cmul(v[i][r], t[r - 1]);
       }
       dft_small<RR, INV>(v[i]);
     }
@@ -216,7 +210,7 @@ __device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int N, int N
   for (int i = 0; i < MAXB; ++i) {
     const int b = threadIdx.x + i * NT;
     if (b < total) {
-      const int a = a0 + b / nbf, j = b % nbf;
+      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
       const int k = j & (Ns - 1);
       C* x = s + a * P;
       const int base = (j - k) * RR + k;
@@ -231,44 +225,46 @@ __device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int N, int N
 // the groups last-first: group g's padded destination [g0 P, g1 P) then never overlaps the unpadded
 // source [0, g0 N) of the groups still to be read (P > N).
 template <int RR, bool INV, int NT, int MAXB, int G, bool SRC_PAD, typename C>
-__device__ __forceinline__ void pass_all(C* s, int narr, int N, int Ns, const C* lo, const C* hi) {
+__device__ __forceinline__ void pass_all(C* s, int narr, int logN, int Ns, const C* tw) {
   const int ng = (narr + G - 1) / G;
   for (int gi = 0; gi < ng; ++gi) {
     const int g = SRC_PAD ? gi : ng - 1 - gi;
     const int a0 = g * G, na = min(G, narr - a0);
-    stockham_pass<RR, INV, NT, MAXB, SRC_PAD>(s, a0, na, N, Ns, lo, hi);
+    stockham_pass<RR, INV, NT, MAXB, SRC_PAD>(s, a0, na, logN, Ns, tw);
   }
 }
 
 // Full FFT of narr arrays (forward or inverse, unnormalised), result in the padded layout:
 // one small-radix pass first when log2 N is not a multiple of log2 R, then radix-R passes.
-// MAXB = G butterflies of radix R per thread (NT >= N / R).
-template <int R, bool INV, int NT, int G, bool SRC_PAD, typename C>
-__device__ void fft_all(C* s, int narr, int N, int logN, const C* lo, const C* hi) {
+// The per-pass twiddle tables are stored back to back in pass order (first pass has none).
+// Arrays go G at a time; each thread owns BPT radix-R butterflies per array per pass.
+template <int R, bool INV, int NT, int G, int BPT, bool SRC_PAD, typename C>
+__device__ void fft_all(C* s, int narr, int logN, const C* tw) {
   const int lr = R == 8 ? 3 : 2;
   int Ns = 1;
   const int rem = logN % lr;
   bool from_pad = SRC_PAD;
   if (rem == 1) {
     if (from_pad)
-      pass_all<2, INV, NT, G*(R / 2), G, true>(s, narr, N, Ns, lo, hi);
+      pass_all<2, INV, NT, G * BPT * (R / 2), G, true>(s, narr, logN, Ns, tw);
     else
-      pass_all<2, INV, NT, G*(R / 2), G, false>(s, narr, N, Ns, lo, hi);
+      pass_all<2, INV, NT, G * BPT * (R / 2), G, false>(s, narr, logN, Ns, tw);
     Ns *= 2;
     from_pad = true;
   } else if (rem == 2) {
     if (from_pad)
-      pass_all<4, INV, NT, G*(R / 4), G, true>(s, narr, N, Ns, lo, hi);
+      pass_all<4, INV, NT, G * BPT * (R / 4), G, true>(s, narr, logN, Ns, tw);
     else
-      pass_all<4, INV, NT, G*(R / 4), G, false>(s, narr, N, Ns, lo, hi);
+      pass_all<4, INV, NT, G * BPT * (R / 4), G, false>(s, narr, logN, Ns, tw);
     Ns *= 4;
     from_pad = true;
   }
   for (int p = 0; p < logN / lr; ++p) {
     if (from_pad)
-      pass_all<R, INV, NT, G, G, true>(s, narr, N, Ns, lo, hi);
+      pass_all<R, INV, NT, G * BPT, G, true>(s, narr, logN, Ns, tw);
     else
-      pass_all<R, INV, NT, G, G, false>(s, narr, N, Ns, lo, hi);
+      pass_all<R, INV, NT, G * BPT, G, false>(s, narr, logN, Ns, tw);
+    if (Ns > 1) tw += Ns * (R - 1);
     from_pad = true;
     Ns *= R;
   }
@@ -276,22 +272,33 @@ __device__ void fft_all(C* s, int narr, int N, int logN, const C* lo, const C* h
 
 }  // namespace
 
-// T: data real type; K: coefficient type (double or df); PH / ZS: table records;
-// R: FFT radix; NT: threads; MAXB: radix-R butterflies per thread per pass.
-template <typename T, typename K, typename PH, typename ZS, int R, int NT, int MAXB, bool SPLIT_OUT>
+// Kernel modes: FUSED transforms the family's field and current columns together; SOURCE
+// transforms only the current columns and writes the midpoint source term (with the 1/Nz of the
+// inverse transform) in kz space; MAIN transforms the field columns and adds that precomputed
+// source (used when five columns do not fit in shared memory).
+enum { FUSED = 0, MAIN = 1, SOURCE = 2 };
+
+// T: data real type; K: coefficient type (double or df); PH / ZS: table records; R: FFT radix;
+// NT: threads; G: arrays per pass group; BPT: radix-R butterflies per thread per array;
+// TW_SMEM: twiddle tables copied to shared memory (else read through L1).
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT_OUT, int MODE,
+          bool TW_SMEM>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(SpectralArgs args) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t load_bar;
-  __shared__ C tw_lo[64], tw_hi[64];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int Nz = args.Nz, L = args.logNz, n = args.n;
   const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
-  const bool hasJ = args.hasJ;
+  const bool hasJ = MODE == FUSED ? args.hasJ : false;
   // coefficient array indices: E group (e, a, c), B group (b, d, f), J (eJ, aJ, cJ)
   int idx[5];
   int narr;
-  if (fam == 0) {
+  if (MODE == SOURCE) {
+    idx[0] = fam == 0 ? 6 : 8;
+    idx[1] = 7;
+    narr = fam == 0 ? 2 : 1;
+  } else if (fam == 0) {
     idx[0] = 0; idx[1] = 1; idx[2] = 3; idx[3] = 6; idx[4] = 7;
     narr = hasJ ? 5 : 3;
   } else {
@@ -299,61 +306,88 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
     narr = hasJ ? 4 : 3;
   }
   const C* coef = reinterpret_cast<const C*>(args.coef);
-  const C* tw = reinterpret_cast<const C*>(args.twiddle);
-  // the family's coefficient columns are contiguous in global memory: one bulk copy each into
-  // shared memory (unpadded), completing on one mbarrier; the first FFT pass re-lays them out padded
+  const C* twg = reinterpret_cast<const C*>(args.twiddle);
+  const int P = Nz + (Nz >> 3);
+  const int maxarr = MODE == FUSED ? 5 : (MODE == MAIN ? 3 : 2);
+  const C* tw = TW_SMEM ? s + (size_t)maxarr * P : twg;
+  // the family's columns are contiguous in global memory: one bulk copy each into shared memory
+  // (unpadded; the first FFT pass re-lays them out padded), completing on one mbarrier
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&load_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     const uint32_t col = (uint32_t)(Nz * sizeof(C));
+    const uint32_t twb = TW_SMEM ? (uint32_t)(args.tw_count * sizeof(C)) : 0u;
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
                      smem_addr(&load_bar)),
-                 "r"(narr * col)
+                 "r"(narr * col + twb)
                  : "memory");
     for (int a = 0; a < narr; ++a)
       bulk_g2s(s + (size_t)a * Nz, coef + ((size_t)(md * 9 + idx[a]) * n + j) * Nz, col, &load_bar);
-  }
-  // two-level twiddle tables: lo[m] = W^m (m < 64), hi[m] = W^(64 m) (m < Nz / 64)
-  for (int m = threadIdx.x; m < 64; m += NT) {
-    tw_lo[m] = tw[m & (Nz - 1)];
-    tw_hi[m] = tw[(64 * m) & (Nz - 1)];
+    if (TW_SMEM) bulk_g2s(const_cast<C*>(tw), twg, twb, &load_bar);
   }
   __syncthreads();
   if (!bar_wait(&load_bar, 0)) {
     if (threadIdx.x == 0 && args.err) atomicCAS(args.err, 0, 8);
     return;
   }
-  const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
-  fft_all<R, false, NT, MAXB, false>(s, narr, Nz, L, tw_lo, tw_hi);  // MAXB = array group size
+  fft_all<R, false, NT, G, BPT, false>(s, narr, L, tw);
   // exact rotation per kz (the 1/Nz of the inverse transform folded in)
+  const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
   const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
   const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
   const T dt = (T)args.dt;
   const T inv = (T)1 / (T)Nz;
-  const int PS = Nz + (Nz >> 3);
+  C* src = reinterpret_cast<C*>(args.src) + ((size_t)(md * 2 + fam) * 3 * n + j) * Nz;  // [md][fam][3][n][Nz]
+  const size_t sstride = (size_t)n * Nz;
   for (int q = threadIdx.x; q < Nz; q += NT) {
     const int pq = padx(q);
     K spr, spi, smr, smi, A1, A2;
     T B1, B2;
     zsym_unpack(zs[q], spr, spi, smr, smi);
     phase_unpack(phase[q], A1, A2, B1, B2);
-    C x0 = s[pq], x1 = s[PS + pq], x2 = s[2 * PS + pq];
+    C y0, y1, y2, z0, z1, z2;
+    if (MODE == SOURCE) {
+      C j0 = s[pq], j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
+      if (fam == 0) j1 = s[P + pq];
+      if (fam == 0) {
+        apply_tm(j0, j1, j2, y0, y1, y2, lam, spr, spi, smr, smi);
+        apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
+      } else {
+        apply_te(j0, j1, j2, y0, y1, y2, lam, spr, spi, smr, smi);
+        apply_te(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
+      }
+      const T f = -dt * inv;
+      const C jj[3] = {j0, j1, j2}, yy[3] = {y0, y1, y2}, zz[3] = {z0, z1, z2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C v = cadd(jj[c], cadd(cscale(B1, yy[c]), cscale(B2, zz[c])));
+        v.x *= f;
+        v.y *= f;
+        src[c * sstride + q] = v;
+      }
+      continue;
+    }
+    C x0 = s[pq], x1 = s[P + pq], x2 = s[2 * P + pq];
     C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
     if (hasJ) {
-      j0 = s[3 * PS + pq];
-      if (fam == 0) j1 = s[4 * PS + pq];
+      j0 = s[3 * P + pq];
+      if (fam == 0) j1 = s[4 * P + pq];
     }
-    C y0, y1, y2, z0, z1, z2, yj0, yj1, yj2, zj0, zj1, zj2;
+    C yj0, yj1, yj2, zj0, zj1, zj2;
     if (fam == 0) {
       apply_tm(x0, x1, x2, y0, y1, y2, lam, spr, spi, smr, smi);
       apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
-      apply_tm(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
-      apply_tm(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
+      if (hasJ) {
+        apply_tm(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
+        apply_tm(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
+      }
     } else {
       apply_te(x0, x1, x2, y0, y1, y2, lam, spr, spi, smr, smi);
       apply_te(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
-      apply_te(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
-      apply_te(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
+      if (hasJ) {
+        apply_te(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
+        apply_te(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
+      }
     }
     C r0 = combine(x0, y0, z0, A1, A2, j0, yj0, zj0, B1, B2, dt, hasJ);
     C r1 = combine(x1, y1, z1, A1, A2, j1, yj1, zj1, B1, B2, dt, hasJ);
@@ -361,23 +395,29 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
     r0.x *= inv; r0.y *= inv;
     r1.x *= inv; r1.y *= inv;
     r2.x *= inv; r2.y *= inv;
+    if (MODE == MAIN && args.src) {
+      r0 = cadd(r0, src[q]);
+      r1 = cadd(r1, src[sstride + q]);
+      r2 = cadd(r2, src[2 * sstride + q]);
+    }
     s[pq] = r0;
-    s[PS + pq] = r1;
-    s[2 * PS + pq] = r2;
+    s[P + pq] = r1;
+    s[2 * P + pq] = r2;
   }
+  if (MODE == SOURCE) return;
   __syncthreads();
-  fft_all<R, true, NT, MAXB, true>(s, 3, Nz, L, tw_lo, tw_hi);
+  fft_all<R, true, NT, G, BPT, true>(s, 3, L, tw);
   if (!SPLIT_OUT) {
     C* out = reinterpret_cast<C*>(args.coef);
     for (int a = 0; a < 3; ++a) {
       C* dst = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
-      const C* x = s + (size_t)a * PS;
+      const C* x = s + (size_t)a * P;
       for (int z = threadIdx.x; z < Nz; z += NT) dst[z] = x[padx(z)];
     }
   } else {
     // bf16 split pieces for the tensor-core back-projection (re, im interleaved along z)
     for (int a = 0; a < 3; ++a) {
-      const C* x = s + (size_t)a * PS;
+      const C* x = s + (size_t)a * P;
       for (int z = threadIdx.x; z < Nz; z += NT) {
         const C v = x[padx(z)];
         split_store(args.split_out, args.npieces, md, idx[a], j, z, args.split_rows, Nz, (float)v.x, (float)v.y);
@@ -386,12 +426,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   }
 }
 
-template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT>
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT, int MODE,
+          bool TW_SMEM>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
-  constexpr int MAXB = 3;  // arrays per FFT pass group = radix-R butterflies per thread (NT >= Nz / R)
-  const size_t smem = spectral_smem_bytes(a.Nz, sizeof(T) == 8 ? 0 : 1, a.hasJ);
-  auto k = spectral_kernel<T, K, PH, ZS, R, NT, MAXB, SPLIT>;
+  const int arrays = MODE == FUSED ? (a.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);
+  const size_t smem = ((size_t)arrays * (a.Nz + a.Nz / 8) + (TW_SMEM ? (size_t)a.tw_count : 0)) * sizeof(C);
+  auto k = spectral_kernel<T, K, PH, ZS, R, NT, G, BPT, SPLIT, MODE, TW_SMEM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.n, 2, nmodes);
@@ -399,25 +440,82 @@ static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st
   return cudaGetLastError();
 }
 
-// Threads per block: NT = max(128, 5 Nz / (R * MAXB)) with MAXB = 5 butterflies per thread.
-template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT>
+// Configuration by transform length: NT = max(128, Nz / R) threads up to 512, groups of three arrays
+// while one butterfly per thread per array suffices; beyond that one array at a time with two.
+template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT, int MODE, bool TW_SMEM>
 static cudaError_t launch_sized(const SpectralArgs& a, int nmodes, cudaStream_t st) {
-  const int need = a.Nz / R;  // threads for MAXB = 5 with 5 arrays
-  if (need <= 128) return launch_one<T, K, PH, ZS, R, 128, SPLIT>(a, nmodes, st);
-  if (need <= 256) return launch_one<T, K, PH, ZS, R, 256, SPLIT>(a, nmodes, st);
-  if (need <= 512) return launch_one<T, K, PH, ZS, R, 512, SPLIT>(a, nmodes, st);
-  return cudaErrorNotSupported;  // plans reject such Nz (shared-memory capacity)
+  const int need = a.Nz / R;
+  if (need <= 128) return launch_one<T, K, PH, ZS, R, 128, 3, 1, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
+  if (need <= 256) return launch_one<T, K, PH, ZS, R, 256, 3, 1, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
+  if (need <= 512) return launch_one<T, K, PH, ZS, R, 512, 3, 1, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
+  if (need <= 1024) return launch_one<T, K, PH, ZS, R, 512, 1, 2, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
+  return cudaErrorNotSupported;
+}
+
+static size_t fused_bytes(int Nz, int precision, bool hasJ, int tw_count) {
+  return ((size_t)(hasJ ? 5 : 3) * (Nz + Nz / 8) + (size_t)tw_count) * (precision == 0 ? 16 : 8);
+}
+
+template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT>
+static cudaError_t launch_prec(const SpectralArgs& a, int nmodes, cudaStream_t st) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  if (fused_bytes(a.Nz, prec, a.hasJ, a.tw_count) <= 227 * 1024)
+    return launch_sized<T, K, PH, ZS, R, SPLIT, FUSED, true>(a, nmodes, st);
+  // two kernels: the current's source term first, then the field columns alone (twiddles via L1)
+  if (a.hasJ) {
+    if (!a.src) return cudaErrorInvalidValue;
+    cudaError_t e = launch_sized<T, K, PH, ZS, R, SPLIT, SOURCE, false>(a, nmodes, st);
+    if (e != cudaSuccess) return e;
+    return launch_sized<T, K, PH, ZS, R, SPLIT, MAIN, false>(a, nmodes, st);
+  }
+  SpectralArgs b = a;
+  b.src = nullptr;
+  return launch_sized<T, K, PH, ZS, R, SPLIT, MAIN, false>(b, nmodes, st);
 }
 
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st) {
-  if (precision == 0) return launch_sized<double, double, PhaseD, ZSymD, 4, false>(a, nmodes, st);
-  if (split_out) return launch_sized<float, df, PhaseF, ZSymF, 8, true>(a, nmodes, st);
-  return launch_sized<float, df, PhaseF, ZSymF, 8, false>(a, nmodes, st);
+  if (precision == 0) return launch_prec<double, double, PhaseD, ZSymD, 4, false>(a, nmodes, st);
+  if (split_out) return launch_prec<float, df, PhaseF, ZSymF, 8, true>(a, nmodes, st);
+  return launch_prec<float, df, PhaseF, ZSymF, 8, false>(a, nmodes, st);
 }
 
-// coefficient columns of the family (5 with a current, else 3) in the padded layout (9/8)
+bool spectral_needs_source(int Nz, int precision, int tw_count) {
+  return fused_bytes(Nz, precision, true, tw_count) > 227 * 1024;
+}
+
+// Smallest shared-memory footprint a plan needs: the three field columns of the two-kernel path
+// (padded layout, twiddles through L1).  The fused path is used whenever it fits.
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ) {
-  return (size_t)(hasJ ? 5 : 3) * (Nz + Nz / 8) * (precision == 0 ? 16 : 8);
+  (void)hasJ;
+  return (size_t)3 * (Nz + Nz / 8) * (precision == 0 ? 16 : 8);
+}
+
+// Per-pass twiddle tables in the order fft_all consumes them, for radix R (8 for FP32, 4 for FP64):
+// the first (small-radix) pass needs none; pass p with sub-length Ns and radix R stores
+// exp(-2 pi i r k / (Ns R)) at k*(R-1) + r-1 for k < Ns, r = 1..R-1.
+int spectral_twiddles(int Nz, int precision, double* re, double* im) {
+  const int R = precision == 0 ? 4 : 8, lr = precision == 0 ? 2 : 3;
+  int logN = 0;
+  while ((1 << logN) < Nz) ++logN;
+  int Ns = 1 << (logN % lr), cnt = 0;
+  const double pi = 3.14159265358979323846;
+  for (int p = 0; p < logN / lr; ++p) {
+    if (Ns > 1) {
+      for (int k = 0; k < Ns; ++k)
+        for (int r = 1; r < R; ++r) {
+          // reduce the angle exactly: r k / (Ns R) of a full turn
+          const long long num = ((long long)r * k) % ((long long)Ns * R);
+          const double ang = -2.0 * pi * (double)num / ((double)Ns * R);
+          if (re) {
+            re[cnt] = cos(ang);
+            im[cnt] = sin(ang);
+          }
+          ++cnt;
+        }
+    }
+    Ns *= R;
+  }
+  return cnt;
 }
 
 }  // namespace fdetd

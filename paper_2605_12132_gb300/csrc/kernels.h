@@ -12,7 +12,8 @@ struct SpectralArgs {
   const void* phase;     // [nmodes][2][n][Nz] PhaseD / PhaseF
   const void* zsym;      // [Nz] ZSymD / ZSymF
   const void* lam;       // [nmodes][2][n] double / df (lambda for TM, mu for TE)
-  const void* twiddle;   // [Nz] complex<T>, exp(-2 pi i k / Nz)
+  const void* twiddle;   // per-pass twiddle tables (spectral_twiddles), complex<T>
+  int tw_count;          // entries in `twiddle`
   __nv_bfloat16* split_out;  // tensor-core path: [nmodes][npieces][6][split_rows][2 Nz]
   int npieces;
   int split_rows;            // coefficient rows per block in split_out (n padded to the K tile)
@@ -20,10 +21,13 @@ struct SpectralArgs {
   double dt;
   int hasJ;
   int* err;              // device failure flag (bounded waits)
+  void* src;             // [nmodes][2][3][n][Nz] complex<T>: kz-space source term (two-kernel path)
 };
 
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ);
+int spectral_twiddles(int Nz, int precision, double* re, double* im);
+bool spectral_needs_source(int Nz, int precision, int tw_count);
 
 // bf16 split of an FP32 value into npieces (2 or 3) terms whose sum reproduces it to
 // 16 / 24 significant bits; piece p of coefficient array c goes to

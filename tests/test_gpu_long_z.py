@@ -1,0 +1,47 @@
+"""Long z columns (two-kernel spectral path: the current's source term is transformed first, then the
+field columns alone) against the oracle on sampled kz columns, with and without a current."""
+import numpy as np
+import pytest
+
+from oracle import maxwell as mx
+from paper_2605_12132_gb300 import inputs
+from tests.gpu_util import zero_axis
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2605_12132_gb300 as fd  # noqa: E402
+
+TOL = {"fp64": 1e-12, "fp32": 1e-6, "bf16x6": 4e-6, "bf16x3": 2.5e-5}
+
+
+@pytest.mark.parametrize("prec,Nz", [("fp32", 8192), ("bf16x3", 8192), ("bf16x6", 8192), ("fp64", 4096)])
+@pytest.mark.parametrize("with_J", [True, False])
+def test_long_z_sampled_kz(prec, Nz, with_J):
+    rng = np.random.default_rng(Nz + with_J)
+    Nr, modes, order, dz, dr, dt = 48, [0, 1], 16, 1 / 16, 1 / 4, 1 / 16
+    F = np.zeros((2, 6, Nz, Nr), complex)
+    F[1] = inputs.pulse_fields(Nz, Nr, dz, dr, 3.0, 8.0)
+    F += 1e-3 * (rng.standard_normal(F.shape) + 1j * rng.standard_normal(F.shape))
+    F = zero_axis(F)
+    J = np.stack([inputs.random_current(Nz, Nr, m, 8.0, 1e-2, 3) for m in modes]) if with_J else None
+    plan = fd.fdetd_plan_modes(Nz, Nr, modes, order, dz, dr, dt, precision=prec)
+    f = torch.from_numpy(F).to(plan.complex_dtype).cuda()
+    j = torch.from_numpy(J).to(plan.complex_dtype).cuda() if with_J else None
+    nsteps = 2
+    fd.fdetd_step(plan, f, j, nsteps)
+    plan.status()
+    G = f.cpu().numpy().astype(np.complex128)
+    qs = [0, 1, Nz // 16, Nz // 2, int(rng.integers(2, Nz // 2))]
+    for i, m in enumerate(modes):
+        ref = mx.step_spectral(F[i], None if J is None else J[i], Nz, Nr, m, order, dz, dr, dt, nsteps=nsteps,
+                               kz_subset=qs, method="expm")
+        Gh = np.fft.fft(G[i], axis=1)
+        col_scale = np.linalg.norm(Gh) / np.sqrt(Nz)
+        for q in qs:
+            err = np.linalg.norm(mx.gather(Gh[:, q, :]) - mx.gather(ref[q])) / max(np.linalg.norm(mx.gather(ref[q])),
+                                                                                 col_scale)
+            assert err < TOL[prec] * nsteps * 2, (prec, m, q, err)
