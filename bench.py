@@ -87,6 +87,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(loaded)}
 
 
+STAGE_SOURCE = {"projection": "k_tc.cu", "spectral": "k_spectral.cu", "backprojection": "k_tc.cu"}
+
+
+def recorded_traffic(stage, workload, prec):
+    """DRAM bytes per launch of a stage's kernel from profiles/traffic.json (one ncu capture), or None
+    when no capture exists for this workload/precision or the kernel source changed since (sha256)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[f"{stage}/{workload}/{prec}"]
+        src = os.path.join(ROOT, "paper_2605_12132_gb300", "csrc", STAGE_SOURCE[stage])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def gemm_flops(w, hasJ):
     """Algorithmic FLOPs of one step's radial transforms: each nonzero n x n block of the
     (3n)^2 projection / back-projection matrices times a complex column, per z row and mode."""
@@ -398,7 +415,8 @@ def main():
             pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if prec == "fp32" else 1.25
             roof = {"bound": "alu", "achieved": algo / per_launch_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = recorded_traffic(stage, w.name, prec)
+    roof["algorithmic"] = algo
     roof["kernel"] = stage
     roof["peak_source"] = src
     roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in ktimes.items()}

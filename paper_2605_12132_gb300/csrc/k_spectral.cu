@@ -221,6 +221,42 @@ __device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int logN, in
   __syncthreads();
 }
 
+// The last radix-RR pass of the inverse transform of the three field columns, storing straight to
+// global memory: with Ns = N / RR a butterfly j writes z = j + r N/RR, consecutive across threads.
+template <int RR, int NT, int MAXB, bool SPLIT_OUT, typename C>
+__device__ __forceinline__ void last_pass_to_global(const C* s, int logN, const C* tw, C* const* dst,
+                                                    const SpectralArgs& args, const int* cidx, int md, int jcol) {
+  constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
+  const int N = 1 << logN;
+  const int lnbf = logN - LR, nbf = 1 << lnbf;
+  const int total = 3 << lnbf;
+  const int P = N + (N >> 3);
+  const int Ns = nbf;
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int a = b >> lnbf, j = b & (nbf - 1);
+      C v[RR];
+#pragma unroll
+      for (int r = 0; r < RR; ++r) v[r] = s[a * P + padx(j + (r << lnbf))];
+      const C* t = tw + j * (RR - 1);
+#pragma unroll
+      for (int r = 1; r < RR; ++r) v[r] = cmulconj(v[r], t[r - 1]);
+      dft_small<RR, true>(v);
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const int z = j + r * Ns;
+        if (!SPLIT_OUT)
+          dst[a][z] = v[r];
+        else
+          split_store(args.split_out, args.npieces, md, cidx[a], jcol, z, args.split_rows, N, (float)v[r].x,
+                      (float)v[r].y);
+      }
+    }
+  }
+}
+
 // One pass over all narr arrays in groups of at most G.  A pass that reads the unpadded layout walks
 // the groups last-first: group g's padded destination [g0 P, g1 P) then never overlaps the unpadded
 // source [0, g0 N) of the groups still to be read (P > N).
@@ -238,8 +274,8 @@ __device__ __forceinline__ void pass_all(C* s, int narr, int logN, int Ns, const
 // one small-radix pass first when log2 N is not a multiple of log2 R, then radix-R passes.
 // The per-pass twiddle tables are stored back to back in pass order (first pass has none).
 // Arrays go G at a time; each thread owns BPT radix-R butterflies per array per pass.
-template <int R, bool INV, int NT, int G, int BPT, bool SRC_PAD, typename C>
-__device__ void fft_all(C* s, int narr, int logN, const C* tw) {
+template <int R, bool INV, int NT, int G, int BPT, bool SRC_PAD, bool SKIP_LAST = false, typename C>
+__device__ const C* fft_all(C* s, int narr, int logN, const C* tw) {
   const int lr = R == 8 ? 3 : 2;
   int Ns = 1;
   const int rem = logN % lr;
@@ -259,7 +295,8 @@ __device__ void fft_all(C* s, int narr, int logN, const C* tw) {
     Ns *= 4;
     from_pad = true;
   }
-  for (int p = 0; p < logN / lr; ++p) {
+  const int npass = logN / lr - (SKIP_LAST ? 1 : 0);
+  for (int p = 0; p < npass; ++p) {
     if (from_pad)
       pass_all<R, INV, NT, G * BPT, G, true>(s, narr, logN, Ns, tw);
     else
@@ -268,6 +305,7 @@ __device__ void fft_all(C* s, int narr, int logN, const C* tw) {
     from_pad = true;
     Ns *= R;
   }
+  return tw;
 }
 
 }  // namespace
@@ -308,8 +346,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   const C* coef = reinterpret_cast<const C*>(args.coef);
   const C* twg = reinterpret_cast<const C*>(args.twiddle);
   const int P = Nz + (Nz >> 3);
-  const int maxarr = MODE == FUSED ? 5 : (MODE == MAIN ? 3 : 2);
-  const C* tw = TW_SMEM ? s + (size_t)maxarr * P : twg;
+  // column slots in shared memory; must match launch_one's sizing (the twiddles follow them)
+  const int slots = MODE == FUSED ? (args.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);
+  const C* tw = TW_SMEM ? s + (size_t)slots * P : twg;
   // the family's columns are contiguous in global memory: one bulk copy each into shared memory
   // (unpadded; the first FFT pass re-lays them out padded), completing on one mbarrier
   if (threadIdx.x == 0) {
@@ -368,30 +407,36 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
       continue;
     }
     C x0 = s[pq], x1 = s[P + pq], x2 = s[2 * P + pq];
-    C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
+    C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0);
     if (hasJ) {
       j0 = s[3 * P + pq];
       if (fam == 0) j1 = s[4 * P + pq];
     }
-    C yj0, yj1, yj2, zj0, zj1, zj2;
-    if (fam == 0) {
-      apply_tm(x0, x1, x2, y0, y1, y2, lam, spr, spi, smr, smi);
-      apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
-      if (hasJ) {
-        apply_tm(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
-        apply_tm(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
-      }
-    } else {
-      apply_te(x0, x1, x2, y0, y1, y2, lam, spr, spi, smr, smi);
-      apply_te(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
-      if (hasJ) {
-        apply_te(j0, j1, j2, yj0, yj1, yj2, lam, spr, spi, smr, smi);
-        apply_te(yj0, yj1, yj2, zj0, zj1, zj2, lam, spr, spi, smr, smi);
-      }
+    // Horner form of x + A1 M x + A2 M^2 x - dt (xJ + B1 M xJ + B2 M^2 xJ):
+    //   p = x - dt xJ,  q = A1 x - dt B1 xJ,  u = A2 x - dt B2 xJ,  r = p + M (q + M u)
+    // (x_J = (eJ, aJ, 0) for TM, (cJ, 0, 0) for TE)
+    const T dB1 = dt * B1, dB2 = dt * B2;
+    C u0 = cscale(A2, x0), u1 = cscale(A2, x1), u2 = cscale(A2, x2);
+    C q0 = cscale(A1, x0), q1 = cscale(A1, x1), q2 = cscale(A1, x2);
+    C p0 = x0, p1 = x1;
+    if (hasJ) {
+      u0.x -= dB2 * j0.x; u0.y -= dB2 * j0.y;
+      u1.x -= dB2 * j1.x; u1.y -= dB2 * j1.y;
+      q0.x -= dB1 * j0.x; q0.y -= dB1 * j0.y;
+      q1.x -= dB1 * j1.x; q1.y -= dB1 * j1.y;
+      p0.x -= dt * j0.x; p0.y -= dt * j0.y;
+      p1.x -= dt * j1.x; p1.y -= dt * j1.y;
     }
-    C r0 = combine(x0, y0, z0, A1, A2, j0, yj0, zj0, B1, B2, dt, hasJ);
-    C r1 = combine(x1, y1, z1, A1, A2, j1, yj1, zj1, B1, B2, dt, hasJ);
-    C r2 = combine(x2, y2, z2, A1, A2, j2, yj2, zj2, B1, B2, dt, hasJ);
+    if (fam == 0) {
+      apply_tm(u0, u1, u2, y0, y1, y2, lam, spr, spi, smr, smi);
+      y0 = cadd(y0, q0); y1 = cadd(y1, q1); y2 = cadd(y2, q2);
+      apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
+    } else {
+      apply_te(u0, u1, u2, y0, y1, y2, lam, spr, spi, smr, smi);
+      y0 = cadd(y0, q0); y1 = cadd(y1, q1); y2 = cadd(y2, q2);
+      apply_te(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
+    }
+    C r0 = cadd(p0, z0), r1 = cadd(p1, z1), r2 = cadd(x2, z2);
     r0.x *= inv; r0.y *= inv;
     r1.x *= inv; r1.y *= inv;
     r2.x *= inv; r2.y *= inv;
@@ -406,31 +451,20 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   }
   if (MODE == SOURCE) return;
   __syncthreads();
-  fft_all<R, true, NT, G, BPT, true>(s, 3, L, tw);
-  if (!SPLIT_OUT) {
-    C* out = reinterpret_cast<C*>(args.coef);
-    for (int a = 0; a < 3; ++a) {
-      C* dst = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
-      const C* x = s + (size_t)a * P;
-      for (int z = threadIdx.x; z < Nz; z += NT) dst[z] = x[padx(z)];
-    }
-  } else {
-    // bf16 split pieces for the tensor-core back-projection (re, im interleaved along z)
-    for (int a = 0; a < 3; ++a) {
-      const C* x = s + (size_t)a * P;
-      for (int z = threadIdx.x; z < Nz; z += NT) {
-        const C v = x[padx(z)];
-        split_store(args.split_out, args.npieces, md, idx[a], j, z, args.split_rows, Nz, (float)v.x, (float)v.y);
-      }
-    }
-  }
+  // inverse transform; the last radix-R pass writes the result (or its bf16 split pieces) to global
+  const C* twl = fft_all<R, true, NT, G, BPT, true, true>(s, 3, L, tw);
+  C* out = reinterpret_cast<C*>(args.coef);
+  C* dst[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dst[a] = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
+  last_pass_to_global<R, NT, 3 * BPT, SPLIT_OUT>(s, L, twl, dst, args, idx, md, j);
 }
 
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT, int MODE,
           bool TW_SMEM>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
-  const int arrays = MODE == FUSED ? (a.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);
+  const int arrays = MODE == FUSED ? (a.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);  // = the kernel's `slots`
   const size_t smem = ((size_t)arrays * (a.Nz + a.Nz / 8) + (TW_SMEM ? (size_t)a.tw_count : 0)) * sizeof(C);
   auto k = spectral_kernel<T, K, PH, ZS, R, NT, G, BPT, SPLIT, MODE, TW_SMEM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
