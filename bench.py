@@ -211,7 +211,10 @@ def run_batch(args):
         batch.add(p, f, j)
         cells += c["Nz"] * c["Nr"] * (c["M"] + 1)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
     batch.capture(1)
+    capture_s = time.perf_counter() - t0
+    groups = batch.groups()
     for _ in range(max(args.warmup, 3)):
         batch.launch()
     torch.cuda.synchronize()
@@ -230,7 +233,11 @@ def run_batch(args):
             "dtype": prec + "-split/f32-accumulate" if prec.startswith("bf16") else prec,
             "data": "synthetic (seeded uneven instances)",
             "config": {"workload": f"{len(cfgs)} uneven instances", "cells_modes": cells, "precision": prec,
-                       "plan_build_s": plan_s, "graph": "one capture of one step per instance, replayed"}}
+                       "plan_build_s": plan_s, "capture_s": capture_s,
+                       "graph": "per step: one persistent grouped projection and back-projection launch per "
+                                "precision group, per-instance spectral kernels on parallel branches; replayed",
+                       "groups": [{k: g[k] for k in ("instances", "tn_proj", "tn_back", "sched_proj", "sched_back",
+                                                     "proj_tiles", "back_tiles", "tuned_ms")} for g in groups]}}
     print(json.dumps(line), flush=True)
 
 
@@ -332,6 +339,10 @@ def main():
     Jd = torch.from_numpy(J).to(cdt).cuda() if J is not None else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    tiles = tuned = None
+    if prec in ("bf16x3", "bf16x6"):
+        tuned = plan.autotune(fields, Jd)       # tile shapes / schedules, timed on these arrays (read only)
+        tiles = dict(zip(("tn_proj", "tn_back", "sched_proj", "sched_back"), plan.tile_config))
 
     for _ in range(args.warmup):
         fd.fdetd_step(plan, fields, Jd, 1)
@@ -439,7 +450,7 @@ def main():
                 "config": {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order,
                            "precision": prec, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between timed steps (256 MiB write)", "fp64_value": fp64_value,
-                           "wall_s": t_wall},
+                           "wall_s": t_wall, "tiles": tiles, "autotune_ms": tuned},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)

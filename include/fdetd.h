@@ -133,20 +133,54 @@ int fdetd_plan_kernel_times(fdetd_plan_t plan, double* ms, long* calls);
 int fdetd_plan_destroy(fdetd_plan_t plan);
 
 /*
- * Batches of uneven instances advanced by one CUDA graph.
+ * Tile shapes and schedules of the tensor-core radial transforms (no counterpart in the
+ * paper; they change speed, not results: every configuration sums each output over K in
+ * the same order, so outputs are bitwise identical).
+ *
+ * cfg[4] = {N tile of the projection (128 or 256), N tile of the back-projection (128 or
+ * 256; 128 for BF16X6; Nz must be a multiple of half of it), tile order of the projection,
+ * tile order of the back-projection (0: longest tiles first, round-robin over the persistent
+ * CTAs; 1: the same in snake order)}.
+ *
+ * fdetd_plan_autotune times every valid configuration on the caller's device arrays (fields,
+ * J: as for fdetd_step; only read - the back-projection candidates write into a temporary
+ * array) on `stream`, keeps the fastest in the plan, and writes the two best times (ms per
+ * launch: projection, back-projection) to ms[2] if ms is not NULL.  Blocking (synchronises
+ * the stream); allocates a temporary array of the fields' size.  A no-op for the FP64 and
+ * FP32 precisions.  fdetd_plan_tile_config reads the plan's configuration and
+ * fdetd_plan_set_tile_config sets it (FDETD_ERR_ARG if invalid or not a tensor-core plan).
+ */
+int fdetd_plan_autotune(fdetd_plan_t plan, const void* fields, const void* J, void* stream, double* ms);
+int fdetd_plan_tile_config(fdetd_plan_t plan, int* cfg);
+int fdetd_plan_set_tile_config(fdetd_plan_t plan, const int* cfg);
+
+/*
+ * Batches of uneven instances advanced by one CUDA graph (no counterpart in the paper).
  *
  * fdetd_batch_add registers an instance (a plan with its own device fields and optional J;
  * each plan at most once per batch because its scratch buffers are private to it) and writes
  * its index to *index (may be NULL).
- * fdetd_batch_capture records `nsteps` steps of every instance into one CUDA graph, each
- * instance on its own branch (forked from and joined back into `stream`), so independent
- * instances run concurrently on the GPU; fdetd_batch_launch replays it on `stream`.
- * Re-capture after adding instances.  The pointers registered must stay valid while the
- * graph is launched.  Host-side, capture uses only stream-ordered calls (no allocation).
+ * fdetd_batch_capture groups the tensor-core instances by precision (up to 64 per group),
+ * chooses each group's tile configuration (autotuned on the registered arrays, which it
+ * only reads, unless fdetd_batch_set_autotune(batch, 0)), and records `nsteps` steps into
+ * one CUDA graph: per step one persistent grouped projection launch and one grouped
+ * back-projection launch per group, covering every (instance, mode, z tile, output tile) of
+ * the group, with each instance's spectral kernel on its own graph branch in between;
+ * instances on the CUDA-core precisions run their own step sequence on concurrent
+ * branches.  Blocking before the capture (tile tables, tuning); fdetd_batch_launch replays
+ * the graph on `stream`.  Re-capture after adding instances.  The registered pointers must
+ * stay valid while the graph is launched.
+ * fdetd_batch_group_info(batch, g, info[7], ms[2]) reports group g after a capture: info =
+ * {N tile of the projection, N tile of the back-projection, projection tile order,
+ * back-projection tile order, instances, projection tiles, back-projection tiles}, ms = the
+ * tuned times per launch (0 when not tuned); returns the number of groups (0 if none; info
+ * is left untouched when g is out of range), or -FDETD_ERR_ARG for a NULL batch or info.
  */
 int fdetd_batch_create(fdetd_batch_t* out);
 int fdetd_batch_add(fdetd_batch_t batch, fdetd_plan_t plan, void* fields, const void* J, int* index);
+int fdetd_batch_set_autotune(fdetd_batch_t batch, int on);
 int fdetd_batch_capture(fdetd_batch_t batch, int nsteps, void* stream);
+int fdetd_batch_group_info(fdetd_batch_t batch, int group, int* info, double* ms);
 int fdetd_batch_launch(fdetd_batch_t batch, void* stream);
 int fdetd_batch_destroy(fdetd_batch_t batch);
 

@@ -52,6 +52,11 @@ def lib():
     L.fdetd_batch_create.argtypes = [ctypes.POINTER(c_vp)]
     L.fdetd_batch_add.argtypes = [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_int)]
     L.fdetd_batch_capture.argtypes = [c_vp, c_int, c_vp]
+    L.fdetd_batch_set_autotune.argtypes = [c_vp, c_int]
+    L.fdetd_batch_group_info.argtypes = [c_vp, c_int, ctypes.POINTER(c_int), dp]
+    L.fdetd_plan_autotune.argtypes = [c_vp, c_vp, c_vp, c_vp, dp]
+    L.fdetd_plan_tile_config.argtypes = [c_vp, ctypes.POINTER(c_int)]
+    L.fdetd_plan_set_tile_config.argtypes = [c_vp, ctypes.POINTER(c_int)]
     L.fdetd_batch_launch.argtypes = [c_vp, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
     L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
@@ -114,6 +119,30 @@ class FdetdPlan:
         calls = (ctypes.c_long * 3)()
         _check(lib().fdetd_plan_kernel_times(self.handle, ms, calls))
         return {name: (ms[i], calls[i]) for i, name in enumerate(("projection", "spectral", "backprojection"))}
+
+    @property
+    def tile_config(self):
+        """Tensor-core tile configuration (tn_proj, tn_back, sched_proj, sched_back)."""
+        cfg = (ctypes.c_int * 4)()
+        _check(lib().fdetd_plan_tile_config(self.handle, cfg))
+        return tuple(cfg)
+
+    @tile_config.setter
+    def tile_config(self, cfg):
+        arr = (ctypes.c_int * 4)(*cfg)
+        _check(lib().fdetd_plan_set_tile_config(self.handle, arr))
+
+    def autotune(self, fields, J=None, stream=None):
+        """Time the tensor-core tile configurations on these device arrays (read only) and keep the
+        fastest; returns (best projection ms, best back-projection ms).  No-op for fp64 / fp32."""
+        _check_tensor(fields, self, 6, "fields")
+        jp = None
+        if J is not None:
+            _check_tensor(J, self, 3, "J")
+            jp = J.data_ptr()
+        ms = (ctypes.c_double * 2)()
+        _check(lib().fdetd_plan_autotune(self.handle, fields.data_ptr(), jp, _stream_handle(stream), ms))
+        return ms[0], ms[1]
 
     def close(self):
         if self.handle:
@@ -273,8 +302,28 @@ class FdetdBatch:
         self._keep.append((plan, fields, J))
         return idx.value
 
+    def set_autotune(self, on=True):
+        _check(lib().fdetd_batch_set_autotune(self.handle, int(on)))
+
     def capture(self, nsteps=1, stream=None):
         _check(lib().fdetd_batch_capture(self.handle, nsteps, _stream_handle(stream)))
+
+    def groups(self):
+        """Per tensor-core group after capture: the chosen tiles, sizes and tuned times."""
+        out = []
+        gi = 0
+        while True:
+            info = (ctypes.c_int * 7)()
+            ms = (ctypes.c_double * 2)()
+            ng = lib().fdetd_batch_group_info(self.handle, gi, info, ms)
+            if ng < 0:
+                _check(-ng)
+            if gi >= ng:
+                return out
+            out.append({"tn_proj": info[0], "tn_back": info[1], "sched_proj": info[2], "sched_back": info[3],
+                        "instances": info[4], "proj_tiles": info[5], "back_tiles": info[6],
+                        "tuned_ms": (ms[0], ms[1])})
+            gi += 1
 
     def launch(self, stream=None):
         _check(lib().fdetd_batch_launch(self.handle, _stream_handle(stream)))

@@ -3,7 +3,9 @@
 // propagator.  See include/fdetd.h for the contract of every entry point.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -259,13 +261,7 @@ extern "C" int fdetd_plan(fdetd_plan_t* out, int Nz, int Nr, int M, int order, d
   return fdetd_plan_modes(out, Nz, Nr, modes.data(), M + 1, order, dz, dr, dt, precision, flags);
 }
 
-extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nsteps, void* stream) {
-  if (!p) return fail(FDETD_ERR_ARG, "plan is null");
-  if (!fields) return fail(FDETD_ERR_ARG, "fields is null");
-  if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
-  if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
-  cudaStream_t st = (cudaStream_t)stream;
-  const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
+static SpectralArgs spectral_args(fdetd_plan_s* p, bool hasJ) {
   SpectralArgs sa;
   sa.coef = p->d_coef;
   sa.phase = p->d_phase;
@@ -275,39 +271,197 @@ extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nstep
   sa.tw_count = p->tw_count;
   sa.split_out = p->tc ? tc_split_buffer(p->tc) : nullptr;
   sa.npieces = p->precision == FDETD_PREC_BF16X3 ? 2 : 3;
-  sa.split_rows = p->tc ? tc_split_rows(p->tc) : 0;
+  sa.split_kstages = p->tc ? tc_split_kstages(p->tc) : 0;
   sa.err = p->d_err;
   sa.src = p->d_src;
   sa.Nz = p->Nz;
   sa.logNz = p->logNz;
   sa.n = p->Nr;
   sa.dt = p->dt;
-  sa.hasJ = J != nullptr;
-  for (int s = 0; s < nsteps; ++s) {
-    cudaError_t e;
-    prof_mark(p, 0, true, st);
-    if (p->tc) {
-      e = tc_project(p->tc, fields, J, p->d_coef, st);
-    } else {
-      ProjArgs pa{fields, J, p->d_P, p->d_coef, p->Nz, p->Nr};
-      e = launch_project_simt(pa, p->nmodes, prec, st);
-    }
-    prof_mark(p, 0, false, st);
-    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("projection: ") + cudaGetErrorString(e));
-    prof_mark(p, 1, true, st);
-    e = launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
-    prof_mark(p, 1, false, st);
-    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("spectral: ") + cudaGetErrorString(e));
-    prof_mark(p, 2, true, st);
-    if (p->tc) {
-      e = tc_backproject(p->tc, fields, st);
-    } else {
-      BackArgs ba{fields, p->d_Q, p->d_coef, p->Nz, p->Nr};
-      e = launch_backproject_simt(ba, p->nmodes, prec, st);
-    }
-    prof_mark(p, 2, false, st);
-    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("back-projection: ") + cudaGetErrorString(e));
+  sa.hasJ = hasJ;
+  return sa;
+}
+
+// The three stages of one step (projection, z transforms with the exact rotation, back-projection).
+static int stage_project(fdetd_plan_s* p, void* fields, const void* J, cudaStream_t st) {
+  const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
+  cudaError_t e;
+  prof_mark(p, 0, true, st);
+  if (p->tc) {
+    e = tc_project(p->tc, fields, J, p->d_coef, st);
+  } else {
+    ProjArgs pa{fields, J, p->d_P, p->d_coef, p->Nz, p->Nr};
+    e = launch_project_simt(pa, p->nmodes, prec, st);
   }
+  prof_mark(p, 0, false, st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("projection: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+static int stage_spectral(fdetd_plan_s* p, bool hasJ, cudaStream_t st) {
+  const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
+  const SpectralArgs sa = spectral_args(p, hasJ);
+  prof_mark(p, 1, true, st);
+  cudaError_t e = launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
+  prof_mark(p, 1, false, st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("spectral: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+static int stage_backproject(fdetd_plan_s* p, void* fields, cudaStream_t st) {
+  const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
+  cudaError_t e;
+  prof_mark(p, 2, true, st);
+  if (p->tc) {
+    e = tc_backproject(p->tc, fields, st);
+  } else {
+    BackArgs ba{fields, p->d_Q, p->d_coef, p->Nz, p->Nr};
+    e = launch_backproject_simt(ba, p->nmodes, prec, st);
+  }
+  prof_mark(p, 2, false, st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("back-projection: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nsteps, void* stream) {
+  if (!p) return fail(FDETD_ERR_ARG, "plan is null");
+  if (!fields) return fail(FDETD_ERR_ARG, "fields is null");
+  if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
+  if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = stage_project(p, fields, J, st);
+    if (!rc) rc = stage_spectral(p, J != nullptr, st);
+    if (!rc) rc = stage_backproject(p, fields, st);
+    if (rc) return rc;
+  }
+  return FDETD_OK;
+}
+
+// ---- autotuning of the tensor-core tile shapes and schedules
+
+static float time_launches(const std::function<cudaError_t()>& f, cudaStream_t st, int reps, cudaError_t* err) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  float ms = -1.f;
+  *err = cudaEventCreate(&a);
+  if (*err == cudaSuccess) *err = cudaEventCreate(&b);
+  if (*err == cudaSuccess) *err = f();  // warm-up
+  if (*err == cudaSuccess) *err = cudaEventRecord(a, st);
+  for (int r = 0; *err == cudaSuccess && r < reps; ++r) *err = f();
+  if (*err == cudaSuccess) *err = cudaEventRecord(b, st);
+  if (*err == cudaSuccess) *err = cudaEventSynchronize(b);
+  if (*err == cudaSuccess) *err = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return ms / reps;
+}
+
+// Times every candidate (N tile and tile order of each kernel) on the instances' own data and
+// returns the fastest.  The projection candidates read the fields and overwrite only the plans'
+// coefficient scratch; the back-projection candidates write into one scratch array (sized for the
+// largest instance and shared by all of them), so the caller's fields are never modified.
+static int tune_group(std::vector<fdetd_plan_s*>& plans, const std::vector<void*>& fields,
+                      const std::vector<const void*>& J, cudaStream_t st, TcConfig* best, float* best_ms) {
+  const int count = (int)plans.size();
+  std::vector<TcPlan*> tp(count);
+  std::vector<const void*> fp(count);
+  size_t maxb = 0;
+  for (int k = 0; k < count; ++k) {
+    tp[k] = plans[k]->tc;
+    fp[k] = fields[k];
+    maxb = std::max(maxb, (size_t)plans[k]->nmodes * 6 * plans[k]->Nz * plans[k]->Nr * 8);
+  }
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, maxb) != cudaSuccess) return fail(FDETD_ERR_OOM, "autotune scratch allocation failed");
+  TcConfig cur = tc_default_config(tc_pieces(tp[0]));
+  float bp = 1e30f, bb = 1e30f;
+  int rc = FDETD_OK;
+  for (int which = 0; which < 2 && rc == FDETD_OK; ++which)
+    for (int tn : {128, 256})
+      for (int sched : {0, 1}) {
+        if (rc != FDETD_OK) break;
+        TcConfig c = cur;
+        if (which == 0) {
+          c.tn_p = tn;
+          c.sched_p = sched;
+        } else {
+          c.tn_b = tn;
+          c.sched_b = sched;
+        }
+        if (!tc_config_valid(tp.data(), count, c)) continue;
+        TcGroup* G = nullptr;
+        cudaError_t e = tc_group_create(&G, tp.data(), fp.data(), J.data(), count, c);
+        if (e != cudaSuccess) {
+          rc = fail(FDETD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        for (int k = 0; k < count; ++k) {
+          tc_group_set_coef(G, k, plans[k]->d_coef);
+          if (which == 1) tc_group_set_fields(G, k, scratch);
+        }
+        const float ms = time_launches(
+            [&]() { return which == 0 ? tc_group_project(G, st) : tc_group_backproject(G, st); }, st, 3, &e);
+        tc_group_destroy(G);
+        if (e != cudaSuccess) {
+          rc = fail(FDETD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        if (which == 0 && ms < bp) {
+          bp = ms;
+          cur.tn_p = tn;
+          cur.sched_p = sched;
+        }
+        if (which == 1 && ms < bb) {
+          bb = ms;
+          cur.tn_b = tn;
+          cur.sched_b = sched;
+        }
+      }
+  cudaFree(scratch);
+  if (rc) return rc;
+  *best = cur;
+  if (best_ms) {
+    best_ms[0] = bp;
+    best_ms[1] = bb;
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_autotune(fdetd_plan_t p, const void* fields, const void* J, void* stream, double* ms) {
+  if (!p || !fields) return fail(FDETD_ERR_ARG, "null argument");
+  if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  if (!p->tc) return FDETD_OK;
+  std::vector<fdetd_plan_s*> pl{p};
+  std::vector<void*> f{const_cast<void*>(fields)};
+  std::vector<const void*> j{J};
+  TcConfig best;
+  float bms[2] = {0, 0};
+  int rc = tune_group(pl, f, j, (cudaStream_t)stream, &best, bms);
+  if (rc) return rc;
+  if (tc_plan_set_config(p->tc, best) != cudaSuccess) return fail(FDETD_ERR_CUDA, "autotune: invalid configuration");
+  if (ms) {
+    ms[0] = bms[0];
+    ms[1] = bms[1];
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_tile_config(fdetd_plan_t p, int* cfg) {
+  if (!p || !cfg) return fail(FDETD_ERR_ARG, "null argument");
+  if (!p->tc) return fail(FDETD_ERR_ARG, "not a tensor-core plan");
+  const TcConfig c = tc_plan_config(p->tc);
+  cfg[0] = c.tn_p;
+  cfg[1] = c.tn_b;
+  cfg[2] = c.sched_p;
+  cfg[3] = c.sched_b;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_set_tile_config(fdetd_plan_t p, const int* cfg) {
+  if (!p || !cfg) return fail(FDETD_ERR_ARG, "null argument");
+  if (!p->tc) return fail(FDETD_ERR_ARG, "not a tensor-core plan");
+  const TcConfig c{cfg[0], cfg[1], cfg[2], cfg[3]};
+  if (tc_plan_set_config(p->tc, c) != cudaSuccess) return fail(FDETD_ERR_ARG, "invalid tile configuration");
   return FDETD_OK;
 }
 
@@ -442,6 +596,15 @@ struct fdetd_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int steps = 0;
+  int autotune = 1;
+  // tensor-core instances of one precision share grouped projection / back-projection launches
+  struct Group {
+    TcGroup* g = nullptr;
+    std::vector<int> members;
+    TcConfig cfg;
+    float tuned_ms[2] = {0, 0};
+  };
+  std::vector<Group> groups;
 };
 
 static void batch_release_graph(fdetd_batch_s* b) {
@@ -449,6 +612,9 @@ static void batch_release_graph(fdetd_batch_s* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+  for (auto& g : b->groups)
+    if (g.g) tc_group_destroy(g.g);
+  b->groups.clear();
 }
 
 extern "C" int fdetd_batch_create(fdetd_batch_t* out) {
@@ -482,6 +648,11 @@ extern "C" int fdetd_batch_add(fdetd_batch_t b, fdetd_plan_t plan, void* fields,
   return FDETD_OK;
 }
 
+// Groups the tensor-core instances by precision (at most kMaxGroupInstances per group), picks each
+// group's tile shapes and schedules (autotuned on the instances' data unless disabled), and
+// captures `nsteps` steps: per step, one grouped projection launch per group, every instance's
+// spectral kernel on its own branch, one grouped back-projection launch per group.  Instances on
+// the CUDA-core paths run their own step sequence on concurrent branches.
 extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
   if (!b || nsteps < 1) return fail(FDETD_ERR_ARG, "bad batch or nsteps");
   if (b->inst.empty()) return fail(FDETD_ERR_ARG, "empty batch");
@@ -489,6 +660,44 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
     if (i.plan->profiling) return fail(FDETD_ERR_ARG, "turn profiling off before capturing");
   batch_release_graph(b);
   cudaStream_t s0 = (cudaStream_t)stream;
+  // ---- groups (built and tuned before the capture: tile tables are uploaded synchronously)
+  for (int np : {2, 3}) {
+    std::vector<int> ids;
+    for (size_t k = 0; k < b->inst.size(); ++k)
+      if (b->inst[k].plan->tc && tc_pieces(b->inst[k].plan->tc) == np) ids.push_back((int)k);
+    for (size_t c0 = 0; c0 < ids.size(); c0 += kMaxGroupInstances) {
+      fdetd_batch_s::Group G;
+      G.members.assign(ids.begin() + c0, ids.begin() + std::min(ids.size(), c0 + (size_t)kMaxGroupInstances));
+      std::vector<fdetd_plan_s*> pl;
+      std::vector<TcPlan*> tp;
+      std::vector<void*> f;
+      std::vector<const void*> fc, j;
+      for (int k : G.members) {
+        pl.push_back(b->inst[k].plan);
+        tp.push_back(b->inst[k].plan->tc);
+        f.push_back(b->inst[k].fields);
+        fc.push_back(b->inst[k].fields);
+        j.push_back(b->inst[k].J);
+      }
+      G.cfg = tc_default_config(np);
+      if (b->autotune) {
+        int rc = tune_group(pl, f, j, s0, &G.cfg, G.tuned_ms);
+        if (rc) {
+          batch_release_graph(b);
+          return rc;
+        }
+      }
+      cudaError_t e = tc_group_create(&G.g, tp.data(), fc.data(), j.data(), (int)G.members.size(), G.cfg);
+      if (e != cudaSuccess) {
+        batch_release_graph(b);
+        return fail(FDETD_ERR_CUDA, std::string("batch group: ") + cudaGetErrorString(e));
+      }
+      for (size_t k = 0; k < G.members.size(); ++k) tc_group_set_coef(G.g, (int)k, pl[k]->d_coef);
+      b->groups.push_back(G);
+    }
+  }
+  if (cudaStreamSynchronize(s0) != cudaSuccess) return fail(FDETD_ERR_CUDA, "batch: stream error before capture");
+  // ---- capture
   cudaStream_t cap = s0;
   cudaStream_t own = nullptr;
   if (!cap) {  // the legacy default stream cannot be captured
@@ -498,11 +707,35 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = FDETD_OK;
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
-  for (size_t k = 0; e == cudaSuccess && k < b->inst.size(); ++k) {
+  // CUDA-core instances: their own step sequence on a side branch
+  std::vector<int> simt;
+  for (size_t k = 0; e == cudaSuccess && rc == FDETD_OK && k < b->inst.size(); ++k) {
+    if (b->inst[k].plan->tc) continue;
+    simt.push_back((int)k);
     e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
-    if (e != cudaSuccess) break;
-    rc = fdetd_step(b->inst[k].plan, b->inst[k].fields, b->inst[k].J, nsteps, b->side[k]);
-    if (rc != FDETD_OK) break;
+    if (e == cudaSuccess) rc = fdetd_step(b->inst[k].plan, b->inst[k].fields, b->inst[k].J, nsteps, b->side[k]);
+  }
+  for (int s = 0; s < nsteps && e == cudaSuccess && rc == FDETD_OK; ++s) {
+    for (auto& G : b->groups) {
+      e = tc_group_project(G.g, cap);
+      if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
+    for (auto& G : b->groups)
+      for (int k : G.members) {
+        if (e != cudaSuccess || rc != FDETD_OK) break;
+        e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+        if (e == cudaSuccess) rc = stage_spectral(b->inst[k].plan, b->inst[k].J != nullptr, b->side[k]);
+        if (e == cudaSuccess && rc == FDETD_OK) e = cudaEventRecord(b->join[k], b->side[k]);
+        if (e == cudaSuccess && rc == FDETD_OK) e = cudaStreamWaitEvent(cap, b->join[k], 0);
+      }
+    for (auto& G : b->groups) {
+      if (e != cudaSuccess || rc != FDETD_OK) break;
+      e = tc_group_backproject(G.g, cap);
+    }
+  }
+  for (int k : simt) {
+    if (e != cudaSuccess || rc != FDETD_OK) break;
     e = cudaEventRecord(b->join[k], b->side[k]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, b->join[k], 0);
   }
@@ -523,6 +756,31 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
   b->graph = g;
   b->steps = nsteps;
   return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_set_autotune(fdetd_batch_t b, int on) {
+  if (!b) return fail(FDETD_ERR_ARG, "batch is null");
+  b->autotune = on != 0;
+  batch_release_graph(b);
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_group_info(fdetd_batch_t b, int gi, int* info, double* ms) {
+  if (!b || !info) return -FDETD_ERR_ARG;
+  if (gi < 0 || gi >= (int)b->groups.size()) return (int)b->groups.size();
+  const auto& G = b->groups[gi];
+  info[0] = G.cfg.tn_p;
+  info[1] = G.cfg.tn_b;
+  info[2] = G.cfg.sched_p;
+  info[3] = G.cfg.sched_b;
+  info[4] = (int)G.members.size();
+  info[5] = tc_group_tiles(G.g, 0);
+  info[6] = tc_group_tiles(G.g, 1);
+  if (ms) {
+    ms[0] = G.tuned_ms[0];
+    ms[1] = G.tuned_ms[1];
+  }
+  return (int)b->groups.size();
 }
 
 extern "C" int fdetd_batch_launch(fdetd_batch_t b, void* stream) {

@@ -83,6 +83,11 @@ __device__ __forceinline__ void zsym_unpack(const ZSymF& z, df& spr, df& spi, df
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) from global memory into L2
+__device__ __forceinline__ void l2_prefetch(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((uint64_t)src), "r"(bytes) : "memory");
+}
+
 // bulk asynchronous copy of `bytes` (multiple of 16) from global to shared, completing on `bar`
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -250,7 +255,7 @@ __device__ __forceinline__ void last_pass_to_global(const C* s, int logN, const 
         if (!SPLIT_OUT)
           dst[a][z] = v[r];
         else
-          split_store(args.split_out, args.npieces, md, cidx[a], jcol, z, args.split_rows, N, (float)v[r].x,
+          split_store(args.split_out, args.npieces, md, cidx[a], jcol, z, args.split_kstages, N, (float)v[r].x,
                       (float)v[r].y);
       }
     }
@@ -363,6 +368,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
     for (int a = 0; a < narr; ++a)
       bulk_g2s(s + (size_t)a * Nz, coef + ((size_t)(md * 9 + idx[a]) * n + j) * Nz, col, &load_bar);
     if (TW_SMEM) bulk_g2s(const_cast<C*>(tw), twg, twb, &load_bar);
+    // the rotation reads this column's phase factors (and, in MAIN mode, the source term) straight
+    // from global memory: start pulling them into L2 now, while the forward transforms run
+    const PH* ph = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
+    l2_prefetch(ph, (uint32_t)(Nz * sizeof(PH)));
+    if (MODE == MAIN && args.src)
+      for (int c = 0; c < 3; ++c)
+        l2_prefetch(reinterpret_cast<const C*>(args.src) + (((size_t)(md * 2 + fam) * 3 + c) * n + j) * Nz, col);
   }
   __syncthreads();
   if (!bar_wait(&load_bar, 0)) {

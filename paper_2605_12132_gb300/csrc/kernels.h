@@ -14,9 +14,9 @@ struct SpectralArgs {
   const void* lam;       // [nmodes][2][n] double / df (lambda for TM, mu for TE)
   const void* twiddle;   // per-pass twiddle tables (spectral_twiddles), complex<T>
   int tw_count;          // entries in `twiddle`
-  __nv_bfloat16* split_out;  // tensor-core path: [nmodes][npieces][6][split_rows][2 Nz]
+  __nv_bfloat16* split_out;  // tensor-core path: pre-tiled pieces, see split_store
   int npieces;
-  int split_rows;            // coefficient rows per block in split_out (n padded to the K tile)
+  int split_kstages;         // 64-wide j stages of the back-projection (ceil(n / 64))
   int Nz, logNz, n;
   double dt;
   int hasJ;
@@ -30,18 +30,23 @@ int spectral_twiddles(int Nz, int precision, double* re, double* im);
 bool spectral_needs_source(int Nz, int precision, int tw_count);
 
 // bf16 split of an FP32 value into npieces (2 or 3) terms whose sum reproduces it to
-// 16 / 24 significant bits; piece p of coefficient array c goes to
-// out[((md * npieces + p) * 6 + c) * rows + j][2 z + part].
-__device__ __forceinline__ void split_store(__nv_bfloat16* out, int npieces, int md, int c, int j, int z, int rows,
+// 16 / 24 significant bits, stored in the pre-tiled operand layout of the back-projection:
+// 16 KB blocks (md, piece, c, ks = j / 64, zb = z / 64), each [2 halves][64 j rows][128 B]
+// holding (z, re/im) pairs of 64 z along N, the 16-byte chunks of a row swizzled by (j & 7)
+// (the 128-byte swizzle the MMA descriptor expects).
+__device__ __forceinline__ void split_store(__nv_bfloat16* out, int npieces, int md, int c, int j, int z, int kst,
                                             int Nz, float vr, float vi) {
   float r0 = vr, r1 = vi;
+  const int zl = z & 63, jr = j & 63;
+  const uint32_t off = (uint32_t)(zl >> 5) * 8192u + (uint32_t)jr * 128u +
+                       ((uint32_t)(((zl & 31) >> 2) ^ (jr & 7)) << 4) + (uint32_t)(zl & 3) * 4u;
   for (int p = 0; p < npieces; ++p) {
     const __nv_bfloat16 h0 = __float2bfloat16_rn(r0), h1 = __float2bfloat16_rn(r1);
     __nv_bfloat162 pr;
     pr.x = h0;
     pr.y = h1;
-    const size_t row = ((size_t)(md * npieces + p) * 6 + c) * rows + j;
-    *reinterpret_cast<__nv_bfloat162*>(out + row * (size_t)(2 * Nz) + 2 * z) = pr;
+    const size_t blk = ((((size_t)md * npieces + p) * 6 + c) * kst + (j >> 6)) * (size_t)(Nz >> 6) + (z >> 6);
+    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<unsigned char*>(out) + blk * 16384 + off) = pr;
     r0 -= __bfloat162float(h0);
     r1 -= __bfloat162float(h1);
   }
@@ -66,16 +71,57 @@ cudaError_t launch_project_simt(const ProjArgs& a, int nmodes, int precision, cu
 cudaError_t launch_backproject_simt(const BackArgs& a, int nmodes, int precision, cudaStream_t st);
 
 // ---------------------------------------------------------------- tensor-core projections
-struct TcPlan;  // defined in k_tc.cu
+// One instance of a grouped launch (kernel parameter; pointers are device pointers).
+constexpr int kMaxGroupInstances = 64;
+struct GInst {
+  float2* fields;      // [nmodes][6][Nz][n] complex64, read by the projection, written by the back-projection
+  const float2* J;     // [nmodes][3][Nz][n] or null
+  float* coef;         // [nmodes][9][n][2 Nz] FP32 coefficient scratch
+  const uint8_t* P;    // pre-tiled projection pieces
+  const uint8_t* Q;    // pre-tiled back-projection pieces
+  const uint8_t* S;    // pre-tiled split coefficients (written by the spectral kernel)
+  int* err;            // device failure flag of the instance's plan
+  int Nz, n, njb, pad;
+};
+struct GroupParams {
+  GInst inst[kMaxGroupInstances];
+  int count;
+};
+// Tile shapes and schedules of the persistent kernels (chosen by the autotuner):
+// tn_p / tn_b = N tile of the projection / back-projection (128 or 256); sched = tile order
+// (0: longest first, round-robin over CTAs; 1: longest first, snake order).
+struct TcConfig {
+  int tn_p, tn_b, sched_p, sched_b;
+};
+
+struct TcPlan;   // defined in k_tc.cu
+struct TcGroup;  // a tile table over one or more instances
 cudaError_t tc_create(TcPlan** out, int Nz, int n, int nmodes, int npieces, const double* P, const double* Q,
                       int* err, char* msg, size_t msglen);
 void tc_destroy(TcPlan* p);
 size_t tc_device_bytes(const TcPlan* p);
 __nv_bfloat16* tc_split_buffer(TcPlan* p);
-int tc_split_rows(const TcPlan* p);
+int tc_split_kstages(const TcPlan* p);
+int tc_pieces(const TcPlan* p);
+TcConfig tc_default_config(int npieces);
+TcConfig tc_plan_config(const TcPlan* p);
+cudaError_t tc_plan_set_config(TcPlan* p, const TcConfig& c);
+bool tc_config_valid(const TcPlan* const* plans, int count, const TcConfig& c);
+// single-instance launches through a one-instance group kept by the plan (built on first use,
+// which must not happen during a stream capture: tc_prepare builds it ahead)
+cudaError_t tc_prepare(TcPlan* p, const void* fields, const void* J, void* coef);
 cudaError_t tc_project(TcPlan* p, const void* fields, const void* J, void* coef, cudaStream_t st);
 cudaError_t tc_backproject(TcPlan* p, void* fields, cudaStream_t st);
 int tc_launches_per_step(const TcPlan* p);
+// grouped launches over up to kMaxGroupInstances instances of one precision
+cudaError_t tc_group_create(TcGroup** out, TcPlan* const* plans, const void* const* fields, const void* const* J,
+                            int count, const TcConfig& cfg);
+void tc_group_set_coef(TcGroup* g, int k, void* coef);
+void tc_group_set_fields(TcGroup* g, int k, void* fields);
+void tc_group_destroy(TcGroup* g);
+cudaError_t tc_group_project(TcGroup* g, cudaStream_t st);
+cudaError_t tc_group_backproject(TcGroup* g, cudaStream_t st);
+int tc_group_tiles(const TcGroup* g, int which);
 
 // ---------------------------------------------------------------- envelope
 struct EnvArgs {
