@@ -14,9 +14,9 @@
 // in FP32 (round to nearest).
 //
 // Projection  (per mode, group, output block):  D[(z,part), j] = sum_r X[(z,part), r] P[j, r]
-//   A = field rows (64 z x re/im, r contiguous): one bulk copy per z row stages FP32 complex
-//       values in shared memory; four converter warps split them in place into 64B-swizzled
-//       bf16 pieces (forming the rotated components tau*F on the way);
+//   A = field rows (64 z x re/im, r contiguous): a TMA box (per-instance tensor map in the
+//       kernel parameters) stages FP32 complex values in shared memory; four converter warps
+//       split them in place into 64B-swizzled bf16 pieces (forming tau*F on the way);
 //   B = P pieces [j][r], K-major, pre-tiled and pre-swizzled at plan time (one bulk copy);
 //   M = 128, N = TN (128 or 256), K = 32 per pipeline stage.
 // Back-projection (per mode, group, output field): D[r, (z,part)] = sum_j Q[r, j] C[j, (z,part)]
@@ -31,6 +31,9 @@
 // Every mbarrier wait is bounded; on timeout the kernel records an error code in the instance's
 // flag, tells the other roles to stop through a shared abort flag, drains its own copies and
 // MMAs, and frees TMEM before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -89,6 +92,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                    smem_u32(dst)),
                "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+
+// 2D TMA tile load (tensor map in kernel-parameter space), completing on `bar`
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
 }
 
 // tcgen05 shared-memory matrix descriptor: start>>4 [0,14), LBO>>4 [16,30), SBO>>4 [32,46),
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const float4 v = src[k];
-            // radii beyond Nr were not copied: their staging bytes are stale and count as zero
+            // radii beyond Nr are zero-filled by the TMA box; masked here as well
             const bool in0 = r0 + c * 8 + 2 * k < n, in1 = r0 + c * 8 + 2 * k + 1 < n;
             re[it][2 * k] = in0 ? v.x : 0.f;
             im[it][2 * k] = in0 ? v.y : 0.f;
@@ -385,7 +397,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
       if (lane == 0) mbar_arrive(&sb->tempty[b]);
     }
   } else if (warp == 8) {
-    // ---- producer: FP32 field rows (one bulk copy per z row) and the pre-tiled P pieces
+    // ---- producer: the FP32 field tile (TMA) and the pre-tiled P pieces (bulk copies)
     int q = 0;
     bool live = true;
     for (int ti = blockIdx.x; live && ti < ntiles; ti += gridDim.x) {
@@ -407,21 +419,18 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
           break;
         }
         const int ib = bl[t / nks], rs = t % nks, r0 = rs * 32;
-        const uint32_t rowbytes = (uint32_t)min(32, n - r0) * 8u;
-        const float2* src;
-        if (g == 2) {
-          src = I.J + ((size_t)(md * 3 + ib) * Nz + z0) * n + r0;
-        } else {
-          const int field = (g == 1) ? (ib == 0 ? 4 : (ib == 1 ? 3 : 5)) : ib;
-          src = I.fields + ((size_t)(md * 6 + field) * Nz + z0) * n + r0;
-        }
         if (lane == 0) {
-          mbar_expect_tx(&sb->fullS[s], 64u * rowbytes);
+          // FP32 field tile: 64 z rows x 32 complex, one TMA box (radii beyond Nr are zero-filled)
+          mbar_expect_tx(&sb->fullS[s], 64u * 256u);
+          if (g == 2) {
+            tma_load_2d(stage_A(s), &gp.jmap[tl.x], &sb->fullS[s], 2 * r0, (md * 3 + ib) * Nz + z0);
+          } else {
+            const int field = (g == 1) ? (ib == 0 ? 4 : (ib == 1 ? 3 : 5)) : ib;
+            tma_load_2d(stage_A(s), &gp.fmap[tl.x], &sb->fullS[s], 2 * r0, (md * 6 + field) * Nz + z0);
+          }
           mbar_expect_tx(&sb->fullB[s], (uint32_t)NP * C::kBp);
         }
         __syncwarp();
-        unsigned char* A = stage_A(s);
-        for (int zl = lane; zl < 64; zl += 32) bulk_g2s(A + zl * 256, src + (size_t)zl * n, rowbytes, &sb->fullS[s]);
         if (lane < NP) {
           // P block (md, g, piece, ob, ib, rs, jb): 128 rows x 32 K, 8 KB; TN/128 consecutive jb blocks
           const size_t blk = (((((size_t)(md * 2 + (g == 1 ? 1 : 0)) * NP + lane) * 3 + ob) * 3 + ib) * nks + rs) *
@@ -793,6 +802,40 @@ static std::vector<uint8_t> tile_Q(const double* Q, int nmodes, int n, int np, i
   return out;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// FP32 view of a complex array with `rows` rows of n values (2 n floats), boxes of 32 complex x 64 rows
+static bool encode_rows(CUtensorMap* m, const void* ptr, int n, long rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)2 * n * 4};
+  cuuint32_t box[2] = {64, 64};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// (re-)encodes instance k's field / current maps for the pointers in params.inst[k]
+static bool encode_instance(GroupParams& gp, int k, int nmodes) {
+  const GInst& I = gp.inst[k];
+  if (!encode_rows(&gp.fmap[k], I.fields, I.n, (long)nmodes * 6 * I.Nz)) return false;
+  if (I.J && !encode_rows(&gp.jmap[k], I.J, I.n, (long)nmodes * 3 * I.Nz)) return false;
+  return true;
+}
+
 static int num_sms() {
   static int sms = 0;
   if (!sms) {
@@ -953,7 +996,7 @@ cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const do
     return cudaErrorNotSupported;
   }
   if (n % 2) {
-    snprintf(msg, msglen, "the tensor-core path needs an even Nr (16-byte aligned field rows for the bulk copies)");
+    snprintf(msg, msglen, "the tensor-core path needs an even Nr (16-byte field row stride for TMA)");
     return cudaErrorNotSupported;
   }
   int dev = 0, cc_major = 0, cc_minor = 0;
@@ -962,6 +1005,10 @@ cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const do
   cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (cc_major != 10 || cc_minor != 3) {
     snprintf(msg, msglen, "tcgen05 kernels are built for sm_103a (found sm_%d%d)", cc_major, cc_minor);
+    return cudaErrorNotSupported;
+  }
+  if (!get_encode()) {
+    snprintf(msg, msglen, "cuTensorMapEncodeTiled unavailable");
     return cudaErrorNotSupported;
   }
   cudaError_t e = opt_in_all();
@@ -1053,6 +1100,10 @@ cudaError_t tc_group_create(TcGroup** out, TcPlan* const* plans, const void* con
     I.Nz = t->Nz;
     I.n = t->n;
     I.njb = t->njb;
+    if (!encode_instance(G->params, k, t->nmodes)) {
+      delete G;
+      return cudaErrorInvalidValue;
+    }
   }
   G->params.count = count;
   cudaError_t e = build_tiles(G);
@@ -1065,6 +1116,7 @@ cudaError_t tc_group_create(TcGroup** out, TcPlan* const* plans, const void* con
 }
 
 void tc_group_set_coef(TcGroup* G, int k, void* coef) { G->params.inst[k].coef = (float*)coef; }
+// the back-projection writes through GInst.fields; the projection's tensor map is left as it is
 void tc_group_set_fields(TcGroup* G, int k, void* fields) { G->params.inst[k].fields = (float2*)fields; }
 
 void tc_group_destroy(TcGroup* G) {
@@ -1088,10 +1140,13 @@ static cudaError_t self_group(TcPlan* t, const void* fields, const void* J, void
     cudaError_t e = tc_group_create(&t->self[h], pl, f, j, 1, t->cfg);
     if (e != cudaSuccess) return e;
   }
-  GInst& I = t->self[h]->params.inst[0];
+  GroupParams& gp = t->self[h]->params;
+  GInst& I = gp.inst[0];
+  const bool moved = I.fields != (float2*)fields || I.J != (const float2*)J;
   I.fields = (float2*)fields;
   I.J = (const float2*)J;
   I.coef = (float*)coef;
+  if (moved && !encode_instance(gp, 0, t->nmodes)) return cudaErrorInvalidValue;
   t->last = h;
   return cudaSuccess;
 }

@@ -1,5 +1,6 @@
 // Kernel argument records and launchers of the FDETD step (internal).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -85,6 +86,8 @@ struct GInst {
 };
 struct GroupParams {
   GInst inst[kMaxGroupInstances];
+  CUtensorMap fmap[kMaxGroupInstances];  // FP32 views of the fields (rows of 2 n floats), 64 x 64 boxes
+  CUtensorMap jmap[kMaxGroupInstances];  // the same for J (unused entries zero)
   int count;
 };
 // Tile shapes and schedules of the persistent kernels (chosen by the autotuner):
