@@ -155,6 +155,19 @@ int fdetd_plan_tile_config(fdetd_plan_t plan, int* cfg);
 int fdetd_plan_set_tile_config(fdetd_plan_t plan, const int* cfg);
 
 /*
+ * fdetd_probe_mma_rounding - diagnostic with no counterpart in the paper: runs one small
+ * tcgen05 kind::f16 MMA test on hand-picked bf16 operands (one MMA on K = 0..15, then `reps`
+ * (0..64) accumulating MMAs on K = 16..31) and writes 12 rows x 2 columns of FP32 results to
+ * host_out[24] (row-major).  The rows are listed at the top of csrc/k_probe.cu; they show the
+ * rounding of the tensor core's FP32 accumulation, which the split-BF16 kernels are designed
+ * around.  Synchronises `stream`; allocates and frees small device buffers.  Returns
+ * FDETD_ERR_UNSUPPORTED on a GPU other than sm_103, FDETD_ERR_TIMEOUT if its bounded wait
+ * expired.
+ */
+int fdetd_probe_mma_rounding(float* host_out, int reps, void* stream);
+
+
+/*
  * Batches of uneven instances advanced by one CUDA graph (no counterpart in the paper).
  *
  * fdetd_batch_add registers an instance (a plan with its own device fields and optional J;

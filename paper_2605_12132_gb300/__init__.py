@@ -23,6 +23,7 @@ from ._native import (  # noqa: F401
     fdetd_host_tables,
     fdetd_plan,
     fdetd_plan_modes,
+    fdetd_probe_mma_rounding,
     fdetd_step,
     fdetd_step_host,
     lib,

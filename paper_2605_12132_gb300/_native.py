@@ -57,6 +57,7 @@ def lib():
     L.fdetd_plan_autotune.argtypes = [c_vp, c_vp, c_vp, c_vp, dp]
     L.fdetd_plan_tile_config.argtypes = [c_vp, ctypes.POINTER(c_int)]
     L.fdetd_plan_set_tile_config.argtypes = [c_vp, ctypes.POINTER(c_int)]
+    L.fdetd_probe_mma_rounding.argtypes = [ctypes.POINTER(ctypes.c_float), c_int, c_vp]
     L.fdetd_batch_launch.argtypes = [c_vp, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
     L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
@@ -218,6 +219,13 @@ def fdetd_host_tables(Nz, Nr, m, order, dz, dr, dt):
     out["sp"] = sp[0::2] + 1j * sp[1::2]
     out["sm"] = sm[0::2] + 1j * sm[1::2]
     return out
+
+
+def fdetd_probe_mma_rounding(reps=1, stream=None):
+    """Diagnostic tcgen05 accumulation test (see include/fdetd.h): a (12, 2) float32 array."""
+    out = (ctypes.c_float * 24)()
+    _check(lib().fdetd_probe_mma_rounding(out, reps, _stream_handle(stream)))
+    return np.array(out, dtype=np.float32).reshape(12, 2)
 
 
 def fdetd_host_coeffs(kind, order):
