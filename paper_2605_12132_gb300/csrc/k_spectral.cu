@@ -390,12 +390,25 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   const T inv = (T)1 / (T)Nz;
   C* src = reinterpret_cast<C*>(args.src) + ((size_t)(md * 2 + fam) * 3 * n + j) * Nz;  // [md][fam][3][n][Nz]
   const size_t sstride = (size_t)n * Nz;
+  // the table entries of the next kz are loaded one iteration ahead (they come from L2)
+  PH ph_next{};
+  ZS zs_next{};
+  if ((int)threadIdx.x < Nz) {  // NT may exceed a short transform length
+    ph_next = phase[threadIdx.x];
+    zs_next = zs[threadIdx.x];
+  }
   for (int q = threadIdx.x; q < Nz; q += NT) {
     const int pq = padx(q);
+    const PH ph_cur = ph_next;
+    const ZS zs_cur = zs_next;
+    if (q + NT < Nz) {
+      ph_next = phase[q + NT];
+      zs_next = zs[q + NT];
+    }
     K spr, spi, smr, smi, A1, A2;
     T B1, B2;
-    zsym_unpack(zs[q], spr, spi, smr, smi);
-    phase_unpack(phase[q], A1, A2, B1, B2);
+    zsym_unpack(zs_cur, spr, spi, smr, smi);
+    phase_unpack(ph_cur, A1, A2, B1, B2);
     C y0, y1, y2, z0, z1, z2;
     if (MODE == SOURCE) {
       C j0 = s[pq], j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);

@@ -20,7 +20,7 @@ if not torch.cuda.is_available():
 
 import paper_2605_12132_gb300 as fd  # noqa: E402
 
-TOL = {"bf16x6": 4e-6, "bf16x3": 2.5e-5}
+TOL = {"bf16x6": 1e-6, "bf16x3": 2.5e-5}
 
 
 def _configs(prec, Nz):
