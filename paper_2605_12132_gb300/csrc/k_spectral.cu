@@ -226,17 +226,66 @@ __device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int logN, in
   __syncthreads();
 }
 
-// The last radix-RR pass of the inverse transform of the three field columns, storing straight to
-// global memory: with Ns = N / RR a butterfly j writes z = j + r N/RR, consecutive across threads.
+// Inverse transform by transposed Stockham passes in reverse order: the transpose of forward pass
+// (RR, Ns) reads x[(j - k) RR + k + r Ns] (k = j mod Ns), applies the inverse RR-point DFT, multiplies
+// by the conjugated twiddle of the forward table entry (k, r) and writes y[j + r N/RR].  The product
+// of the transposed passes in reverse order is the transpose of the forward transform, which (the DFT
+// matrix being symmetric) with conjugated twiddles is the inverse DFT; both directions share one
+// twiddle table, and the first inverse pass touches exactly the elements the last forward pass wrote
+// for the same butterfly, so the two can be fused with the rotation in registers.
+template <int RR, int NT, int MAXB, typename C>
+__device__ __forceinline__ void stockham_pass_T(C* s, int a0, int na, int logN, int Ns, const C* tw) {
+  constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
+  const int N = 1 << logN;
+  const int lnbf = logN - LR, nbf = 1 << lnbf;
+  const int total = na << lnbf;
+  const int P = N + (N >> 3);
+  C v[MAXB][RR];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
+      const int k = j & (Ns - 1);
+      const int base = (j - k) * RR + k;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) v[i][r] = s[a * P + padx(base + r * Ns)];
+      dft_small<RR, true>(v[i]);
+      if (Ns > 1) {
+        const C* t = tw + k * (RR - 1);
+#pragma unroll
+        for (int r = 1; r < RR; ++r) v[i][r] = cmulconj(v[i][r], t[r - 1]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = threadIdx.x + i * NT;
+    if (b < total) {
+      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
+#pragma unroll
+      for (int r = 0; r < RR; ++r) s[a * P + padx(j + (r << lnbf))] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int RR, int NT, int MAXB, int G, typename C>
+__device__ __forceinline__ void pass_all_T(C* s, int narr, int logN, int Ns, const C* tw) {
+  for (int a0 = 0; a0 < narr; a0 += G) stockham_pass_T<RR, NT, MAXB>(s, a0, min(G, narr - a0), logN, Ns, tw);
+}
+
+// The last transposed pass (Ns = 1, no twiddles) of the three field columns, storing straight to
+// global memory: butterfly j writes z = j + r N/RR, consecutive across threads.
 template <int RR, int NT, int MAXB, bool SPLIT_OUT, typename C>
-__device__ __forceinline__ void last_pass_to_global(const C* s, int logN, const C* tw, C* const* dst,
-                                                    const SpectralArgs& args, const int* cidx, int md, int jcol) {
+__device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* const* dst, const SpectralArgs& args,
+                                                      const int* cidx, int md, int jcol) {
   constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
   const int N = 1 << logN;
   const int lnbf = logN - LR, nbf = 1 << lnbf;
   const int total = 3 << lnbf;
   const int P = N + (N >> 3);
-  const int Ns = nbf;
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
     const int b = threadIdx.x + i * NT;
@@ -244,14 +293,11 @@ __device__ __forceinline__ void last_pass_to_global(const C* s, int logN, const 
       const int a = b >> lnbf, j = b & (nbf - 1);
       C v[RR];
 #pragma unroll
-      for (int r = 0; r < RR; ++r) v[r] = s[a * P + padx(j + (r << lnbf))];
-      const C* t = tw + j * (RR - 1);
-#pragma unroll
-      for (int r = 1; r < RR; ++r) v[r] = cmulconj(v[r], t[r - 1]);
+      for (int r = 0; r < RR; ++r) v[r] = s[a * P + padx(j * RR + r)];
       dft_small<RR, true>(v);
 #pragma unroll
       for (int r = 0; r < RR; ++r) {
-        const int z = j + r * Ns;
+        const int z = j + (r << lnbf);
         if (!SPLIT_OUT)
           dst[a][z] = v[r];
         else
@@ -311,6 +357,44 @@ __device__ const C* fft_all(C* s, int narr, int logN, const C* tw) {
     Ns *= R;
   }
   return tw;
+}
+
+// Exact midpoint update of one (kz, j) point: Horner form of
+//   x + A1 M x + A2 M^2 x - dt (xJ + B1 M xJ + B2 M^2 xJ):
+//   p = x - dt xJ,  q = A1 x - dt B1 xJ,  u = A2 x - dt B2 xJ,  r = p + M (q + M u),
+// x_J = (eJ, aJ, 0) for TM, (cJ, 0, 0) for TE; the result is scaled by `inv` (1/Nz of the inverse DFT).
+template <typename T, typename K, typename C>
+__device__ __forceinline__ void rotate_point(C& x0, C& x1, C& x2, C j0, C j1, bool hasJ, int fam, K lam, K spr,
+                                             K spi, K smr, K smi, K A1, K A2, T B1, T B2, T dt, T inv) {
+  C y0, y1, y2, z0, z1, z2;
+  const T dB1 = dt * B1, dB2 = dt * B2;
+  C u0 = cscale(A2, x0), u1 = cscale(A2, x1), u2 = cscale(A2, x2);
+  C q0 = cscale(A1, x0), q1 = cscale(A1, x1), q2 = cscale(A1, x2);
+  C p0 = x0, p1 = x1;
+  if (hasJ) {
+    u0.x -= dB2 * j0.x; u0.y -= dB2 * j0.y;
+    u1.x -= dB2 * j1.x; u1.y -= dB2 * j1.y;
+    q0.x -= dB1 * j0.x; q0.y -= dB1 * j0.y;
+    q1.x -= dB1 * j1.x; q1.y -= dB1 * j1.y;
+    p0.x -= dt * j0.x; p0.y -= dt * j0.y;
+    p1.x -= dt * j1.x; p1.y -= dt * j1.y;
+  }
+  if (fam == 0) {
+    apply_tm(u0, u1, u2, y0, y1, y2, lam, spr, spi, smr, smi);
+    y0 = cadd(y0, q0); y1 = cadd(y1, q1); y2 = cadd(y2, q2);
+    apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
+  } else {
+    apply_te(u0, u1, u2, y0, y1, y2, lam, spr, spi, smr, smi);
+    y0 = cadd(y0, q0); y1 = cadd(y1, q1); y2 = cadd(y2, q2);
+    apply_te(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
+  }
+  C r0 = cadd(p0, z0), r1 = cadd(p1, z1), r2 = cadd(x2, z2);
+  r0.x *= inv; r0.y *= inv;
+  r1.x *= inv; r1.y *= inv;
+  r2.x *= inv; r2.y *= inv;
+  x0 = r0;
+  x1 = r1;
+  x2 = r2;
 }
 
 }  // namespace
@@ -381,8 +465,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
     if (threadIdx.x == 0 && args.err) atomicCAS(args.err, 0, 8);
     return;
   }
-  fft_all<R, false, NT, G, BPT, false>(s, narr, L, tw);
-  // exact rotation per kz (the 1/Nz of the inverse transform folded in)
   const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
   const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
   const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
@@ -390,27 +472,16 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   const T inv = (T)1 / (T)Nz;
   C* src = reinterpret_cast<C*>(args.src) + ((size_t)(md * 2 + fam) * 3 * n + j) * Nz;  // [md][fam][3][n][Nz]
   const size_t sstride = (size_t)n * Nz;
-  // the table entries of the next kz are loaded one iteration ahead (they come from L2)
-  PH ph_next{};
-  ZS zs_next{};
-  if ((int)threadIdx.x < Nz) {  // NT may exceed a short transform length
-    ph_next = phase[threadIdx.x];
-    zs_next = zs[threadIdx.x];
-  }
-  for (int q = threadIdx.x; q < Nz; q += NT) {
-    const int pq = padx(q);
-    const PH ph_cur = ph_next;
-    const ZS zs_cur = zs_next;
-    if (q + NT < Nz) {
-      ph_next = phase[q + NT];
-      zs_next = zs[q + NT];
-    }
-    K spr, spi, smr, smi, A1, A2;
-    T B1, B2;
-    zsym_unpack(zs_cur, spr, spi, smr, smi);
-    phase_unpack(ph_cur, A1, A2, B1, B2);
-    C y0, y1, y2, z0, z1, z2;
-    if (MODE == SOURCE) {
+  if (MODE == SOURCE) {
+    // the current's midpoint source term -dt exp(dt M / 2) x_J / Nz in kz space, to global memory
+    fft_all<R, false, NT, G, BPT, false>(s, narr, L, tw);
+    for (int q = threadIdx.x; q < Nz; q += NT) {
+      const int pq = padx(q);
+      K spr, spi, smr, smi, A1, A2;
+      T B1, B2;
+      zsym_unpack(zs[q], spr, spi, smr, smi);
+      phase_unpack(phase[q], A1, A2, B1, B2);
+      C y0, y1, y2, z0, z1, z2;
       C j0 = s[pq], j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
       if (fam == 0) j1 = s[P + pq];
       if (fam == 0) {
@@ -429,60 +500,80 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
         v.y *= f;
         src[c * sstride + q] = v;
       }
-      continue;
     }
-    C x0 = s[pq], x1 = s[P + pq], x2 = s[2 * P + pq];
-    C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0);
-    if (hasJ) {
-      j0 = s[3 * P + pq];
-      if (fam == 0) j1 = s[4 * P + pq];
-    }
-    // Horner form of x + A1 M x + A2 M^2 x - dt (xJ + B1 M xJ + B2 M^2 xJ):
-    //   p = x - dt xJ,  q = A1 x - dt B1 xJ,  u = A2 x - dt B2 xJ,  r = p + M (q + M u)
-    // (x_J = (eJ, aJ, 0) for TM, (cJ, 0, 0) for TE)
-    const T dB1 = dt * B1, dB2 = dt * B2;
-    C u0 = cscale(A2, x0), u1 = cscale(A2, x1), u2 = cscale(A2, x2);
-    C q0 = cscale(A1, x0), q1 = cscale(A1, x1), q2 = cscale(A1, x2);
-    C p0 = x0, p1 = x1;
-    if (hasJ) {
-      u0.x -= dB2 * j0.x; u0.y -= dB2 * j0.y;
-      u1.x -= dB2 * j1.x; u1.y -= dB2 * j1.y;
-      q0.x -= dB1 * j0.x; q0.y -= dB1 * j0.y;
-      q1.x -= dB1 * j1.x; q1.y -= dB1 * j1.y;
-      p0.x -= dt * j0.x; p0.y -= dt * j0.y;
-      p1.x -= dt * j1.x; p1.y -= dt * j1.y;
-    }
-    if (fam == 0) {
-      apply_tm(u0, u1, u2, y0, y1, y2, lam, spr, spi, smr, smi);
-      y0 = cadd(y0, q0); y1 = cadd(y1, q1); y2 = cadd(y2, q2);
-      apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
-    } else {
-      apply_te(u0, u1, u2, y0, y1, y2, lam, spr, spi, smr, smi);
-      y0 = cadd(y0, q0); y1 = cadd(y1, q1); y2 = cadd(y2, q2);
-      apply_te(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
-    }
-    C r0 = cadd(p0, z0), r1 = cadd(p1, z1), r2 = cadd(x2, z2);
-    r0.x *= inv; r0.y *= inv;
-    r1.x *= inv; r1.y *= inv;
-    r2.x *= inv; r2.y *= inv;
-    if (MODE == MAIN && args.src) {
-      r0 = cadd(r0, src[q]);
-      r1 = cadd(r1, src[sstride + q]);
-      r2 = cadd(r2, src[2 * sstride + q]);
-    }
-    s[pq] = r0;
-    s[P + pq] = r1;
-    s[2 * P + pq] = r2;
+    return;
   }
-  if (MODE == SOURCE) return;
+  // forward transforms: every pass but the last for all columns, the last pass for the current
+  // columns (their kz values are read by any butterfly of the fused step below)
+  constexpr int LR = R == 8 ? 3 : 2;
+  const int lnbf = L - LR, nbf = 1 << lnbf;
+  const C* twl = fft_all<R, false, NT, G, BPT, false, true>(s, narr, L, tw);
+  if (narr > 3) stockham_pass<R, false, NT, G * BPT, true>(s, 3, narr - 3, L, nbf, twl);
+  // fused, per butterfly jb of the last forward pass of the three field columns: the pass (in
+  // registers), the exact rotation of its R kz values jb + r Nz/R, and the first (transposed) inverse
+  // pass, which reads and writes exactly those elements - no barrier between them
+  for (int jb = threadIdx.x; jb < nbf; jb += NT) {
+    C v[3][R];
+    const C* t = twl + jb * (R - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[a][r] = s[a * P + padx(jb + (r << lnbf))];
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[a][r] = cmul(v[a][r], t[r - 1]);
+      dft_small<R, false>(v[a]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int q = jb + (r << lnbf);
+      const int pq = padx(q);
+      K spr, spi, smr, smi, A1, A2;
+      T B1, B2;
+      zsym_unpack(zs[q], spr, spi, smr, smi);
+      phase_unpack(phase[q], A1, A2, B1, B2);
+      C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0);
+      if (hasJ) {
+        j0 = s[3 * P + pq];
+        if (fam == 0) j1 = s[4 * P + pq];
+      }
+      rotate_point<T, K, C>(v[0][r], v[1][r], v[2][r], j0, j1, hasJ, fam, lam, spr, spi, smr, smi, A1, A2, B1, B2,
+                            dt, inv);
+      if (MODE == MAIN && args.src) {
+        v[0][r] = cadd(v[0][r], src[q]);
+        v[1][r] = cadd(v[1][r], src[sstride + q]);
+        v[2][r] = cadd(v[2][r], src[2 * sstride + q]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dft_small<R, true>(v[a]);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[a][r] = cmulconj(v[a][r], t[r - 1]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[a * P + padx(jb + (r << lnbf))] = v[a][r];
+    }
+  }
   __syncthreads();
-  // inverse transform; the last radix-R pass writes the result (or its bf16 split pieces) to global
-  const C* twl = fft_all<R, true, NT, G, BPT, true, true>(s, 3, L, tw);
+  // remaining inverse passes: transposes of the forward radix-R passes in reverse order (each pass
+  // table sits before the next pass's in the forward layout), then the first forward pass's
+  // transpose, which writes the result (or its bf16 split pieces) to global memory
+  const int rem = L % LR, npass = L / LR;
+  const C* tp = twl;
+  for (int p = npass - 2; p >= (rem ? 0 : 1); --p) {
+    const int Nsp = (1 << rem) << (LR * p);
+    if (Nsp > 1) tp -= Nsp * (R - 1);
+    pass_all_T<R, NT, G * BPT, G>(s, 3, L, Nsp, tp);
+  }
   C* out = reinterpret_cast<C*>(args.coef);
   C* dst[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) dst[a] = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
-  last_pass_to_global<R, NT, 3 * BPT, SPLIT_OUT>(s, L, twl, dst, args, idx, md, j);
+  if (rem == 1)
+    last_pass_T_to_global<2, NT, 3 * BPT * (R / 2), SPLIT_OUT>(s, L, dst, args, idx, md, j);
+  else if (rem == 2)
+    last_pass_T_to_global<4, NT, 3 * BPT * (R / 4), SPLIT_OUT>(s, L, dst, args, idx, md, j);
+  else
+    last_pass_T_to_global<R, NT, 3 * BPT, SPLIT_OUT>(s, L, dst, args, idx, md, j);
 }
 
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT, int MODE,
