@@ -25,7 +25,7 @@ COUNTS = [1, 100, 1000]
 # trip differ from the identity by the same small operator every step (coherent), on top of the
 # random rounding of the FP32 state.  None of the FP32-state paths reaches 1e-6 after 1000 steps.
 BOUND = {"fp64": [3e-12, 3e-10, 3e-9], "fp32": [1e-6, 1.5e-5, 2e-4],
-         "bf16x6": [1e-5, 5e-4, 5e-3], "bf16x3": [3e-5, 1.2e-3, 1.2e-2]}
+         "bf16x6": [1e-6, 2.5e-4, 2.5e-3], "bf16x3": [3e-5, 1.2e-3, 1.2e-2]}
 W = inputs.workload("lwfa_m01_2048x256")
 QS = [128, 120, 140, 1, 700]   # q = Nz dz = 128 is the carrier kz = 2 pi; 1 and 700 lie outside the band
 
