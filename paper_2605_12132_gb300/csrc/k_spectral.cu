@@ -279,14 +279,14 @@ __device__ __forceinline__ void pass_all_T(C* s, int narr, int logN, int Ns, con
 // The last transposed pass (Ns = 1, no twiddles) of the three field columns, storing straight to
 // global memory: butterfly j writes z = j + r N/RR, consecutive across threads.
 template <int RR, int NT, int MAXB, bool SPLIT_OUT, typename C>
-__device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* const* dst, const SpectralArgs& args,
-                                                      const int* cidx, int md, int jcol) {
+__device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* const* dst, const SplitColumn* sc) {
   constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
   const int N = 1 << logN;
   const int lnbf = logN - LR, nbf = 1 << lnbf;
   const int total = 3 << lnbf;
   const int P = N + (N >> 3);
-#pragma unroll
+  // the bf16 split stores are kept rolled: unrolled, they push the kernel out of the instruction cache
+#pragma unroll(SPLIT_OUT ? 1 : MAXB)
   for (int i = 0; i < MAXB; ++i) {
     const int b = threadIdx.x + i * NT;
     if (b < total) {
@@ -301,8 +301,7 @@ __device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* c
         if (!SPLIT_OUT)
           dst[a][z] = v[r];
         else
-          split_store(args.split_out, args.npieces, md, cidx[a], jcol, z, args.split_kstages, N, (float)v[r].x,
-                      (float)v[r].y);
+          split_store(sc[a], z, (float)v[r].x, (float)v[r].y);
       }
     }
   }
@@ -568,12 +567,17 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   C* dst[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) dst[a] = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
+  SplitColumn sc[3];
+  if (SPLIT_OUT) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sc[a] = split_column(args.split_out, args.npieces, md, idx[a], j, args.split_kstages, Nz);
+  }
   if (rem == 1)
-    last_pass_T_to_global<2, NT, 3 * BPT * (R / 2), SPLIT_OUT>(s, L, dst, args, idx, md, j);
+    last_pass_T_to_global<2, NT, 3 * BPT * (R / 2), SPLIT_OUT>(s, L, dst, sc);
   else if (rem == 2)
-    last_pass_T_to_global<4, NT, 3 * BPT * (R / 4), SPLIT_OUT>(s, L, dst, args, idx, md, j);
+    last_pass_T_to_global<4, NT, 3 * BPT * (R / 4), SPLIT_OUT>(s, L, dst, sc);
   else
-    last_pass_T_to_global<R, NT, 3 * BPT, SPLIT_OUT>(s, L, dst, args, idx, md, j);
+    last_pass_T_to_global<R, NT, 3 * BPT, SPLIT_OUT>(s, L, dst, sc);
 }
 
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT, int MODE,

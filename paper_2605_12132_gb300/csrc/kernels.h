@@ -30,24 +30,42 @@ size_t spectral_smem_bytes(int Nz, int precision, bool hasJ);
 int spectral_twiddles(int Nz, int precision, double* re, double* im);
 bool spectral_needs_source(int Nz, int precision, int tw_count);
 
-// bf16 split of an FP32 value into npieces (2 or 3) terms whose sum reproduces it to
-// 16 / 24 significant bits, stored in the pre-tiled operand layout of the back-projection:
-// 16 KB blocks (md, piece, c, ks = j / 64, zb = z / 64), each [2 halves][64 j rows][128 B]
-// holding (z, re/im) pairs of 64 z along N, the 16-byte chunks of a row swizzled by (j & 7)
-// (the 128-byte swizzle the MMA descriptor expects).
-__device__ __forceinline__ void split_store(__nv_bfloat16* out, int npieces, int md, int c, int j, int z, int kst,
-                                            int Nz, float vr, float vi) {
+// bf16 split of FP32 values into npieces (2 or 3) terms whose sum reproduces them to 16 / 24
+// significant bits, stored in the pre-tiled operand layout of the back-projection: 16 KB blocks
+// (md, piece, c, ks = j / 64, zb = z / 64), each [2 halves][64 j rows][128 B] holding (z, re/im)
+// pairs of 64 z along N, the 16-byte chunks of a row swizzled by (j & 7) (the 128-byte swizzle the
+// MMA descriptor expects).  SplitColumn holds what is fixed for one coefficient column (md, c, j).
+struct SplitColumn {
+  unsigned char* base;  // block (md, piece 0, c, j / 64, zb = 0) + row (j & 63)
+  size_t piece_stride;  // bytes between pieces: 6 kst (Nz / 64) 16 KB
+  int npieces, jr7;     // pieces; j & 7
+};
+
+__device__ __forceinline__ SplitColumn split_column(__nv_bfloat16* out, int npieces, int md, int c, int j, int kst,
+                                                    int Nz) {
+  SplitColumn d;
+  const size_t nzb = (size_t)(Nz >> 6);
+  d.base = reinterpret_cast<unsigned char*>(out) +
+           (((((size_t)md * npieces) * 6 + c) * kst + (j >> 6)) * nzb) * 16384 + (size_t)(j & 63) * 128;
+  d.piece_stride = (size_t)6 * kst * nzb * 16384;
+  d.npieces = npieces;
+  d.jr7 = j & 7;
+  return d;
+}
+
+__device__ __forceinline__ void split_store(const SplitColumn& d, int z, float vr, float vi) {
+  const int zl = z & 63;
+  const size_t off = (size_t)(z >> 6) * 16384 + (size_t)(zl >> 5) * 8192 +
+                     ((uint32_t)(((zl & 31) >> 2) ^ d.jr7) << 4) + (uint32_t)(zl & 3) * 4u;
+  unsigned char* q = d.base + off;
   float r0 = vr, r1 = vi;
-  const int zl = z & 63, jr = j & 63;
-  const uint32_t off = (uint32_t)(zl >> 5) * 8192u + (uint32_t)jr * 128u +
-                       ((uint32_t)(((zl & 31) >> 2) ^ (jr & 7)) << 4) + (uint32_t)(zl & 3) * 4u;
-  for (int p = 0; p < npieces; ++p) {
+  for (int p = 0; p < d.npieces; ++p) {
     const __nv_bfloat16 h0 = __float2bfloat16_rn(r0), h1 = __float2bfloat16_rn(r1);
     __nv_bfloat162 pr;
     pr.x = h0;
     pr.y = h1;
-    const size_t blk = ((((size_t)md * npieces + p) * 6 + c) * kst + (j >> 6)) * (size_t)(Nz >> 6) + (z >> 6);
-    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<unsigned char*>(out) + blk * 16384 + off) = pr;
+    *reinterpret_cast<__nv_bfloat162*>(q) = pr;
+    q += d.piece_stride;
     r0 -= __bfloat162float(h0);
     r1 -= __bfloat162float(h1);
   }
