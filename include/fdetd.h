@@ -65,6 +65,7 @@ enum {
 typedef struct fdetd_plan_s* fdetd_plan_t;
 typedef struct fdetd_batch_s* fdetd_batch_t;
 typedef struct envelope_plan_s* envelope_plan_t;
+typedef struct fdetd_taylor_s* fdetd_taylor_t;
 
 /*
  * fdetd_plan - build the exact exponential step of modes m = 0..M.
@@ -165,6 +166,34 @@ int fdetd_plan_set_tile_config(fdetd_plan_t plan, const int* cfg);
  * expired.
  */
 int fdetd_probe_mma_rounding(float* host_out, int reps, void* stream);
+
+/*
+ * The paper's own time stepper (Sec. 2.5 summary, Eq. maxwellAM_solution2): both exponentials of the
+ * midpoint step replaced by N-term Taylor polynomials of the real-space operator H, applied by
+ * banded stencils (no radial transform):
+ *     Psi <- T_N(h H)^S Psi - dt T_N(h' H)^S' J_state,   T_N(A) = sum_{n<=N} A^n / n!,
+ * h = dt / S, h' = (dt / 2) / S', S' = max(1, S / 2), J_state = (J_rho, J_theta, J_z, 0, 0, 0).
+ * H is the operator of fdetd_plan (same stencils, axis treatment and periodic z); the result is the
+ * exact step only up to the Taylor truncation, and it is stable only for dt small enough that
+ * h |H| lies in the Taylor polynomial's stability region.
+ *
+ * fdetd_taylor_plan: taylor_order N in 2..32, substeps S in 1..1024; modes as for
+ * fdetd_plan_modes; FP32 (complex64 fields, same layout as fdetd_step).  Allocates five field-sized
+ * work arrays.  fdetd_taylor_step advances `fields` (device) in place by nsteps steps on `stream`;
+ * J (device, [modes][3][Nz][Nr]) or NULL is constant over the call (its source term is computed once
+ * per call).  The axis slots of E_rho, B_theta, B_z are written from the interior values at the end
+ * of the call (Sec. 2.4).  Errors: FDETD_ERR_ARG, FDETD_ERR_OOM, FDETD_ERR_CUDA (fdetd_last_error).
+ * fdetd_taylor_launches_per_step = N S term kernels (plus one axis kernel per call).
+ * fdetd_taylor_host_bands (host only): the four banded radial operators [4][Nr][order+1] and the axis
+ * weights [2][order/2] of mode m, as the kernels use them (layout in csrc/plan_host.cpp).
+ */
+int fdetd_taylor_plan(fdetd_taylor_t* out, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
+                      double dr, double dt, int taylor_order, int substeps);
+int fdetd_taylor_step(fdetd_taylor_t plan, void* fields, const void* J, int nsteps, void* stream);
+int fdetd_taylor_launches_per_step(fdetd_taylor_t plan);
+int fdetd_taylor_destroy(fdetd_taylor_t plan);
+int fdetd_taylor_host_bands(int Nr, int order, double dr, int m, double* bands, double* axis);
+
 
 
 /*

@@ -24,6 +24,10 @@ from ._native import (  # noqa: F401
     fdetd_plan,
     fdetd_plan_modes,
     fdetd_probe_mma_rounding,
+    TaylorPlan,
+    fdetd_taylor_host_bands,
+    fdetd_taylor_plan,
+    fdetd_taylor_step,
     fdetd_step,
     fdetd_step_host,
     lib,

@@ -58,6 +58,12 @@ def lib():
     L.fdetd_plan_tile_config.argtypes = [c_vp, ctypes.POINTER(c_int)]
     L.fdetd_plan_set_tile_config.argtypes = [c_vp, ctypes.POINTER(c_int)]
     L.fdetd_probe_mma_rounding.argtypes = [ctypes.POINTER(ctypes.c_float), c_int, c_vp]
+    L.fdetd_taylor_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, ctypes.POINTER(c_int), c_int, c_int, c_dbl,
+                                    c_dbl, c_dbl, c_int, c_int]
+    L.fdetd_taylor_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.fdetd_taylor_launches_per_step.argtypes = [c_vp]
+    L.fdetd_taylor_destroy.argtypes = [c_vp]
+    L.fdetd_taylor_host_bands.argtypes = [c_int, c_int, c_dbl, c_int, dp, dp]
     L.fdetd_batch_launch.argtypes = [c_vp, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
     L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
@@ -219,6 +225,66 @@ def fdetd_host_tables(Nz, Nr, m, order, dz, dr, dt):
     out["sp"] = sp[0::2] + 1j * sp[1::2]
     out["sm"] = sm[0::2] + 1j * sm[1::2]
     return out
+
+
+class TaylorPlan:
+    """The paper's Taylor-polynomial time stepper on the GPU (see include/fdetd.h)."""
+
+    def __init__(self, handle, Nz, Nr, modes, order, dz, dr, dt, taylor_order, substeps):
+        self.handle = handle
+        self.Nz, self.Nr, self.modes, self.order = Nz, Nr, list(modes), order
+        self.dz, self.dr, self.dt = dz, dr, dt
+        self.taylor_order, self.substeps = taylor_order, substeps
+        self.precision = "fp32"
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex64
+
+    @property
+    def launches_per_step(self):
+        return lib().fdetd_taylor_launches_per_step(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().fdetd_taylor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fdetd_taylor_plan(Nz, Nr, modes, order, dz, dr, dt, taylor_order=4, substeps=1):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * len(modes))(*modes)
+    _check(lib().fdetd_taylor_plan(ctypes.byref(h), Nz, Nr, arr, len(modes), order, dz, dr, dt, taylor_order,
+                                   substeps))
+    return TaylorPlan(h, Nz, Nr, modes, order, dz, dr, dt, taylor_order, substeps)
+
+
+def fdetd_taylor_step(plan, fields, J=None, nsteps=1, stream=None):
+    """Advance cuda complex64 `fields` [modes][6][Nz][Nr] in place by nsteps Taylor steps."""
+    if not fields.is_cuda:
+        raise FdetdError("fields must be a CUDA tensor")
+    _check_tensor(fields, plan, 6, "fields")
+    jp = None
+    if J is not None:
+        _check_tensor(J, plan, 3, "J")
+        jp = J.data_ptr()
+    _check(lib().fdetd_taylor_step(plan.handle, fields.data_ptr(), jp, nsteps, _stream_handle(stream)))
+    return fields
+
+
+def fdetd_taylor_host_bands(Nr, order, dr, m):
+    """Host-only: the four banded radial operators [4][Nr][order+1] and axis weights [2][order/2]."""
+    bands = np.zeros((4, Nr, order + 1))
+    axis = np.zeros((2, order // 2))
+    _check(lib().fdetd_taylor_host_bands(Nr, order, dr, m, _dptr(bands), _dptr(axis)))
+    return bands, axis
 
 
 def fdetd_probe_mma_rounding(reps=1, stream=None):

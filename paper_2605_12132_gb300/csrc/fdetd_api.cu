@@ -22,6 +22,8 @@ static int fail(int code, const std::string& msg) {
   return code;
 }
 
+int fdetd::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 static df to_df(double x) {
   df r;
   r.h = (float)x;

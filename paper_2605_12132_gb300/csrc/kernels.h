@@ -5,7 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace fdetd {
+
+// Records an error message for fdetd_last_error and returns code (defined in fdetd_api.cu).
+int set_error(int code, const std::string& msg);
 
 // ---------------------------------------------------------------- spectral kernel
 struct SpectralArgs {

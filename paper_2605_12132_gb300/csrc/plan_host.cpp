@@ -489,6 +489,47 @@ static int build_mode(ModePlan& P, int n, int order, double dr, int m, std::stri
   return 0;
 }
 
+// Banded radial operators of the real-space operator H of one mode (Sec. 2.5), for the paper's
+// Taylor scheme.  Row k of band b holds the coefficients of columns k - ND .. k + ND (zero outside
+// 0..n-1), W = 2 ND + 1 per row, bands [4][n][W]:
+//   0: D^+ acting on B_z with its axis value (the Sec. 2.4 extrapolation for m = 0) folded into
+//      columns 1..ND, column 0 zero            (E_theta_t = D_z^+ B_rho - band0 B_z ...)
+//   1: rho_k^-1 D^+ rho_-,j on B_theta         (E_z_t = ... + band1 B_theta)
+//   2: D^- on E_z, row 0 zero                  (B_theta_t = ... + band2 E_z)
+//   3: rho_-,k^-1 D^- rho_j on E_theta, row 0 zero (B_z_t = ... - band3 E_theta)
+// axis[2][ND]: extrapolation weights of the axis slot from slots 1..ND for the polar fields
+// (E_rho, B_theta; nonzero for m = 1) and the scalar field (B_z; nonzero for m = 0).
+int taylor_bands(int n, int order, double dr, int m, std::vector<double>& bands, std::vector<double>& axis) {
+  if (order < 2 || order > 32 || (order & 1) || n < order / 2 + 2) return 1;
+  const std::vector<double> c = staggered_coeffs(order);
+  const int ND = order / 2, W = 2 * ND + 1;
+  const int parity = m & 1;
+  Mat Dm = d_minus(n, c, dr, parity), Dp = d_plus(n, c, dr, parity);
+  const std::vector<double> ax = axis_coeffs(ND);
+  std::vector<double> w_scalar(n, 0.0);
+  for (int k = 0; k < ND; ++k)
+    if (m == 0) w_scalar[k + 1] = ax[k];  // weight of slot k + 1 in the B_z axis value
+  bands.assign((size_t)4 * n * W, 0.0);
+  auto B = [&](int b, int k, int j) -> double& { return bands[((size_t)b * n + k) * W + (j - k + ND)]; };
+  for (int k = 0; k < n; ++k) {
+    const double rho = (k + 0.5) * dr, rhom = k * dr;
+    for (int j = std::max(0, k - ND); j <= std::min(n - 1, k + ND); ++j) {
+      if (j >= 1) B(0, k, j) = Dp(k, j) + Dp(k, 0) * w_scalar[j];
+      B(1, k, j) = Dp(k, j) * (j * dr) / rho;
+      if (k >= 1) {
+        B(2, k, j) = Dm(k, j);
+        B(3, k, j) = Dm(k, j) * ((j + 0.5) * dr) / rhom;
+      }
+    }
+  }
+  axis.assign((size_t)2 * ND, 0.0);
+  for (int k = 0; k < ND; ++k) {
+    if (m == 1) axis[k] = ax[k];
+    if (m == 0) axis[ND + k] = ax[k];
+  }
+  return 0;
+}
+
 int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
                     double dr, double dt, std::string& msg) {
   if (order < 2 || order > 32 || (order & 1)) {

@@ -133,3 +133,40 @@ def test_plan_errors_are_reported():
         native.fdetd_host_tables(16, 8, 0, 7, 0.1, 0.1, 0.1)
     with pytest.raises(native.FdetdError):
         native.fdetd_host_tables(16, 3, 0, 8, 0.1, 0.1, 0.1)
+
+
+def _dense_from_bands(band, order):
+    n = band.shape[0]
+    ND = order // 2
+    A = np.zeros((n, n))
+    for k in range(n):
+        for t in range(2 * ND + 1):
+            j = k - ND + t
+            if 0 <= j < n:
+                A[k, j] = band[k, t]
+    return A
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+@pytest.mark.parametrize("order", [4, 8, 16])
+def test_taylor_bands_reproduce_oracle_radial_operators(m, order):
+    """The banded operators of the Taylor stepper are the oracle's radial blocks of H (Sec. 2.5)."""
+    _lib_or_skip()
+    Nr, dr = 23, 0.25
+    rad = mx.Radial(Nr, order, dr, m)
+    bands, axis = native.fdetd_taylor_host_bands(Nr, order, dr, m)
+    dense = [_dense_from_bands(bands[b], order) for b in range(4)]
+    # band 0 acts on B_z slots 1.. with the axis value folded in: D^+ X0
+    A0 = rad.Dp @ rad.X0
+    assert np.allclose(dense[0][:, 1:], A0, atol=1e-12 * np.abs(A0).max()) and np.all(dense[0][:, 0] == 0)
+    A1 = rad.Dp * rad.rhom[None, :] / rad.rho[:, None]
+    assert np.allclose(dense[1], A1, atol=1e-12 * np.abs(A1).max())
+    A2 = rad.Dm.copy()
+    A2[0] = 0
+    assert np.allclose(dense[2], A2, atol=1e-12 * np.abs(A2).max())
+    A3 = np.zeros_like(rad.Dm)
+    A3[1:] = rad.Dm[1:] * rad.rho[None, :] / rad.rhom[1:, None]
+    assert np.allclose(dense[3], A3, atol=1e-12 * np.abs(A3).max())
+    ND = order // 2
+    assert np.allclose(axis[0], rad.axis_polar[:ND]) and np.all(rad.axis_polar[ND:] == 0)
+    assert np.allclose(axis[1], rad.axis_scalar[:ND]) and np.all(rad.axis_scalar[ND:] == 0)
