@@ -241,6 +241,51 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_taylor(args, w):
+    """The paper's Taylor-polynomial stepper (banded stencils, FP32) on the same workload; its error after one
+    step against the exact exponential step (FP64 path) is reported beside the throughput."""
+    import torch
+    import paper_2605_12132_gb300 as fd
+    from paper_2605_12132_gb300 import inputs
+    F, J = inputs.workload_inputs(w)
+    plan = fd.fdetd_taylor_plan(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, args.taylor_order, args.substeps)
+    f0 = torch.from_numpy(F).to(torch.complex64).cuda()
+    Jd = torch.from_numpy(J).to(torch.complex64).cuda() if J is not None else None
+    f = f0.clone()
+    fd.fdetd_taylor_step(plan, f, Jd, 1)
+    torch.cuda.synchronize()
+    p64 = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision="fp64")
+    x64 = torch.from_numpy(F).cuda()
+    fd.fdetd_step(p64, x64, torch.from_numpy(J).cuda() if J is not None else None, 1)
+    torch.cuda.synchronize()
+    a, b = f.cpu().numpy().astype(np.complex128), x64.cpu().numpy()
+    err = max(float(np.linalg.norm(a[i, c] - b[i, c]) / max(np.linalg.norm(b[i, c]), 0.1 * np.linalg.norm(b[i])))
+              for i in range(len(w.modes)) for c in range(6))
+    p64.close()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        fd.fdetd_taylor_step(plan, f, Jd, 1)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        fd.fdetd_taylor_step(plan, f, Jd, 1)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in evs)
+    cells = w.Nz * w.Nr * len(w.modes)
+    line = {"metric": METRIC + " [paper's Taylor stepper]", "value": cells * args.steps / (ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian pulse + seeded smooth random current)",
+            "config": {"workload": w.name, "taylor_order": args.taylor_order, "substeps": args.substeps,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "error_vs_exact_step": err, "launches_per_step": plan.launches_per_step + 1}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Poisson stream of field- and envelope-advance requests through the continuous-batching server."""
     import torch
@@ -291,7 +336,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "taylor"])
+    ap.add_argument("--taylor-order", type=int, default=4)
+    ap.add_argument("--substeps", type=int, default=1)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=10.0)
@@ -310,6 +357,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "taylor":
+        return run_taylor(args, w)
 
     import torch
     import paper_2605_12132_gb300 as fd
