@@ -304,9 +304,30 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
           const int item = threadIdx.x + it * 128;  // 64 z x 4 chunks of 8 r
           const int zl = item >> 2, c = item & 3;
           const float4* src = reinterpret_cast<const float4*>(stg + zl * 64 + c * 16);
+          // read the four 16-byte pieces in an order rotated by (c + zl): a warp's 32 reads then fall
+          // on all eight 16-byte bank groups (4 wavefronts) instead of two; t[k] is re-rotated after
+          const int rot = (c + zl) & 3;
+          float4 t[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) t[k] = src[(k + rot) & 3];
+          if (rot & 1) {
+            const float4 x = t[3];
+            t[3] = t[2];
+            t[2] = t[1];
+            t[1] = t[0];
+            t[0] = x;
+          }
+          if (rot & 2) {
+            float4 x = t[0];
+            t[0] = t[2];
+            t[2] = x;
+            x = t[1];
+            t[1] = t[3];
+            t[3] = x;
+          }
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const float4 v = src[k];
+            const float4 v = t[k];
             // radii beyond Nr are zero-filled by the TMA box; masked here as well
             const bool in0 = r0 + c * 8 + 2 * k < n, in1 = r0 + c * 8 + 2 * k + 1 < n;
             re[it][2 * k] = in0 ? v.x : 0.f;
@@ -345,9 +366,13 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
               im[it][2 * k] -= __low2float(hi);
               im[it][2 * k + 1] -= __high2float(hi);
             }
+            // even z rows store re first, odd ones im first: each store instruction of a warp then
+            // covers all eight 16-byte bank groups
             unsigned char* Pp = A + p * 8192;
-            *reinterpret_cast<uint4*>(Pp + off_re) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-            *reinterpret_cast<uint4*>(Pp + off_im) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            const bool odd = zl & 1;
+            const uint4 vr = make_uint4(wr[0], wr[1], wr[2], wr[3]), vi = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            *reinterpret_cast<uint4*>(Pp + (odd ? off_im : off_re)) = odd ? vi : vr;
+            *reinterpret_cast<uint4*>(Pp + (odd ? off_re : off_im)) = odd ? vr : vi;
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
