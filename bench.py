@@ -286,6 +286,44 @@ def run_taylor(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_destagger(args, w):
+    """Destagger of the workload's fields to the primary grids (HBM-bound: 12 complex values per cell*mode)."""
+    import torch
+    import paper_2605_12132_gb300 as fd
+    from paper_2605_12132_gb300 import inputs
+    prec = args.precision or "bf16x6"
+    F, _ = inputs.workload_inputs(w)
+    plan = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision=prec)
+    f = torch.from_numpy(F).to(plan.complex_dtype).cuda()
+    out = torch.empty_like(f)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        fd.fdetd_destagger(plan, f, out)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        fd.fdetd_destagger(plan, f, out)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in evs) / args.steps
+    cells = w.Nz * w.Nr * len(w.modes)
+    algo = cells * 12 * f.element_size()
+    peaks, src = _peaks()
+    roof = {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"traffic": None, "algorithmic": algo, "kernel": "destagger", "peak_source": src})
+    line = {"metric": "destaggered cell*mode/s (fields moved to the primary grids)", "value": cells / (ms / 1e3),
+            "unit": "cell*mode/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic (seeded Gaussian pulse)",
+            "config": {"workload": w.name, "precision": prec, "l2": "flushed between timed calls (256 MiB write)"},
+            "roofline": roof}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Poisson stream of field- and envelope-advance requests through the continuous-batching server."""
     import torch
@@ -336,7 +374,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "taylor"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "taylor", "destagger"])
     ap.add_argument("--taylor-order", type=int, default=4)
     ap.add_argument("--substeps", type=int, default=1)
     ap.add_argument("--instances", type=int, default=64)
@@ -359,6 +397,8 @@ def main():
         return run_serve(args)
     if args.mode == "taylor":
         return run_taylor(args, w)
+    if args.mode == "destagger":
+        return run_destagger(args, w)
 
     import torch
     import paper_2605_12132_gb300 as fd

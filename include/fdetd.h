@@ -101,6 +101,20 @@ int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* modes, int nm
  */
 int fdetd_step(fdetd_plan_t plan, void* fields, const void* J, int nsteps, void* stream);
 
+/*
+ * fdetd_destagger - move the field modes from the Yee grid to the primary grids z_i = i dz,
+ * rho_k = (k + 1/2) dr (Sec. 3 field interpolation, Eqs. shapesAM_destagger_E, _B, _Bth), with
+ * the upstaggering Lagrange interpolation S^(+) of Eq. spatialAM_staggerS at the plan's order:
+ *     E_rho -> S_rho^(+, mA) E_rho,  E_z -> S_z^(+) E_z,  B_rho -> S_z^(+) B_rho,
+ *     B_z -> S_rho^(+, mS) B_z,  B_theta -> S_rho^(+, mA) S_z^(+) B_theta,  E_theta copied.
+ * z is periodic; radially the axis slot 0 of E_rho, B_theta, B_z must hold the axis value (as
+ * fdetd_step writes it), nodes below the axis are mirror images with the symmetric or
+ * antisymmetric extension of Eqs. spatialAM_derivativeS/A, nodes past the outer edge are dropped.
+ * fields: device, layout and precision of fdetd_step (read only); out: device, same layout, all
+ * six fields on the primary grids; must not overlap fields.  Asynchronous on `stream`.
+ */
+int fdetd_destagger(fdetd_plan_t plan, const void* fields, void* out, void* stream);
+
 /* End-to-end variant with HOST arrays (same layouts): copies fields (and J) to the
  * device, runs fdetd_step, copies the fields back; synchronises `stream`. */
 int fdetd_step_host(fdetd_plan_t plan, void* host_fields, const void* host_J, int nsteps, void* stream);

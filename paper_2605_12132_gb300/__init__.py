@@ -19,6 +19,7 @@ from ._native import (  # noqa: F401
     envelope_plan,
     envelope_step,
     envelope_step_static,
+    fdetd_destagger,
     fdetd_host_coeffs,
     fdetd_host_tables,
     fdetd_plan,

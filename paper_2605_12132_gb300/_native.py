@@ -36,6 +36,7 @@ def lib():
                                    c_dbl, c_dbl, c_dbl, c_int, c_u64]
     L.fdetd_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.fdetd_step_host.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.fdetd_destagger.argtypes = [c_vp, c_vp, c_vp, c_vp]
     L.fdetd_plan_device_bytes.argtypes = [c_vp]
     L.fdetd_plan_device_bytes.restype = ctypes.c_size_t
     L.fdetd_plan_launches_per_step.argtypes = [c_vp]
@@ -196,6 +197,19 @@ def fdetd_step(plan, fields, J=None, nsteps=1, stream=None):
         jp = J.data_ptr()
     _check(lib().fdetd_step(plan.handle, fields.data_ptr(), jp, nsteps, _stream_handle(stream)))
     return fields
+
+
+def fdetd_destagger(plan, fields, out=None, stream=None):
+    """Fields of `plan` on the Yee grid -> all six on the primary grids (new tensor unless `out` given)."""
+    import torch
+    _check_tensor(fields, plan, 6, "fields")
+    if not fields.is_cuda:
+        raise FdetdError("fields must be a CUDA tensor")
+    if out is None:
+        out = torch.empty_like(fields)
+    _check_tensor(out, plan, 6, "out")
+    _check(lib().fdetd_destagger(plan.handle, fields.data_ptr(), out.data_ptr(), _stream_handle(stream)))
+    return out
 
 
 def fdetd_step_host(plan, host_fields, host_J=None, nsteps=1, stream=None):

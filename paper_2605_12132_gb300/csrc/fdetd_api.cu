@@ -467,6 +467,19 @@ extern "C" int fdetd_plan_set_tile_config(fdetd_plan_t p, const int* cfg) {
   return FDETD_OK;
 }
 
+extern "C" int fdetd_destagger(fdetd_plan_t p, const void* fields, void* out, void* stream) {
+  if (!p || !fields || !out) return fail(FDETD_ERR_ARG, "null argument");
+  if (fields == out) return fail(FDETD_ERR_ARG, "out must not alias fields");
+  const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
+  const size_t bytes = (size_t)p->nmodes * 6 * p->Nz * p->Nr * elt;
+  const char *a = (const char*)fields, *b = (const char*)out;
+  if (a < b + bytes && b < a + bytes) return fail(FDETD_ERR_ARG, "out must not overlap fields");
+  cudaError_t e = launch_destagger(fields, out, p->Nz, p->Nr, p->order, p->modes.data(), p->nmodes,
+                                   p->precision == FDETD_PREC_FP64, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("destagger: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_step_host(fdetd_plan_t p, void* host_fields, const void* host_J, int nsteps, void* stream) {
   if (!p || !host_fields) return fail(FDETD_ERR_ARG, "null argument");
   const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;

@@ -149,6 +149,10 @@ cudaError_t tc_group_project(TcGroup* g, cudaStream_t st);
 cudaError_t tc_group_backproject(TcGroup* g, cudaStream_t st);
 int tc_group_tiles(const TcGroup* g, int which);
 
+// ---------------------------------------------------------------- destagger to the primary grids
+cudaError_t launch_destagger(const void* in, void* out, int Nz, int n, int order, const int* modes, int nmodes,
+                             bool fp64, cudaStream_t st);
+
 // ---------------------------------------------------------------- envelope
 struct EnvArgs {
   // One Taylor term: out = scale * H_a(in); accout = accin + out.
