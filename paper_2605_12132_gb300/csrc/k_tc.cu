@@ -304,20 +304,20 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
           const int item = threadIdx.x + it * 128;  // 64 z x 4 chunks of 8 r
           const int zl = item >> 2, c = item & 3;
           const float4* src = reinterpret_cast<const float4*>(stg + zl * 64 + c * 16);
-          // read the four 16-byte pieces in an order rotated by (c + zl): a warp's 32 reads then fall
+          // read the four 16-byte pieces in an order rotated by rr = (c + zl): a warp's 32 reads then fall
           // on all eight 16-byte bank groups (4 wavefronts) instead of two; t[k] is re-rotated after
-          const int rot = (c + zl) & 3;
+          const int rr = (c + zl) & 3;
           float4 t[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) t[k] = src[(k + rot) & 3];
-          if (rot & 1) {
+          for (int k = 0; k < 4; ++k) t[k] = src[(k + rr) & 3];
+          if (rr & 1) {
             const float4 x = t[3];
             t[3] = t[2];
             t[2] = t[1];
             t[1] = t[0];
             t[0] = x;
           }
-          if (rot & 2) {
+          if (rr & 2) {
             float4 x = t[0];
             t[0] = t[2];
             t[2] = x;
