@@ -305,6 +305,18 @@ int envelope_step_static(void* a, const float* chi, int Nz, int Nr, int order, i
 /* Number of kernels one envelope step launches. */
 int envelope_plan_launches_per_step(envelope_plan_t plan);
 
+/*
+ * envelope_step_absorbing - the envelope step with the scalar absorbing layer of the appendix
+ * (Eqs. absorbingA_Adt, absorbingA_waveA with h = 1, absorbingA_solution2): per step
+ *     (a, a~) <- exp(-sigma dt / 4) T_N(dt H_a[chi + sigma^2]) exp(-sigma dt / 4) (a, a~),
+ * the damping pointwise on both components and the absorbing term sigma^2 merged into the
+ * susceptibility.  sigma: device, [Nz][Nr] float32, >= 0 (zero outside the layers); other
+ * arguments as envelope_step.  sigma = 0 gives envelope_step exactly.
+ */
+int envelope_step_absorbing(envelope_plan_t plan, void* a, const float* chi, const float* sigma, int nsteps,
+                            void* stream);
+
+
 int envelope_plan_destroy(envelope_plan_t plan);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated to len). */

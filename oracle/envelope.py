@@ -105,3 +105,19 @@ def envelope_expm(a, at, chi, order, dz, dr, t, k0=K0, m=0):
     x = scipy.linalg.expm(A * t) @ np.concatenate([a.ravel(), at.ravel()])
     n = Nz * Nr
     return x[:n].reshape(Nz, Nr), x[n:].reshape(Nz, Nr)
+
+
+def envelope_step_absorbing(a, at, chi, sigma, order, taylor_order, dz, dr, dt, nsteps=1, k0=K0, m=0):
+    """The envelope step with the scalar absorbing layer of the appendix (Eq. absorbingA_solution2).
+
+    The absorbing wave equation (Eqs. absorbingA_Adt, absorbingA_waveA with h = 1) adds -sigma/2 to
+    both components and -sigma^2 a to da~/dt; the split-operator step damps (a, a~) pointwise by
+    exp(-sigma dt / 4), applies the Taylor step of H_a with chi + sigma^2 (the sigma^2 term merged
+    into the susceptibility as the appendix suggests), and damps again.
+    """
+    damp = np.exp(-sigma * dt / 4)
+    for _ in range(nsteps):
+        a, at = a * damp, at * damp
+        a, at = envelope_step(a, at, chi + sigma ** 2, order, taylor_order, dz, dr, dt, 1, k0, m)
+        a, at = a * damp, at * damp
+    return a, at

@@ -18,6 +18,7 @@ from ._native import (  # noqa: F401
     FdetdPlan,
     envelope_plan,
     envelope_step,
+    envelope_step_absorbing,
     envelope_step_static,
     fdetd_destagger,
     fdetd_host_coeffs,

@@ -49,6 +49,7 @@ def lib():
     L.fdetd_host_coeffs.argtypes = [c_int, c_int, dp]
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.envelope_step_absorbing.argtypes = [c_vp, c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_plan_launches_per_step.argtypes = [c_vp]
     L.fdetd_batch_create.argtypes = [ctypes.POINTER(c_vp)]
     L.fdetd_batch_add.argtypes = [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_int)]
@@ -352,6 +353,19 @@ def envelope_step(plan, a, chi, nsteps=1, stream=None):
     if not chi.is_cuda or chi.dtype != torch.float32 or tuple(chi.shape) != (plan.Nz, plan.Nr) or not chi.is_contiguous():
         raise FdetdError("chi must be a contiguous cuda float32 tensor of shape (Nz, Nr)")
     _check(lib().envelope_step(plan.handle, a.data_ptr(), chi.data_ptr(), nsteps, _stream_handle(stream)))
+    return a
+
+
+def envelope_step_absorbing(plan, a, chi, sigma, nsteps=1, stream=None):
+    """Envelope step with the split-operator absorbing layer (see include/fdetd.h); sigma float32 [Nz][Nr]."""
+    import torch
+    if not a.is_cuda or a.dtype != torch.complex64 or tuple(a.shape) != (2, plan.Nz, plan.Nr) or not a.is_contiguous():
+        raise FdetdError("a must be a contiguous cuda complex64 tensor of shape (2, Nz, Nr)")
+    for name, t in (("chi", chi), ("sigma", sigma)):
+        if not t.is_cuda or t.dtype != torch.float32 or tuple(t.shape) != (plan.Nz, plan.Nr) or not t.is_contiguous():
+            raise FdetdError(f"{name} must be a contiguous cuda float32 tensor of shape (Nz, Nr)")
+    _check(lib().envelope_step_absorbing(plan.handle, a.data_ptr(), chi.data_ptr(), sigma.data_ptr(), nsteps,
+                                         _stream_handle(stream)))
     return a
 
 

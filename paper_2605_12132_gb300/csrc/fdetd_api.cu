@@ -822,6 +822,7 @@ struct envelope_plan_s {
   double dz = 0, dr = 0, dt = 0, k0 = 0;
   float* d_lr = nullptr;
   float2* d_buf = nullptr;  // T0 (a, a~), T1 (a, a~), ACC (a, a~)
+  float* d_chit = nullptr;  // chi + sigma^2 of the absorbing-layer step
   EnvArgs base;
 };
 
@@ -867,8 +868,10 @@ extern "C" int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, in
   size_t tot = 0;
   cudaError_t e = upload((void**)&p->d_lr, bandf.data(), bandf.size() * 4, tot);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_buf, (size_t)6 * Nz * Nr * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_chit, (size_t)Nz * Nr * sizeof(float));
   if (e != cudaSuccess) {
     if (p->d_lr) cudaFree(p->d_lr);
+    if (p->d_buf) cudaFree(p->d_buf);
     delete p;
     return fail(e == cudaErrorMemoryAllocation ? FDETD_ERR_OOM : FDETD_ERR_CUDA, cudaGetErrorString(e));
   }
@@ -888,6 +891,38 @@ extern "C" int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, in
   return FDETD_OK;
 }
 
+// One Taylor-N_T step of (a, a~) in place with susceptibility chi.
+static int envelope_taylor(envelope_plan_t p, float2* psi_a, float2* psi_t, const float* chi, cudaStream_t st) {
+  const size_t plane = (size_t)p->Nz * p->Nr;
+  float2* T[2][2] = {{p->d_buf, p->d_buf + plane}, {p->d_buf + 2 * plane, p->d_buf + 3 * plane}};
+  float2* ACC[2] = {p->d_buf + 4 * plane, p->d_buf + 5 * plane};
+  EnvArgs g = p->base;
+  g.chi = chi;
+  for (int n = 1; n <= p->NT; ++n) {
+    g.scale = (float)(p->dt / n);
+    if (n == 1) {
+      g.in_a = psi_a; g.in_t = psi_t;
+      g.accin_a = psi_a; g.accin_t = psi_t;
+    } else {
+      g.in_a = T[(n - 2) & 1][0]; g.in_t = T[(n - 2) & 1][1];
+      g.accin_a = ACC[0]; g.accin_t = ACC[1];
+    }
+    const bool last = n == p->NT;
+    g.out_a = last ? nullptr : T[(n - 1) & 1][0];
+    g.out_t = last ? nullptr : T[(n - 1) & 1][1];
+    const bool to_psi = last && n > 1;
+    g.accout_a = to_psi ? psi_a : ACC[0];
+    g.accout_t = to_psi ? psi_t : ACC[1];
+    cudaError_t e = launch_envelope_term(g, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
+  }
+  if (p->NT == 1) {
+    cudaError_t e = cudaMemcpyAsync(psi_a, ACC[0], 2 * plane * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return FDETD_OK;
+}
+
 extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int nsteps, void* stream) {
   if (!p || !a || !chi) return fail(FDETD_ERR_ARG, "null argument");
   if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
@@ -895,34 +930,32 @@ extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int n
   cudaStream_t st = (cudaStream_t)stream;
   const size_t plane = (size_t)p->Nz * p->Nr;
   float2* psi_a = (float2*)a;
-  float2* psi_t = psi_a + plane;
-  float2* T[2][2] = {{p->d_buf, p->d_buf + plane}, {p->d_buf + 2 * plane, p->d_buf + 3 * plane}};
-  float2* ACC[2] = {p->d_buf + 4 * plane, p->d_buf + 5 * plane};
-  EnvArgs g = p->base;
-  g.chi = chi;
   for (int s = 0; s < nsteps; ++s) {
-    for (int n = 1; n <= p->NT; ++n) {
-      g.scale = (float)(p->dt / n);
-      if (n == 1) {
-        g.in_a = psi_a; g.in_t = psi_t;
-        g.accin_a = psi_a; g.accin_t = psi_t;
-      } else {
-        g.in_a = T[(n - 2) & 1][0]; g.in_t = T[(n - 2) & 1][1];
-        g.accin_a = ACC[0]; g.accin_t = ACC[1];
-      }
-      const bool last = n == p->NT;
-      g.out_a = last ? nullptr : T[(n - 1) & 1][0];
-      g.out_t = last ? nullptr : T[(n - 1) & 1][1];
-      const bool to_psi = last && n > 1;
-      g.accout_a = to_psi ? psi_a : ACC[0];
-      g.accout_t = to_psi ? psi_t : ACC[1];
-      cudaError_t e = launch_envelope_term(g, st);
-      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
-    }
-    if (p->NT == 1) {
-      cudaError_t e = cudaMemcpyAsync(psi_a, ACC[0], 2 * plane * sizeof(float2), cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
-    }
+    int rc = envelope_taylor(p, psi_a, psi_a + plane, chi, st);
+    if (rc) return rc;
+  }
+  return FDETD_OK;
+}
+
+extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* chi, const float* sigma, int nsteps,
+                                       void* stream) {
+  if (!p || !a || !chi || !sigma) return fail(FDETD_ERR_ARG, "null argument");
+  if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
+  if (((uintptr_t)a & 15) || ((uintptr_t)chi & 15) || ((uintptr_t)sigma & 15))
+    return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t plane = (size_t)p->Nz * p->Nr;
+  float2* psi_a = (float2*)a;
+  cudaError_t e = launch_envelope_chit(chi, sigma, p->d_chit, plane, st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
+  const float damp = (float)(-0.25 * p->dt);
+  for (int s = 0; s < nsteps; ++s) {
+    e = launch_envelope_damp(psi_a, sigma, damp, plane, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
+    int rc = envelope_taylor(p, psi_a, psi_a + plane, p->d_chit, st);
+    if (rc) return rc;
+    e = launch_envelope_damp(psi_a, sigma, damp, plane, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
   }
   return FDETD_OK;
 }
@@ -933,6 +966,7 @@ extern "C" int envelope_plan_destroy(envelope_plan_t p) {
   if (!p) return FDETD_OK;
   if (p->d_lr) cudaFree(p->d_lr);
   if (p->d_buf) cudaFree(p->d_buf);
+  if (p->d_chit) cudaFree(p->d_chit);
   delete p;
   return FDETD_OK;
 }

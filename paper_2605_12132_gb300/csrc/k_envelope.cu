@@ -61,4 +61,31 @@ cudaError_t launch_envelope_term(const EnvArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Absorbing layer (appendix, Eq. absorbingA_solution2): the split-operator step
+//   exp(-sigma dt / 4) exp(H_a dt) exp(-sigma dt / 4) with chi~ = chi + sigma^2 inside H_a.
+__global__ void envelope_chit_kernel(const float* chi, const float* sigma, float* chit, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) chit[i] = chi[i] + sigma[i] * sigma[i];
+}
+
+// (a, a~) *= exp(c sigma) pointwise, a and a~ the two consecutive planes of n points
+__global__ void envelope_damp_kernel(float2* psi, const float* sigma, float c, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float f = expf(c * sigma[i]);
+  float2 u = psi[i], v = psi[n + i];
+  psi[i] = make_float2(f * u.x, f * u.y);
+  psi[n + i] = make_float2(f * v.x, f * v.y);
+}
+
+cudaError_t launch_envelope_chit(const float* chi, const float* sigma, float* chit, size_t n, cudaStream_t st) {
+  envelope_chit_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(chi, sigma, chit, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_envelope_damp(float2* psi, const float* sigma, float c, size_t n, cudaStream_t st) {
+  envelope_damp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, sigma, c, n);
+  return cudaGetLastError();
+}
+
 }  // namespace fdetd

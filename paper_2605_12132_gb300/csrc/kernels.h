@@ -174,5 +174,7 @@ struct EnvArgs {
   float k2;             // 2 k0
 };
 cudaError_t launch_envelope_term(const EnvArgs& a, cudaStream_t st);
+cudaError_t launch_envelope_chit(const float* chi, const float* sigma, float* chit, size_t n, cudaStream_t st);
+cudaError_t launch_envelope_damp(float2* psi, const float* sigma, float c, size_t n, cudaStream_t st);
 
 }  // namespace fdetd

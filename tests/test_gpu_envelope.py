@@ -67,3 +67,23 @@ def test_envelope_argument_errors():
     with pytest.raises(fd.FdetdError):
         fd.envelope_step(plan, torch.zeros((2, 64, 41), dtype=torch.complex64, device="cuda"),
                          torch.zeros((64, 41), device="cuda"))
+
+
+def test_envelope_absorbing_layer_matches_oracle():
+    rng = np.random.default_rng(9)
+    Nz, Nr, order, NT, dz, dr, dt = 64, 40, 8, 4, 0.2, 0.25, 0.05
+    a = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    at = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    chi = 0.5 * rng.random((Nz, Nr))
+    z = np.arange(Nz) * dz
+    sigma = np.repeat((3.0 * np.clip((z - 8.0) / 4.0, 0, None) ** 2)[:, None], Nr, axis=1)
+    plan = fd.envelope_plan(Nz, Nr, order, NT, dz, dr, dt)
+    psi = torch.from_numpy(np.stack([a, at])).to(torch.complex64).cuda()
+    c = torch.from_numpy(chi).to(torch.float32).cuda()
+    s = torch.from_numpy(sigma).to(torch.float32).cuda()
+    fd.envelope_step_absorbing(plan, psi, c, s, 3)
+    torch.cuda.synchronize()
+    out = psi.cpu().numpy().astype(np.complex128)
+    ra, rt = ev.envelope_step_absorbing(a, at, chi, sigma.astype(np.float32).astype(np.float64), order, NT, dz, dr,
+                                        dt, nsteps=3)
+    assert _rel(out[0], ra) < 2e-6 and _rel(out[1], rt) < 2e-6

@@ -94,3 +94,48 @@ def test_separable_mode_closed_form(q):
     na, nb = P @ np.array([alpha, beta])
     np.testing.assert_allclose(sa, na * phase * v[None, :], atol=1e-12)
     np.testing.assert_allclose(stt, nb * phase * v[None, :], atol=1e-12)
+
+
+def test_absorbing_step_without_layer_is_the_plain_step():
+    rng = np.random.default_rng(7)
+    Nz, Nr = 32, 12
+    a = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    at = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    chi = 0.3 * rng.random((Nz, Nr))
+    x = ev.envelope_step_absorbing(a, at, chi, np.zeros((Nz, Nr)), 4, 4, 0.2, 0.25, 0.05, nsteps=2)
+    y = ev.envelope_step(a, at, chi, 4, 4, 0.2, 0.25, 0.05, nsteps=2)
+    assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+
+
+def test_absorbing_step_with_a_uniform_layer_factorises():
+    # a constant sigma commutes with H_a: the step is exp(-sigma dt / 2) times the plain step with chi + sigma^2
+    rng = np.random.default_rng(8)
+    Nz, Nr, s0, dt = 32, 12, 0.7, 0.05
+    a = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    at = rng.standard_normal((Nz, Nr)) + 1j * rng.standard_normal((Nz, Nr))
+    chi = 0.3 * rng.random((Nz, Nr))
+    x = ev.envelope_step_absorbing(a, at, chi, np.full((Nz, Nr), s0), 4, 4, 0.2, 0.25, dt, nsteps=3)
+    y = ev.envelope_step(a, at, chi + s0 ** 2, 4, 4, 0.2, 0.25, dt, nsteps=3)
+    f = np.exp(-s0 * dt / 2) ** 3
+    assert np.allclose(x[0], f * y[0], rtol=1e-13, atol=0) and np.allclose(x[1], f * y[1], rtol=1e-13, atol=0)
+
+
+def test_absorbing_layer_absorbs_an_outgoing_pulse():
+    # a pulse travelling in +z (at ~c) through a layer occupying the upper part of the periodic box is
+    # absorbed there, while without the layer it keeps nearly all of its norm
+    Nz, Nr, order, NT, dz, dr, dt = 192, 12, 4, 4, 0.25, 0.5, 0.05
+    z = np.arange(Nz) * dz
+    r = (np.arange(Nr) + 0.5) * dr
+    zc, tau, w0, z0 = 20.0, 2.0, 3.0, 28.0
+    a = (np.exp(-((z - zc) / tau) ** 2)[:, None] * np.exp(-(r / w0) ** 2)[None, :]).astype(complex)
+    at = np.zeros_like(a)
+    chi = np.zeros((Nz, Nr))
+    ramp = np.clip((z - z0) / (z[-1] - z0), 0.0, None)
+    sigma = np.repeat((4.0 * ramp ** 2)[:, None], Nr, axis=1)
+    nsteps = 600                      # 30 time units: the pulse crosses the whole layer
+    x = ev.envelope_step_absorbing(a, at, chi, sigma, order, NT, dz, dr, dt, nsteps=nsteps)
+    y = ev.envelope_step(a, at, chi, order, NT, dz, dr, dt, nsteps=nsteps)
+    kept = np.linalg.norm(y[0]) / np.linalg.norm(a)
+    absorbed = np.linalg.norm(x[0]) / np.linalg.norm(a)
+    # >= 50x in amplitude, >= 2500x in energy (a stronger layer reflects more of the pulse)
+    assert kept > 0.5 and absorbed < 0.02 * kept, (kept, absorbed)
