@@ -20,6 +20,8 @@ from ._native import (  # noqa: F401
     envelope_step,
     envelope_step_absorbing,
     envelope_step_static,
+    fdetd_current_correct,
+    fdetd_current_host_bands,
     fdetd_destagger,
     fdetd_host_coeffs,
     fdetd_host_tables,

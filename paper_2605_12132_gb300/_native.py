@@ -37,6 +37,8 @@ def lib():
     L.fdetd_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.fdetd_step_host.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.fdetd_destagger.argtypes = [c_vp, c_vp, c_vp, c_vp]
+    L.fdetd_current_correct.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
+    L.fdetd_current_host_bands.argtypes = [c_int, c_int, c_dbl, c_int, dp, dp, dp, dp]
     L.fdetd_plan_device_bytes.argtypes = [c_vp]
     L.fdetd_plan_device_bytes.restype = ctypes.c_size_t
     L.fdetd_plan_launches_per_step.argtypes = [c_vp]
@@ -211,6 +213,30 @@ def fdetd_destagger(plan, fields, out=None, stream=None):
     _check_tensor(out, plan, 6, "out")
     _check(lib().fdetd_destagger(plan.handle, fields.data_ptr(), out.data_ptr(), _stream_handle(stream)))
     return out
+
+
+def fdetd_current_correct(plan, J, rho_xy, out=None, stream=None):
+    """Deposited J [modes][3][Nz][Nr] and rho_xy [modes][Nz][Nr] -> corrected J on the field step's Yee grid."""
+    import torch
+    _check_tensor(J, plan, 3, "J")
+    shape = (len(plan.modes), plan.Nz, plan.Nr)
+    if tuple(rho_xy.shape) != shape or rho_xy.dtype != plan.complex_dtype or not rho_xy.is_contiguous():
+        raise FdetdError(f"rho_xy must be a contiguous {plan.complex_dtype} tensor of shape {shape}")
+    if out is None:
+        out = torch.empty_like(J)
+    _check_tensor(out, plan, 3, "out")
+    _check(lib().fdetd_current_correct(plan.handle, J.data_ptr(), rho_xy.data_ptr(), out.data_ptr(),
+                                       _stream_handle(stream)))
+    return out
+
+
+def fdetd_current_host_bands(Nr, order, dr, m):
+    """Host-only: Div+ and D- bands [Nr][order+1] and the LU factors of the radial Laplacian of mode m."""
+    N = order // 2
+    divp, dm = np.zeros((Nr, order + 1)), np.zeros((Nr, order + 1))
+    lo, up = np.zeros((Nr, N)), np.zeros((Nr, N + 1))
+    _check(lib().fdetd_current_host_bands(Nr, order, dr, m, _dptr(divp), _dptr(dm), _dptr(lo), _dptr(up)))
+    return divp, dm, lo, up
 
 
 def fdetd_step_host(plan, host_fields, host_J=None, nsteps=1, stream=None):

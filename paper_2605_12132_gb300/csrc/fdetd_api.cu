@@ -48,6 +48,8 @@ struct fdetd_plan_s {
   size_t hostio_bytes = 0;
   TcPlan* tc = nullptr;
   size_t bytes = 0;
+  double* d_cur = nullptr;   // current correction: divp, dm, lo, up per mode (built on first use)
+  void* d_cur_work = nullptr;
   // optional per-kernel timing: events recorded around each launch on the launch stream
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -84,8 +86,8 @@ static void prof_collect(fdetd_plan_s* p) {
 static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
-  void* ptrs[] = {p->d_P,    p->d_Q,      p->d_phase, p->d_zsym, p->d_lam,
-                  p->d_tw,   p->d_coef,   p->d_src,   p->d_hostio, p->d_err};
+  void* ptrs[] = {p->d_P,  p->d_Q,    p->d_phase,  p->d_zsym, p->d_lam,      p->d_tw,
+                  p->d_coef, p->d_src, p->d_hostio, p->d_err,  (void*)p->d_cur, p->d_cur_work};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -477,6 +479,83 @@ extern "C" int fdetd_destagger(fdetd_plan_t p, const void* fields, void* out, vo
   cudaError_t e = launch_destagger(fields, out, p->Nz, p->Nr, p->order, p->modes.data(), p->nmodes,
                                    p->precision == FDETD_PREC_FP64, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("destagger: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_current_correct(fdetd_plan_t p, const void* J, const void* rho_xy, void* J_out, void* stream) {
+  if (!p || !J || !rho_xy || !J_out) return fail(FDETD_ERR_ARG, "null argument");
+  const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
+  const size_t jb = (size_t)p->nmodes * 3 * p->Nz * p->Nr * elt, rb = (size_t)p->nmodes * p->Nz * p->Nr * elt;
+  auto overlap = [](const void* a, size_t na, const void* b, size_t nb) {
+    const char *x = (const char*)a, *y = (const char*)b;
+    return x < y + nb && y < x + na;
+  };
+  if (overlap(J_out, jb, J, jb) || overlap(J_out, jb, rho_xy, rb)) return fail(FDETD_ERR_ARG, "J_out must not overlap the inputs");
+  const int n = p->Nr, ND = p->order / 2, W = 2 * ND + 1;
+  const size_t nm = (size_t)p->nmodes;
+  // array-major: divp of every mode, then dm, lo, up ([mode][n][...] within each)
+  const size_t o_dm = nm * n * W, o_lo = 2 * nm * n * W, o_up = o_lo + nm * n * ND, total = o_up + nm * n * (ND + 1);
+  if (!p->d_cur) {
+    std::vector<double> all(total);
+    for (int i = 0; i < p->nmodes; ++i) {
+      std::vector<double> divp, dm, lo, up;
+      const int rc = current_bands(n, p->order, p->dr, p->modes[i], divp, dm, lo, up);
+      if (rc) return fail(FDETD_ERR_EIG, "current correction: vanishing pivot of the radial Laplacian");
+      std::copy(divp.begin(), divp.end(), all.data() + (size_t)i * n * W);
+      std::copy(dm.begin(), dm.end(), all.data() + o_dm + (size_t)i * n * W);
+      std::copy(lo.begin(), lo.end(), all.data() + o_lo + (size_t)i * n * ND);
+      std::copy(up.begin(), up.end(), all.data() + o_up + (size_t)i * n * (ND + 1));
+    }
+    size_t dummy = 0;
+    cudaError_t e = upload((void**)&p->d_cur, all.data(), all.size() * 8, dummy);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_cur_work, nm * n * p->Nz * 16);
+    if (e != cudaSuccess) {
+      if (p->d_cur) cudaFree(p->d_cur);
+      p->d_cur = nullptr;
+      return fail(FDETD_ERR_OOM, std::string("current correction: ") + cudaGetErrorString(e));
+    }
+    p->bytes += all.size() * 8 + nm * n * p->Nz * 16;
+  }
+  CurParams cp;
+  memset(&cp, 0, sizeof(cp));
+  cp.J = J;
+  cp.rho_xy = rho_xy;
+  cp.out = J_out;
+  cp.work = p->d_cur_work;
+  cp.dr = p->dr;
+  cp.Nz = p->Nz;
+  cp.n = n;
+  cp.ND = ND;
+  cp.nm = p->nmodes;
+  for (int i = 0; i < p->nmodes; ++i) cp.m[i] = p->modes[i];
+  for (int i = -ND + 1; i <= ND; ++i) {
+    double num = 1.0, den = 1.0;
+    for (int l = -ND + 1; l <= ND; ++l)
+      if (l != i) {
+        num *= 0.5 - l;
+        den *= (double)(i - l);
+      }
+    cp.w[i + ND - 1] = num / den;
+  }
+  cp.divp = p->d_cur;
+  cp.dm = p->d_cur + o_dm;
+  cp.lo = p->d_cur + o_lo;
+  cp.up = p->d_cur + o_up;
+  cudaError_t e = launch_current(cp, p->precision == FDETD_PREC_FP64, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("current correction: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_current_host_bands(int Nr, int order, double dr, int m, double* divp, double* dm, double* lo,
+                                        double* up) {
+  std::vector<double> a, b, c, d;
+  const int rc = current_bands(Nr, order, dr, m, a, b, c, d);
+  if (rc == 1) return fail(FDETD_ERR_ARG, "bad order or Nr");
+  if (rc == 2) return fail(FDETD_ERR_EIG, "vanishing pivot");
+  if (divp) std::copy(a.begin(), a.end(), divp);
+  if (dm) std::copy(b.begin(), b.end(), dm);
+  if (lo) std::copy(c.begin(), c.end(), lo);
+  if (up) std::copy(d.begin(), d.end(), up);
   return FDETD_OK;
 }
 

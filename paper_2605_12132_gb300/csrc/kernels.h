@@ -149,6 +149,20 @@ cudaError_t tc_group_project(TcGroup* g, cudaStream_t st);
 cudaError_t tc_group_backproject(TcGroup* g, cudaStream_t st);
 int tc_group_tiles(const TcGroup* g, int which);
 
+// ---------------------------------------------------------------- current pipeline
+struct CurParams {
+  const void* J;       // [nm][3][Nz][n] complex<T> deposited on the primary grids
+  const void* rho_xy;  // [nm][Nz][n] complex<T>
+  void* out;           // [nm][3][Nz][n] complex<T>
+  void* work;          // [nm][n][Nz] complex<double>
+  const double *divp, *dm, *lo, *up;  // [nm] x current_bands layout
+  double w[32];        // half-point Lagrange weights
+  double dr;
+  int Nz, n, ND, nm;
+  int m[64];
+};
+cudaError_t launch_current(const CurParams& p, bool fp64, cudaStream_t st);
+
 // ---------------------------------------------------------------- destagger to the primary grids
 cudaError_t launch_destagger(const void* in, void* out, int Nz, int n, int order, const int* modes, int nmodes,
                              bool fp64, cudaStream_t st);

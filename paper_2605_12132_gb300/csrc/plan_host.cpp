@@ -530,6 +530,76 @@ int taylor_bands(int n, int order, double dr, int m, std::vector<double>& bands,
   return 0;
 }
 
+// Banded radial operators of the planar current correction of mode m (Sec. 3, Eqs.
+// shapesAM_currentRHS2m ... shapesAM_currentJth), rows k over columns k - ND .. k + ND (W = 2 ND + 1):
+//   divp: rho_k^-1 D^+ rho_-,j       (staggered J_rho -> primary divergence; column 0 is zero)
+//   dm:   D^-                        (primary phi -> staggered gradient, every row including the axis)
+// and the LU factors (no pivoting; the pivots of this operator stay far from zero) of
+//   A = L_rho^(mS) - m^2 rho^-2,  L_rho = D^2 + rho^-1 D^(C) centred (Eq. spatialAM_laplaceR),
+// primary-grid mirror j < 0 -> -1 - j with the sign (-1)^m, taps past the outer edge dropped:
+//   lo[k][d - 1] = l(k, k - d) (unit lower factor), up[k][d] = u(k, k + d), d = 0..ND.
+// Returns 0, or 1 for bad arguments, 2 for a vanishing pivot.
+int current_bands(int n, int order, double dr, int m, std::vector<double>& divp, std::vector<double>& dm,
+                  std::vector<double>& lo, std::vector<double>& up) {
+  if (order < 2 || order > 32 || (order & 1) || n < order / 2 + 2) return 1;
+  const int ND = order / 2, W = 2 * ND + 1, parity = m & 1;
+  const std::vector<double> c = staggered_coeffs(order);
+  Mat Dm = d_minus(n, c, dr, parity), Dp = d_plus(n, c, dr, parity);
+  divp.assign((size_t)n * W, 0.0);
+  dm.assign((size_t)n * W, 0.0);
+  for (int k = 0; k < n; ++k)
+    for (int j = std::max(0, k - ND); j <= std::min(n - 1, k + ND); ++j) {
+      divp[(size_t)k * W + (j - k + ND)] = Dp(k, j) * (j * dr) / ((k + 0.5) * dr);
+      dm[(size_t)k * W + (j - k + ND)] = Dm(k, j);
+    }
+  // dense band of A (row k, column k + d for |d| <= ND)
+  double e0 = 0;
+  const std::vector<double> e = centred_d2_coeffs(order, &e0);
+  const std::vector<double> d1 = centred_d1_coeffs(order);
+  const double sg = parity ? -1.0 : 1.0;
+  std::vector<double> A((size_t)n * W, 0.0);
+  auto Aat = [&](int k, int j) -> double& { return A[(size_t)k * W + (j - k + ND)]; };
+  for (int k = 0; k < n; ++k) {
+    const double rho = (k + 0.5) * dr;
+    Aat(k, k) += e0 / (dr * dr) - (double)m * m / (rho * rho);
+    for (int t = 1; t <= ND; ++t) {
+      const int js[2] = {k + t, k - t};
+      const double ws[2] = {e[t - 1] / (dr * dr) + d1[t - 1] / (dr * rho), e[t - 1] / (dr * dr) - d1[t - 1] / (dr * rho)};
+      for (int q = 0; q < 2; ++q) {
+        int j = js[q];
+        double w = ws[q];
+        if (j < 0) {
+          j = -1 - j;
+          w *= sg;
+        }
+        if (j < n) Aat(k, j) += w;
+      }
+    }
+  }
+  // banded LU without pivoting (Doolittle)
+  lo.assign((size_t)n * ND, 0.0);
+  up.assign((size_t)n * (ND + 1), 0.0);
+  double amax = 0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  for (int k = 0; k < n; ++k) {
+    for (int j = k; j <= std::min(n - 1, k + ND); ++j) {
+      double s = Aat(k, j);
+      for (int q = std::max(0, j - ND); q < k; ++q)
+        if (k - q <= ND) s -= lo[(size_t)k * ND + (k - q - 1)] * up[(size_t)q * (ND + 1) + (j - q)];
+      up[(size_t)k * (ND + 1) + (j - k)] = s;
+    }
+    const double piv = up[(size_t)k * (ND + 1)];
+    if (std::fabs(piv) < 1e-12 * amax) return 2;
+    for (int i = k + 1; i <= std::min(n - 1, k + ND); ++i) {
+      double s = Aat(i, k);
+      for (int q = std::max(0, i - ND); q < k; ++q)
+        if (k - q <= ND) s -= lo[(size_t)i * ND + (i - q - 1)] * up[(size_t)q * (ND + 1) + (k - q)];
+      lo[(size_t)i * ND + (i - k - 1)] = s / piv;
+    }
+  }
+  return 0;
+}
+
 int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
                     double dr, double dt, std::string& msg) {
   if (order < 2 || order > 32 || (order & 1)) {

@@ -59,6 +59,10 @@ int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, 
 // Returns 0, or 1 for a bad order / too few radial points.
 int taylor_bands(int n, int order, double dr, int m, std::vector<double>& bands, std::vector<double>& axis);
 
+// Banded operators and LU factors of the planar current correction (layout at the definition).
+int current_bands(int n, int order, double dr, int m, std::vector<double>& divp, std::vector<double>& dm,
+                  std::vector<double>& lo, std::vector<double>& up);
+
 // Phase coefficients of exp(t M) = I + A1 M + A2 M^2 for a 3x3 block with eigenvalues {0, +-i w}:
 // A1 = sin(w t)/w, A2 = (1 - cos(w t))/w^2 (limits at w = 0).
 void phase_coeffs(double w, double t, double* A1, double* A2);
