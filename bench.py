@@ -324,6 +324,83 @@ def run_destagger(args, w):
     print(json.dumps(line), flush=True)
 
 
+def _time_calls(fn, steps, warmup, flush=True):
+    """Mean CUDA-event time (ms) of fn() over `steps` calls after `warmup`, L2 flushed before each."""
+    import torch
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush else None
+    stream = torch.cuda.current_stream()
+    for _ in range(max(warmup, 3)):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        if buf is not None:
+            buf.zero_()
+        evs[k][0].record(stream)
+        fn()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(x.elapsed_time(y) for x, y in evs) / steps
+
+
+def run_envelope(args):
+    """The envelope propagator (second entry point) on the 4096x256 envelope workload: plain and with an
+    absorbing layer over the last eighth of the box."""
+    import torch
+    import paper_2605_12132_gb300 as fd
+    from paper_2605_12132_gb300 import inputs
+    ew = inputs.envelope_workload("envelope_4096x256")
+    a, at, chi = inputs.envelope_inputs(ew)
+    plan = fd.envelope_plan(ew.Nz, ew.Nr, ew.order, ew.taylor_order, ew.dz, ew.dr, ew.dt)
+    psi = torch.from_numpy(np.stack([a, at])).to(torch.complex64).cuda()
+    c = torch.from_numpy(chi).to(torch.float32).cuda()
+    z = np.arange(ew.Nz) / ew.Nz
+    sig = np.repeat((8.0 * np.clip((z - 0.875) / 0.125, 0, None) ** 2)[:, None], ew.Nr, axis=1)
+    sigma = torch.from_numpy(sig).to(torch.float32).cuda()
+    ms_plain = _time_calls(lambda: fd.envelope_step(plan, psi, c, 1), args.steps, args.warmup)
+    ms_abs = _time_calls(lambda: fd.envelope_step_absorbing(plan, psi, c, sigma, 1), args.steps, args.warmup)
+    cells = ew.Nz * ew.Nr
+    # per Taylor term: state 16 B + chi 4 B read, term 16 B written, running sum 16 B read + 16 B written
+    algo = cells * ew.taylor_order * 68
+    peaks, src = _peaks()
+    ach = algo / (ms_plain / 1e3) / 1e9
+    line = {"metric": "envelope cell*steps/s (exponential laser-envelope propagator, Taylor-N)",
+            "value": cells / (ms_plain / 1e3), "unit": "cell*steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_plain, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (Gaussian envelope, seeded smooth chi)",
+            "config": {"workload": ew.name, "taylor_order": ew.taylor_order, "order": ew.order,
+                       "absorbing_layer_ms_per_step": ms_abs, "l2": "flushed between timed calls (256 MiB write)"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "algorithmic": algo,
+                         "kernel": "envelope_term_kernel", "peak_source": src}}
+    print(json.dumps(line), flush=True)
+
+
+def run_current(args, w):
+    """The current pipeline (stagger, planar divergence error, banded FP64 Poisson solve, correction) on the
+    field workload's grid with seeded deposited currents and densities."""
+    import torch
+    import paper_2605_12132_gb300 as fd
+    prec = args.precision or "bf16x6"
+    rng = np.random.default_rng(3)
+    nm = len(w.modes)
+    plan = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision=prec)
+    dt_c = plan.complex_dtype
+    J = torch.from_numpy(rng.standard_normal((nm, 3, w.Nz, w.Nr)) + 0j).to(dt_c).cuda()
+    rho = torch.from_numpy(rng.standard_normal((nm, w.Nz, w.Nr)) + 0j).to(dt_c).cuda()
+    out = torch.empty_like(J)
+    ms = _time_calls(lambda: fd.fdetd_current_correct(plan, J, rho, out), args.steps, args.warmup)
+    cells = w.Nz * w.Nr * nm
+    line = {"metric": "current-corrected cell*mode/s (stagger + planar current correction)",
+            "value": cells / (ms / 1e3), "unit": "cell*mode/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 solve / " + ("f64" if prec == "fp64" else "f32") + " data",
+            "data": "synthetic (seeded random deposited current and density)",
+            "config": {"workload": w.name, "precision": prec, "launches": 4,
+                       "l2": "flushed between timed calls (256 MiB write)"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Poisson stream of field- and envelope-advance requests through the continuous-batching server."""
     import torch
@@ -374,7 +451,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "taylor", "destagger"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "taylor", "destagger", "envelope", "current"])
     ap.add_argument("--taylor-order", type=int, default=4)
     ap.add_argument("--substeps", type=int, default=1)
     ap.add_argument("--instances", type=int, default=64)
@@ -399,6 +476,10 @@ def main():
         return run_taylor(args, w)
     if args.mode == "destagger":
         return run_destagger(args, w)
+    if args.mode == "envelope":
+        return run_envelope(args)
+    if args.mode == "current":
+        return run_current(args, w)
 
     import torch
     import paper_2605_12132_gb300 as fd
