@@ -6,7 +6,7 @@
 // The half-point value uses the 2 N_D nearest nodes (weights w_t, t = -N_D+1 .. N_D); z is periodic;
 // radially the operand sits on rho_-,j = j dr with the axis value in slot 0, nodes j < 0 mirror to -j
 // with the sign of the symmetric / antisymmetric extension, nodes past the outer edge are dropped.
-// One thread per (mode, z, radial point); the stencils read neighbours through the read-only cache.
+// The stencils read neighbours through the read-only cache; B_theta goes through a shared row.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -22,68 +22,75 @@ struct DestagArgs {
   signed char signA[64], signS[64];  // +1 symmetric / -1 antisymmetric extension per mode
 };
 
+// One CTA per 8 z rows of one mode (a warp per row, lanes over the radii).  Phase 1: the z stencils
+// (E_z, B_rho written; B_theta interpolated in z into shared memory).  Phase 2: the radial stencils
+// (E_rho, B_z from global memory; B_theta from the shared row), E_theta copied.  B_theta's 2-D
+// interpolation is separable, so it costs 2 x 2 N_D reads per point instead of (2 N_D)^2.
 template <typename T>
 __global__ void __launch_bounds__(256) destagger_kernel(DestagArgs<T> a) {
   typedef typename cplx<T>::type C;
-  const int k = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int z = blockIdx.y * 8 + (threadIdx.x >> 5);
-  const int md = blockIdx.z;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  C* btz = reinterpret_cast<C*>(dsm);  // [8][n]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int z = blockIdx.x * 8 + warp, md = blockIdx.y;
   const int n = a.n, Nz = a.Nz, N = a.N;
-  if (k >= n || z >= Nz) return;
   const size_t fs = (size_t)Nz * n;
   const C* F = a.in + (size_t)md * 6 * fs;
   C* O = a.out + (size_t)md * 6 * fs;
-  const T sA = (T)a.signA[md], sS = (T)a.signS[md];
-  C er = cmake<C>(0, 0), ez = er, br = er, bt = er, bz = er;
-  for (int t = -N + 1; t <= N; ++t) {
-    const T wt = a.w[t + N - 1];
-    // radial node k + t (mirror through the axis for negative indices)
-    int j = k + t;
-    T sgnA = (T)1, sgnS = (T)1;
-    if (j < 0) {
-      j = -j;
-      sgnA = sA;
-      sgnS = sS;
-    }
-    if (j < n) {
-      const size_t row = (size_t)z * n + j;
-      const C vr = __ldg(&F[row]), vz = __ldg(&F[5 * fs + row]);
-      er.x += wt * sgnA * vr.x;
-      er.y += wt * sgnA * vr.y;
-      bz.x += wt * sgnS * vz.x;
-      bz.y += wt * sgnS * vz.y;
-      // B_theta: the z interpolation at radial node j, then the radial weight
-      C btz = cmake<C>(0, 0);
-      for (int s = -N + 1; s <= N; ++s) {
-        int zz = z + s;
+  const bool live = z < Nz;
+  if (live) {
+    for (int k = lane; k < n; k += 32) {
+      C ez = cmake<C>(0, 0), br = ez, bt = ez;
+      for (int t = -N + 1; t <= N; ++t) {
+        const T wt = a.w[t + N - 1];
+        int zz = z + t;
         if (zz < 0) zz += Nz;
         if (zz >= Nz) zz -= Nz;
-        const C v = __ldg(&F[4 * fs + (size_t)zz * n + j]);
-        const T ws = a.w[s + N - 1];
-        btz.x += ws * v.x;
-        btz.y += ws * v.y;
+        const size_t q = (size_t)zz * n + k;
+        const C v2 = __ldg(&F[2 * fs + q]), v3 = __ldg(&F[3 * fs + q]), v4 = __ldg(&F[4 * fs + q]);
+        ez.x += wt * v2.x;
+        ez.y += wt * v2.y;
+        br.x += wt * v3.x;
+        br.y += wt * v3.y;
+        bt.x += wt * v4.x;
+        bt.y += wt * v4.y;
       }
-      bt.x += wt * sgnA * btz.x;
-      bt.y += wt * sgnA * btz.y;
+      const size_t i0 = (size_t)z * n + k;
+      O[2 * fs + i0] = ez;
+      O[3 * fs + i0] = br;
+      btz[warp * n + k] = bt;
     }
-    // z node z + t (periodic) at radius k
-    int zz = z + t;
-    if (zz < 0) zz += Nz;
-    if (zz >= Nz) zz -= Nz;
-    const size_t q = (size_t)zz * n + k;
-    const C vz2 = __ldg(&F[2 * fs + q]), vb = __ldg(&F[3 * fs + q]);
-    ez.x += wt * vz2.x;
-    ez.y += wt * vz2.y;
-    br.x += wt * vb.x;
-    br.y += wt * vb.y;
   }
-  const size_t i0 = (size_t)z * n + k;
-  O[i0] = er;
-  O[fs + i0] = F[fs + i0];
-  O[2 * fs + i0] = ez;
-  O[3 * fs + i0] = br;
-  O[4 * fs + i0] = bt;
-  O[5 * fs + i0] = bz;
+  __syncthreads();
+  if (!live) return;
+  const T sA = (T)a.signA[md], sS = (T)a.signS[md];
+  const size_t row = (size_t)z * n;
+  for (int k = lane; k < n; k += 32) {
+    C er = cmake<C>(0, 0), bz = er, bt = er;
+    for (int t = -N + 1; t <= N; ++t) {
+      const T wt = a.w[t + N - 1];
+      int j = k + t;
+      T sgA = (T)1, sgS = (T)1;
+      if (j < 0) {
+        j = -j;
+        sgA = sA;
+        sgS = sS;
+      }
+      if (j >= n) continue;
+      const C vr = __ldg(&F[row + j]), vz = __ldg(&F[5 * fs + row + j]), vb = btz[warp * n + j];
+      er.x += wt * sgA * vr.x;
+      er.y += wt * sgA * vr.y;
+      bz.x += wt * sgS * vz.x;
+      bz.y += wt * sgS * vz.y;
+      bt.x += wt * sgA * vb.x;
+      bt.y += wt * sgA * vb.y;
+    }
+    const size_t i0 = row + k;
+    O[i0] = er;
+    O[fs + i0] = __ldg(&F[fs + i0]);
+    O[4 * fs + i0] = bt;
+    O[5 * fs + i0] = bz;
+  }
 }
 
 }  // namespace
@@ -103,7 +110,9 @@ cudaError_t launch_destagger(const void* in, void* out, int Nz, int n, int order
       }
     w[i + N - 1] = num / den;
   }
-  const dim3 grid((n + 31) / 32, (Nz + 7) / 8, nmodes);
+  const dim3 grid((Nz + 7) / 8, nmodes);
+  const size_t smem = (size_t)8 * n * (fp64 ? 16 : 8);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto fill = [&](auto& a) {
     a.Nz = Nz;
     a.n = n;
@@ -121,13 +130,17 @@ cudaError_t launch_destagger(const void* in, void* out, int Nz, int n, int order
     fill(a);
     a.in = (const double2*)in;
     a.out = (double2*)out;
-    destagger_kernel<double><<<grid, 256, 0, st>>>(a);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(destagger_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    destagger_kernel<double><<<grid, 256, smem, st>>>(a);
   } else {
     DestagArgs<float> a;
     fill(a);
     a.in = (const float2*)in;
     a.out = (float2*)out;
-    destagger_kernel<float><<<grid, 256, 0, st>>>(a);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(destagger_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    destagger_kernel<float><<<grid, 256, smem, st>>>(a);
   }
   return cudaGetLastError();
 }
