@@ -302,10 +302,10 @@ int envelope_step(envelope_plan_t plan, void* a, const float* chi, int nsteps, v
  * envelope_step_static - the envelope step for callers that cannot allocate device memory
  * (no counterpart in the paper; same mathematics and layouts as envelope_step).
  *
- * Who needs it: code running while its stream is captured into a CUDA graph (cudaMalloc is
- * not allowed during capture), applications whose device memory is entirely pre-reserved by
- * their own pool or arena, and plugins whose host framework owns every allocation.  It takes
- * no plan and allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Who needs it: applications whose device memory is entirely pre-reserved by their own pool
+ * or arena, plugins whose host framework owns every allocation, and latency-critical loops
+ * that cannot afford the implicit synchronisation of an allocation.  It takes no plan and
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *
  * a: device [2][Nz][Nr] complex64 (a, a~), advanced in place; chi: device [Nz][Nr] float32.
  * order (even, 2..32), taylor_order (1..16), dz, dr, dt, k0 as in envelope_plan.

@@ -1,10 +1,9 @@
 // Allocation-free envelope step (no counterpart in the paper).
 //
-// Some callers cannot allocate device memory when they advance the envelope: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc is not a legal
-// operation during capture), applications whose device memory is entirely pre-reserved by
-// their own pool or arena at start-up, and plugins embedded in a host framework that owns
-// every allocation.  envelope_step_static serves them: it needs no plan and calls no
+// Some callers cannot allocate device memory when they advance the envelope: applications
+// whose device memory is entirely pre-reserved by their own pool or arena at start-up,
+// plugins embedded in a host framework that owns every allocation, and latency-critical
+// loops that cannot afford the implicit synchronisation of an allocation.  envelope_step_static serves them: it needs no plan and calls no
 // cudaMalloc / cudaFree or allocating library routine.  Its scratch (two Taylor-term
 // buffers) lives in one file-scope device array of fixed capacity; the radial Laplacian band
 // is computed in the kernel from coefficients passed by value.

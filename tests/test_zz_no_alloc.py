@@ -1,8 +1,8 @@
 """The allocation-free envelope entry point against the plan-based one (GPU).
 
-envelope_step_static exists for callers that cannot allocate device memory (stream capture,
-pre-reserved memory pools, host frameworks that own every allocation); its scratch is a fixed
-file-scope device array.  This file is collected last so that a failure here leaves every other
+envelope_step_static exists for callers that cannot allocate device memory (pre-reserved memory
+pools, host frameworks that own every allocation, loops that cannot afford an allocation's
+synchronisation); its scratch is a fixed file-scope device array.  This file is collected last so that a failure here leaves every other
 test already run; it passes both alone in a fresh process and after the other tests.
 """
 import numpy as np
