@@ -377,8 +377,8 @@ def run_envelope(args):
 
 
 def run_current(args, w):
-    """The current pipeline (stagger, planar divergence error, banded FP64 Poisson solve, correction) on the
-    field workload's grid with seeded deposited currents and densities."""
+    """The current pipeline (stagger, planar divergence error, banded Poisson solve, correction; one fused
+    launch) on the field workload's grid with seeded deposited currents and densities."""
     import torch
     import paper_2605_12132_gb300 as fd
     prec = args.precision or "bf16x6"
@@ -394,9 +394,9 @@ def run_current(args, w):
     line = {"metric": "current-corrected cell*mode/s (stagger + planar current correction)",
             "value": cells / (ms / 1e3), "unit": "cell*mode/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 solve / " + ("f64" if prec == "fp64" else "f32") + " data",
+            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32 data / double-float solve",
             "data": "synthetic (seeded random deposited current and density)",
-            "config": {"workload": w.name, "precision": prec, "launches": 4,
+            "config": {"workload": w.name, "precision": prec, "launches": 1,
                        "l2": "flushed between timed calls (256 MiB write)"}}
     print(json.dumps(line), flush=True)
 

@@ -122,16 +122,19 @@ int fdetd_destagger(fdetd_plan_t plan, const void* fields, void* out, void* stre
  * the field step):
  *     J_rho <- S_rho^(-, mA) J_rho                      (primary -> staggered radial grid)
  *     delta = rho_xy - Div^+ J_rho - (i sigma m / rho) J_theta
- *     [L_rho^(mS) - m^2 rho^-2] phi = delta            (per mode and z row, banded LU in FP64)
+ *     [L_rho^(mS) - m^2 rho^-2] phi = delta            (per mode and z row, banded LU)
  *     J_rho += D^- phi,  J_theta += (i sigma m / rho) phi,  J_z unchanged.
  * J: device [modes][3][Nz][Nr] deposited on the primary grids (J_rho, J_theta at (z_i, rho_k), J_z
  * at (z_i - dz/2, rho_k)); rho_xy: device [modes][Nz][Nr], the planar density differential at
  * (z_i, rho_k); both in the plan's complex type.  J_out: device, same layout as J, the corrected
  * current on the Yee locations fdetd_step takes; must not overlap J or rho_xy.  The first call
- * builds the banded operators and LU factors on the host and allocates an FP64 work array of
- * modes x Nz x Nr complex values (FDETD_ERR_EIG if a pivot vanishes).  Asynchronous on `stream`.
+ * builds the banded operators and LU factors on the host in FP64 and uploads them (FDETD_ERR_EIG if
+ * a pivot vanishes); no other device memory is allocated.  Divergence, solve and gradient run in
+ * FP64 on FP64 plans and in double-float arithmetic (~46-bit significand) on FP32 plans; the
+ * downstagger runs in the data type.  One launch, asynchronous on `stream`.
  * fdetd_current_host_bands (host only): Div^+ and D^- bands [Nr][order+1], LU factors lo [Nr][order/2]
- * and up [Nr][order/2+1] of one mode, as the kernels use them (layout in csrc/plan_host.cpp).
+ * and up [Nr][order/2+1] of one mode, from which the device tables are built (layout in
+ * csrc/plan_host.cpp).
  */
 int fdetd_current_correct(fdetd_plan_t plan, const void* J, const void* rho_xy, void* J_out, void* stream);
 int fdetd_current_host_bands(int Nr, int order, double dr, int m, double* divp, double* dm, double* lo, double* up);

@@ -48,8 +48,7 @@ struct fdetd_plan_s {
   size_t hostio_bytes = 0;
   TcPlan* tc = nullptr;
   size_t bytes = 0;
-  double* d_cur = nullptr;   // current correction: divp, dm, lo, up per mode (built on first use)
-  void* d_cur_work = nullptr;
+  void* d_cur = nullptr;     // current correction: band tables per mode (built on first use)
   // optional per-kernel timing: events recorded around each launch on the launch stream
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -87,7 +86,7 @@ static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
   void* ptrs[] = {p->d_P,  p->d_Q,    p->d_phase,  p->d_zsym, p->d_lam,      p->d_tw,
-                  p->d_coef, p->d_src, p->d_hostio, p->d_err,  (void*)p->d_cur, p->d_cur_work};
+                  p->d_coef, p->d_src, p->d_hostio, p->d_err,  p->d_cur};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -493,35 +492,50 @@ extern "C" int fdetd_current_correct(fdetd_plan_t p, const void* J, const void* 
   if (overlap(J_out, jb, J, jb) || overlap(J_out, jb, rho_xy, rb)) return fail(FDETD_ERR_ARG, "J_out must not overlap the inputs");
   const int n = p->Nr, ND = p->order / 2, W = 2 * ND + 1;
   const size_t nm = (size_t)p->nmodes;
-  // array-major: divp of every mode, then dm, lo, up ([mode][n][...] within each)
-  const size_t o_dm = nm * n * W, o_lo = 2 * nm * n * W, o_up = o_lo + nm * n * ND, total = o_up + nm * n * (ND + 1);
   if (!p->d_cur) {
-    std::vector<double> all(total);
+    // tables in the order the kernel reads them (array-major, [mode] within each); FP32 plans get each
+    // value as a float pair hi + lo so the device can work in double-float arithmetic
+    const size_t o_dm = nm * W * n, o_lo = 2 * o_dm, o_up = o_lo + nm * n * ND, o_ip = o_up + nm * n * ND,
+                 o_mr = o_ip + nm * n, total = o_mr + nm * n;
+    std::vector<double> all(total, 0.0);
     for (int i = 0; i < p->nmodes; ++i) {
       std::vector<double> divp, dm, lo, up;
       const int rc = current_bands(n, p->order, p->dr, p->modes[i], divp, dm, lo, up);
       if (rc) return fail(FDETD_ERR_EIG, "current correction: vanishing pivot of the radial Laplacian");
-      std::copy(divp.begin(), divp.end(), all.data() + (size_t)i * n * W);
-      std::copy(dm.begin(), dm.end(), all.data() + o_dm + (size_t)i * n * W);
-      std::copy(lo.begin(), lo.end(), all.data() + o_lo + (size_t)i * n * ND);
-      std::copy(up.begin(), up.end(), all.data() + o_up + (size_t)i * n * (ND + 1));
+      for (int k = 0; k < n; ++k) {
+        for (int t = 0; t < W; ++t) {
+          all[(size_t)i * W * n + (size_t)t * n + k] = -divp[(size_t)k * W + t];
+          all[o_dm + (size_t)i * W * n + (size_t)t * n + k] = dm[(size_t)k * W + t];
+        }
+        for (int d = 1; d <= ND; ++d) {
+          all[o_lo + ((size_t)i * n + k) * ND + d - 1] = -lo[(size_t)k * ND + d - 1];
+          all[o_up + ((size_t)i * n + k) * ND + d - 1] = -up[(size_t)k * (ND + 1) + d];
+        }
+        all[o_ip + (size_t)i * n + k] = 1.0 / up[(size_t)k * (ND + 1)];
+        all[o_mr + (size_t)i * n + k] = (double)p->modes[i] / ((k + 0.5) * p->dr);
+      }
     }
+    if (p->precision != FDETD_PREC_FP64)
+      for (double& v : all) {
+        const float h = (float)v, l = (float)(v - (double)h);
+        float pair[2] = {h, l};
+        memcpy(&v, pair, 8);
+      }
     size_t dummy = 0;
-    cudaError_t e = upload((void**)&p->d_cur, all.data(), all.size() * 8, dummy);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_cur_work, nm * n * p->Nz * 16);
+    cudaError_t e = upload(&p->d_cur, all.data(), all.size() * 8, dummy);
     if (e != cudaSuccess) {
       if (p->d_cur) cudaFree(p->d_cur);
       p->d_cur = nullptr;
       return fail(FDETD_ERR_OOM, std::string("current correction: ") + cudaGetErrorString(e));
     }
-    p->bytes += all.size() * 8 + nm * n * p->Nz * 16;
+    p->bytes += all.size() * 8;
   }
   CurParams cp;
   memset(&cp, 0, sizeof(cp));
   cp.J = J;
   cp.rho_xy = rho_xy;
   cp.out = J_out;
-  cp.work = p->d_cur_work;
+  cp.bands = p->d_cur;
   cp.dr = p->dr;
   cp.Nz = p->Nz;
   cp.n = n;
@@ -537,10 +551,6 @@ extern "C" int fdetd_current_correct(fdetd_plan_t p, const void* J, const void* 
       }
     cp.w[i + ND - 1] = num / den;
   }
-  cp.divp = p->d_cur;
-  cp.dm = p->d_cur + o_dm;
-  cp.lo = p->d_cur + o_lo;
-  cp.up = p->d_cur + o_up;
   cudaError_t e = launch_current(cp, p->precision == FDETD_PREC_FP64, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("current correction: ") + cudaGetErrorString(e));
   return FDETD_OK;

@@ -63,8 +63,9 @@ __device__ __forceinline__ void phase_unpack(const PhaseF& p, df& A1, df& A2, fl
   A2 = p.A2;
   const float a2 = p.A2.h + p.A2.l;
   B1 = sqrtf(0.5f * fmaxf(a2, 0.f));
-  const float c = B1 > 0.f ? (p.A1.h + p.A1.l) / (2.f * B1) : 1.f;
-  B2 = B1 > 0.f ? B1 * B1 / (1.f + c) : 0.f;
+  // B1 and B2 scale only the current's term: the fast reciprocal-based division (2 ulp) suffices
+  const float c = B1 > 0.f ? __fdividef(p.A1.h + p.A1.l, 2.f * B1) : 1.f;
+  B2 = B1 > 0.f ? __fdividef(B1 * B1, 1.f + c) : 0.f;
 }
 // s- = (-Re s+, Im s+)
 __device__ __forceinline__ void zsym_unpack(const ZSymD& z, double& spr, double& spi, double& smr, double& smi) {
@@ -277,20 +278,19 @@ __device__ __forceinline__ void pass_all_T(C* s, int narr, int logN, int Ns, con
 }
 
 // The last transposed pass (Ns = 1, no twiddles) of the three field columns, storing straight to
-// global memory: butterfly j writes z = j + r N/RR, consecutive across threads.
-template <int RR, int NT, int MAXB, bool SPLIT_OUT, typename C>
+// global memory: butterfly j writes z = j + r N/RR, consecutive across threads.  The column index is
+// a compile-time loop index, so the column descriptors stay in registers.
+template <int RR, int NT, bool SPLIT_OUT, typename C>
 __device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* const* dst, const SplitColumn* sc) {
   constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
   const int N = 1 << logN;
   const int lnbf = logN - LR, nbf = 1 << lnbf;
-  const int total = 3 << lnbf;
   const int P = N + (N >> 3);
-  // the bf16 split stores are kept rolled: unrolled, they push the kernel out of the instruction cache
-#pragma unroll(SPLIT_OUT ? 1 : MAXB)
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
-    if (b < total) {
-      const int a = b >> lnbf, j = b & (nbf - 1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // the bf16 split stores are kept rolled: unrolled, they push the kernel out of the instruction cache
+#pragma unroll 1
+    for (int j = threadIdx.x; j < nbf; j += NT) {
       C v[RR];
 #pragma unroll
       for (int r = 0; r < RR; ++r) v[r] = s[a * P + padx(j * RR + r)];
@@ -573,11 +573,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
     for (int a = 0; a < 3; ++a) sc[a] = split_column(args.split_out, args.npieces, md, idx[a], j, args.split_kstages, Nz);
   }
   if (rem == 1)
-    last_pass_T_to_global<2, NT, 3 * BPT * (R / 2), SPLIT_OUT>(s, L, dst, sc);
+    last_pass_T_to_global<2, NT, SPLIT_OUT>(s, L, dst, sc);
   else if (rem == 2)
-    last_pass_T_to_global<4, NT, 3 * BPT * (R / 4), SPLIT_OUT>(s, L, dst, sc);
+    last_pass_T_to_global<4, NT, SPLIT_OUT>(s, L, dst, sc);
   else
-    last_pass_T_to_global<R, NT, 3 * BPT, SPLIT_OUT>(s, L, dst, sc);
+    last_pass_T_to_global<R, NT, SPLIT_OUT>(s, L, dst, sc);
 }
 
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT, int MODE,

@@ -154,8 +154,9 @@ struct CurParams {
   const void* J;       // [nm][3][Nz][n] complex<T> deposited on the primary grids
   const void* rho_xy;  // [nm][Nz][n] complex<T>
   void* out;           // [nm][3][Nz][n] complex<T>
-  void* work;          // [nm][n][Nz] complex<double>
-  const double *divp, *dm, *lo, *up;  // [nm] x current_bands layout
+  // -Div^+ [nm][W][n], D^- [nm][W][n], -L [nm][n][ND], -U off-diagonals [nm][n][ND], 1/U(k,k) [nm][n],
+  // m/rho [nm][n], back to back; 8-byte elements: doubles (FP64 data) or (hi, lo) float pairs (FP32 data)
+  const void* bands;
   double w[32];        // half-point Lagrange weights
   double dr;
   int Nz, n, ND, nm;
