@@ -168,8 +168,11 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     if ((e = upload(&p->d_Q, Qf.data(), Qf.size() * 4, p->bytes)) != cudaSuccess) goto cuda_fail;
   }
   {
-    // phase tables [nmodes][2][n][Nz], eigenvalue tables [nmodes][2][n], z symbols [Nz], twiddles [Nz/2]
+    // phase tables [nmodes][2][n][Nz], eigenvalue tables [nmodes][2][n], z symbols [Nz], twiddles;
+    // the per-kz tables are stored in the order the spectral kernel's forward transform leaves kz in
     const size_t nph = (size_t)nmodes * 2 * n * Nz;
+    std::vector<int> kz_at(Nz);
+    spectral_positions(Nz, fp64 ? 0 : 1, kz_at.data());
     std::vector<PhaseD> phd;
     std::vector<PhaseF> phf;
     if (fp64) phd.resize(nph); else phf.resize(nph);
@@ -183,10 +186,10 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
           const bool live = fam == 0 ? mp.tm_live[j] : mp.te_live[j];
           lamd[(size_t)(i * 2 + fam) * n + j] = lv;
           lamf[(size_t)(i * 2 + fam) * n + j] = to_df(lv);
-          for (int q = 0; q < Nz; ++q) {
+          for (int q = 0; q < Nz; ++q) {  // q: position
             double A1 = 0, A2 = 0, B1 = 0, B2 = 0;
             if (live) {
-              const double w = std::sqrt(hp.kappa2[q] + lv);
+              const double w = std::sqrt(hp.kappa2[kz_at[q]] + lv);
               phase_coeffs(w, dt, &A1, &A2);
               phase_coeffs(w, 0.5 * dt, &B1, &B2);
             }
@@ -211,10 +214,11 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     std::vector<ZSymD> zd(Nz);
     std::vector<ZSymF> zf(Nz);
     for (int q = 0; q < Nz; ++q) {
-      zd[q] = ZSymD{hp.sp_re[q], hp.sp_im[q]};
+      const int k = kz_at[q];
+      zd[q] = ZSymD{hp.sp_re[k], hp.sp_im[k]};
       ZSymF f;
-      f.spr = to_df(hp.sp_re[q]);
-      f.spi = to_df(hp.sp_im[q]);
+      f.spr = to_df(hp.sp_re[k]);
+      f.spi = to_df(hp.sp_im[k]);
       zf[q] = f;
     }
     if (fp64) {

@@ -15,8 +15,8 @@
 // out rather than amplifies; it runs in the data type.
 //
 // The solve runs on one warp per 16 rows: lane (row, re/im component) carries a real banded
-// substitution, the last N_D values in registers.  The stencil phases run one thread per radius over
-// the CTA's rows, from rows staged in shared memory.
+// substitution, specialised by the band width.  The stencil phases run one thread per radius over the CTA's rows,
+// from rows staged in shared memory.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -81,7 +81,7 @@ template <> struct CurNum<double> {
   typedef double K;
 };
 
-constexpr int MAX_ND = 16;
+constexpr int MAX_ND = 16;  // half the largest finite-difference order
 
 template <typename T>
 struct CurArgs {
@@ -103,6 +103,62 @@ struct CurArgs {
 
 __device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
+
+// Banded forward and back substitution of one real system of length n at x[0], x[2], ... (shared
+// memory), ND sub- and super-diagonals.  The last ND values sit in registers, the next row's
+// coefficients are loaded while the current row is reduced, and the terms are added farthest first,
+// so only the last one waits for the value just computed.
+template <int ND, typename A, typename K>
+__device__ __forceinline__ void solve_rows(A* x, int n, const K* L, const K* U, const K* ip) {
+  A win[ND];  // win[d - 1] = the value d places back
+  K c[ND], cn[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    lift(win[d], 0.f);
+    c[d] = L[d];  // row 0 (zero: no earlier values)
+  }
+  for (int k = 0; k < n; ++k) {
+    if (k + 1 < n) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d) cn[d] = L[(size_t)(k + 1) * ND + d];
+    }
+    A s = x[2 * k];
+#pragma unroll
+    for (int d = ND; d >= 1; --d) mac(s, c[d - 1], win[d - 1]);
+    s = norm(s);
+    x[2 * k] = s;
+#pragma unroll
+    for (int d = ND - 1; d >= 1; --d) win[d] = win[d - 1];
+    win[0] = s;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) c[d] = cn[d];
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    lift(win[d], 0.f);
+    c[d] = U[(size_t)(n - 1) * ND + d];  // last row (zero: no later values)
+  }
+  K pv = ip[n - 1];
+  for (int k = n - 1; k >= 0; --k) {
+    K pn = pv;
+    if (k > 0) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d) cn[d] = U[(size_t)(k - 1) * ND + d];
+      pn = ip[k - 1];
+    }
+    A s = x[2 * k];
+#pragma unroll
+    for (int d = ND; d >= 1; --d) mac(s, c[d - 1], win[d - 1]);
+    s = mul(s, pv);
+    x[2 * k] = s;
+#pragma unroll
+    for (int d = ND - 1; d >= 1; --d) win[d] = win[d - 1];
+    win[0] = s;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) c[d] = cn[d];
+    pv = pn;
+  }
+}
 
 // One CTA per (R z rows, mode), 256 threads.  Shared memory: js[R][n] holds the staggered J_rho rows
 // (data type); ph[R][n + 1][2] holds first the deposited J_rho rows (staged for the stencil), then
@@ -203,32 +259,18 @@ __global__ void __launch_bounds__(256) current_kernel(CurArgs<T> a) {
     const K* L = a.lo + (size_t)md * n * N;
     const K* U = a.up + (size_t)md * n * N;
     const K* ip = a.ipiv + (size_t)md * n;
-    A win[MAX_ND];  // win[d - 1] = the value d places back
-#pragma unroll
-    for (int d = 0; d < MAX_ND; ++d) lift(win[d], (T)0);
-    for (int k = 0; k < n; ++k) {
-      A s = x[2 * k];
-#pragma unroll
-      for (int d = MAX_ND; d >= 1; --d)
-        if (d <= N) mac(s, L[(size_t)k * N + d - 1], win[d - 1]);
-      s = norm(s);
-      x[2 * k] = s;
-#pragma unroll
-      for (int d = MAX_ND - 1; d >= 1; --d) win[d] = win[d - 1];
-      win[0] = s;
-    }
-#pragma unroll
-    for (int d = 0; d < MAX_ND; ++d) lift(win[d], (T)0);
-    for (int k = n - 1; k >= 0; --k) {
-      A s = x[2 * k];
-#pragma unroll
-      for (int d = MAX_ND; d >= 1; --d)
-        if (d <= N) mac(s, U[(size_t)k * N + d - 1], win[d - 1]);
-      s = mul(s, ip[k]);
-      x[2 * k] = s;
-#pragma unroll
-      for (int d = MAX_ND - 1; d >= 1; --d) win[d] = win[d - 1];
-      win[0] = s;
+    switch (N) {
+#define FDETD_SOLVE_CASE(ND) \
+  case ND:                   \
+    solve_rows<ND>(x, n, L, U, ip); \
+    break;
+      FDETD_SOLVE_CASE(1) FDETD_SOLVE_CASE(2) FDETD_SOLVE_CASE(3) FDETD_SOLVE_CASE(4)
+      FDETD_SOLVE_CASE(5) FDETD_SOLVE_CASE(6) FDETD_SOLVE_CASE(7) FDETD_SOLVE_CASE(8)
+      FDETD_SOLVE_CASE(9) FDETD_SOLVE_CASE(10) FDETD_SOLVE_CASE(11) FDETD_SOLVE_CASE(12)
+      FDETD_SOLVE_CASE(13) FDETD_SOLVE_CASE(14) FDETD_SOLVE_CASE(15) FDETD_SOLVE_CASE(16)
+#undef FDETD_SOLVE_CASE
+      default:
+        break;
     }
   }
   __syncthreads();

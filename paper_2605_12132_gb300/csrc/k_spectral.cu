@@ -14,11 +14,14 @@
 // Ampere equations only).  s+/s- are the DFT symbols of the periodic staggered
 // z stencil D_z^(+/-) (Eq. spatial_derivativeSt along z).
 //
-// The z transform is a mixed-radix Stockham FFT in shared memory: each pass loads
-// every butterfly of every array of the family into registers, twiddles and
-// transforms it there (radix 8 for FP32, radix 4 for FP64, one radix-2/4 pass
-// first when log2 Nz is not a multiple), and writes it back in place after one
-// barrier.  The rotation runs between the forward and inverse transforms.
+// The z transform is an in-place mixed-radix FFT in shared memory (radix 8 for FP32,
+// radix 4 for FP64, the remaining factor last): decimation in frequency forward, so
+// kz comes out digit-reversed and the per-kz tables are stored in that order, and the
+// adjoint stages in reverse order for the inverse, which restores natural z order.
+// Each butterfly writes back where it read, so a stage needs one barrier.  The last
+// forward stage, the rotation and the first inverse stage are fused in registers.
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -89,40 +92,6 @@ __device__ __forceinline__ void l2_prefetch(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((uint64_t)src), "r"(bytes) : "memory");
 }
 
-// bulk asynchronous copy of `bytes` (multiple of 16) from global to shared, completing on `bar`
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"((uint64_t)src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_addr(bar);
-  for (long it = 0; it < (1L << 26); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-template <typename C, typename Kc, typename Tb>
-__device__ __forceinline__ C combine(C x, C y, C z, Kc A1, Kc A2, C xJ, C yJ, C zJ, Tb B1, Tb B2, Tb dt,
-                                     bool hasJ) {
-  C r = cadd(x, cadd(cscale(A1, y), cscale(A2, z)));
-  if (hasJ) {
-    C s = cadd(xJ, cadd(cscale(B1, yJ), cscale(B2, zJ)));
-    r.x -= dt * s.x;
-    r.y -= dt * s.y;
-  }
-  return r;
-}
-
 // multiply by -i (forward) / +i (inverse)
 template <bool INV, typename C>
 __device__ __forceinline__ C rot90(C a) {
@@ -174,130 +143,148 @@ __device__ __forceinline__ void dft_small(C* v) {
   }
 }
 
-// Shared-memory layout of one array: logical element i at physical i + i/8 (one pad slot per
-// 8 elements), which keeps every Stockham pass at most 2-way bank-conflicted.
-__device__ __forceinline__ int padx(int i) { return i + (i >> 3); }
+// Kernel modes: FUSED transforms the family's field and current columns together; SOURCE
+// transforms only the current columns and writes the midpoint source term (with the 1/Nz of the
+// inverse transform) in kz space; MAIN transforms the field columns and adds that precomputed
+// source (used when five columns do not fit in shared memory).
+enum { FUSED = 0, MAIN = 1, SOURCE = 2 };
 
+// ---------------------------------------------------------------- in-place transforms
+// N = 2^logN = RF R^(S-1): a first stage of radix RF (the factor left over by radix R), then radix-R
+// stages.  Forward: decimation in frequency; stage s has radix R_s and stride L_s = N / (R_0 ... R_s)
+// (sub-transform length M_s = R_s L_s); the last stage has stride 1.  Butterfly (block, n1) of stage
+// s reads the R_s elements block M_s + n1 + L_s n2, takes their DFT and multiplies output k2 by
+// W_{M_s}^{n1 k2}; it writes them back where it read them, so a stage needs one barrier, after it.  The forward output at position p is the DFT at kz(p), the digit reversal
+// of p (spectral_positions); the rotation tables are stored in that order.  The inverse applies the
+// adjoint stages in reverse order (conjugated twiddle, then the inverse DFT), which returns natural
+// order.  The twiddle table of stage s holds W_{M_s}^{n1 k2} at (k2 - 1) L_s + n1 (k2 >= 1), stages
+// back to back, so the threads of a warp (consecutive n1) read consecutive entries.  The per-kz
+// tables hold the record of position b RL + r (last stage of radix RL) at r (N / RL) + b, so the
+// threads of a warp (consecutive b) read consecutive records.
+//
+// Shared-memory layout of one column: element p at pad16(p) = p + 2 floor(p / 16), two pad slots
+// after every 16 elements, so 16-byte pairs stay aligned for the asynchronous copies and the strided
+// butterflies of every stage fall on distinct banks.
+__host__ __device__ __forceinline__ int pad16(int p) { return p + ((p >> 4) << 1); }
 
-// One in-place Stockham pass of radix RR over arrays a0 .. a0+na-1 of length N = 2^logN (sub-sequence
-// length Ns before the pass).  Every butterfly of the group is read into registers before the
-// barrier and written after it, so source and destination layouts may differ: SRC_PAD = false reads
-// the unpadded arrays left by the bulk copy (array a at a*N), otherwise arrays sit at a*(N + N/8)
-// in the padded layout.  tw points at this pass's twiddle table: entry k*(RR-1) + r-1 holds
-// exp(-2 pi i r k / (Ns RR)) for k < Ns.  MAXB bounds the butterflies per thread.
-template <int RR, bool INV, int NT, int MAXB, bool SRC_PAD, typename C>
-__device__ __forceinline__ void stockham_pass(C* s, int a0, int na, int logN, int Ns, const C* tw) {
-  constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
-  const int N = 1 << logN;
-  const int lnbf = logN - LR, nbf = 1 << lnbf;
-  const int total = na << lnbf;
-  const int P = N + (N >> 3);
-  C v[MAXB][RR];
+// 16-byte asynchronous global -> shared copy, and the wait for all of a thread's copies
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// RR consecutive complex values at p (16-byte aligned when the values are 8-byte floats)
+template <int RR, typename C>
+__device__ __forceinline__ void load_run(const C* p, C* v) {
+  if constexpr (sizeof(C) == 8 && RR % 2 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
-    if (b < total) {
-      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const int li = j + (r << lnbf);
-        v[i][r] = SRC_PAD ? s[a * P + padx(li)] : s[a * N + li];
-      }
-      if (Ns > 1) {
-        const C* t = tw + (j & (Ns - 1)) * (RR - 1);
-#pragma unroll
-        for (int r = 1; r < RR; ++r) v[i][r] = INV ? cmulconj(v[i][r], t[r - 1]) : cmul(v[i][r], t[r - 1]);
-      }
-      dft_small<RR, INV>(v[i]);
+    for (int i = 0; i < RR / 2; ++i) {
+      const float4 t = q[i];
+      v[2 * i].x = t.x;
+      v[2 * i].y = t.y;
+      v[2 * i + 1].x = t.z;
+      v[2 * i + 1].y = t.w;
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < RR; ++i) v[i] = p[i];
   }
-  __syncthreads();
+}
+template <int RR, typename C>
+__device__ __forceinline__ void store_run(C* p, const C* v) {
+  if constexpr (sizeof(C) == 8 && RR % 2 == 0) {
+    float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
-    if (b < total) {
-      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
-      const int k = j & (Ns - 1);
-      C* x = s + a * P;
-      const int base = (j - k) * RR + k;
+    for (int i = 0; i < RR / 2; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+  } else {
 #pragma unroll
-      for (int r = 0; r < RR; ++r) x[padx(base + r * Ns)] = v[i][r];
+    for (int i = 0; i < RR; ++i) p[i] = v[i];
+  }
+}
+
+template <int RR> struct Log2R { static constexpr int v = RR == 8 ? 3 : (RR == 4 ? 2 : 1); };
+
+// One radix-R stage (not the last) over columns 0 .. narr-1, forward (INV = false) or adjoint.
+// Two butterflies per thread and iteration, both read before either is written.
+template <int R, bool INV, int NT, typename C>
+__device__ __forceinline__ void stage_inplace(C* s, int Pc, int narr, int logN, int logL, const C* tw) {
+  constexpr int LR = Log2R<R>::v;
+  const int lnb = logN - LR, total = narr << lnb;
+  const int bmask = (1 << lnb) - 1, lmask = (1 << logL) - 1;
+  for (int b0 = threadIdx.x; b0 < total; b0 += 2 * NT) {
+    C v[2][R];
+    int ad[2][R], n1s[2];
+    bool ok[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int bi = b0 + u * NT;
+      ok[u] = bi < total;
+      const int bb = ok[u] ? bi : b0;
+      const int a = bb >> lnb, rem = bb & bmask, n1 = rem & lmask;
+      const int p0 = ((rem >> logL) << (logL + LR)) + n1;
+      n1s[u] = n1;
+#pragma unroll
+      for (int r = 0; r < R; ++r) ad[u][r] = a * Pc + pad16(p0 + (r << logL));
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (ok[u]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[u][r] = s[ad[u][r]];
+      }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (ok[u]) {
+        C w[R];
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = tw[((r - 1) << logL) + n1s[u]];
+        if (INV) {
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[u][r] = cmulconj(v[u][r], w[r]);
+          dft_small<R, true>(v[u]);
+        } else {
+          dft_small<R, false>(v[u]);
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], w[r]);
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (ok[u]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[ad[u][r]] = v[u][r];
+      }
   }
   __syncthreads();
 }
 
-// Inverse transform by transposed Stockham passes in reverse order: the transpose of forward pass
-// (RR, Ns) reads x[(j - k) RR + k + r Ns] (k = j mod Ns), applies the inverse RR-point DFT, multiplies
-// by the conjugated twiddle of the forward table entry (k, r) and writes y[j + r N/RR].  The product
-// of the transposed passes in reverse order is the transpose of the forward transform, which (the DFT
-// matrix being symmetric) with conjugated twiddles is the inverse DFT; both directions share one
-// twiddle table, and the first inverse pass touches exactly the elements the last forward pass wrote
-// for the same butterfly, so the two can be fused with the rotation in registers.
-template <int RR, int NT, int MAXB, typename C>
-__device__ __forceinline__ void stockham_pass_T(C* s, int a0, int na, int logN, int Ns, const C* tw) {
-  constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
-  const int N = 1 << logN;
-  const int lnbf = logN - LR, nbf = 1 << lnbf;
-  const int total = na << lnbf;
-  const int P = N + (N >> 3);
-  C v[MAXB][RR];
-#pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
-    if (b < total) {
-      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
-      const int k = j & (Ns - 1);
-      const int base = (j - k) * RR + k;
-#pragma unroll
-      for (int r = 0; r < RR; ++r) v[i][r] = s[a * P + padx(base + r * Ns)];
-      dft_small<RR, true>(v[i]);
-      if (Ns > 1) {
-        const C* t = tw + k * (RR - 1);
-#pragma unroll
-        for (int r = 1; r < RR; ++r) v[i][r] = cmulconj(v[i][r], t[r - 1]);
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < MAXB; ++i) {
-    const int b = threadIdx.x + i * NT;
-    if (b < total) {
-      const int a = a0 + (b >> lnbf), j = b & (nbf - 1);
-#pragma unroll
-      for (int r = 0; r < RR; ++r) s[a * P + padx(j + (r << lnbf))] = v[i][r];
-    }
-  }
-  __syncthreads();
-}
-
-template <int RR, int NT, int MAXB, int G, typename C>
-__device__ __forceinline__ void pass_all_T(C* s, int narr, int logN, int Ns, const C* tw) {
-  for (int a0 = 0; a0 < narr; a0 += G) stockham_pass_T<RR, NT, MAXB>(s, a0, min(G, narr - a0), logN, Ns, tw);
-}
-
-// The last transposed pass (Ns = 1, no twiddles) of the three field columns, storing straight to
-// global memory: butterfly j writes z = j + r N/RR, consecutive across threads.  The column index is
-// a compile-time loop index, so the column descriptors stay in registers.
-template <int RR, int NT, bool SPLIT_OUT, typename C>
-__device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* const* dst, const SplitColumn* sc) {
-  constexpr int LR = RR == 2 ? 1 : (RR == 4 ? 2 : 3);
-  const int N = 1 << logN;
-  const int lnbf = logN - LR, nbf = 1 << lnbf;
-  const int P = N + (N >> 3);
+// The adjoint of stage 0 (one block, stride N / R) for the three field columns, writing the natural
+// order result z = n1 + L n2 to global memory (or its bf16 split pieces).  The column index is a
+// compile-time loop index, so the column descriptors stay in registers.
+template <int R, int NT, bool SPLIT_OUT, typename C>
+__device__ __forceinline__ void stage0_inv_to_global(const C* s, int Pc, int logN, const C* tw, C* const* dst,
+                                                     const SplitColumn* sc) {
+  constexpr int LR = Log2R<R>::v;
+  const int logL = logN - LR, L = 1 << logL;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     // the bf16 split stores are kept rolled: unrolled, they push the kernel out of the instruction cache
 #pragma unroll 1
-    for (int j = threadIdx.x; j < nbf; j += NT) {
-      C v[RR];
+    for (int n1 = threadIdx.x; n1 < L; n1 += NT) {
+      C v[R], w[R];
 #pragma unroll
-      for (int r = 0; r < RR; ++r) v[r] = s[a * P + padx(j * RR + r)];
-      dft_small<RR, true>(v);
+      for (int r = 0; r < R; ++r) v[r] = s[a * Pc + pad16(n1 + (r << logL))];
 #pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const int z = j + (r << lnbf);
+      for (int r = 1; r < R; ++r) w[r] = tw[((r - 1) << logL) + n1];
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmulconj(v[r], w[r]);
+      dft_small<R, true>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int z = n1 + (r << logL);
         if (!SPLIT_OUT)
           dst[a][z] = v[r];
         else
@@ -307,55 +294,18 @@ __device__ __forceinline__ void last_pass_T_to_global(const C* s, int logN, C* c
   }
 }
 
-// One pass over all narr arrays in groups of at most G.  A pass that reads the unpadded layout walks
-// the groups last-first: group g's padded destination [g0 P, g1 P) then never overlaps the unpadded
-// source [0, g0 N) of the groups still to be read (P > N).
-template <int RR, bool INV, int NT, int MAXB, int G, bool SRC_PAD, typename C>
-__device__ __forceinline__ void pass_all(C* s, int narr, int logN, int Ns, const C* tw) {
-  const int ng = (narr + G - 1) / G;
-  for (int gi = 0; gi < ng; ++gi) {
-    const int g = SRC_PAD ? gi : ng - 1 - gi;
-    const int a0 = g * G, na = min(G, narr - a0);
-    stockham_pass<RR, INV, NT, MAXB, SRC_PAD>(s, a0, na, logN, Ns, tw);
-  }
-}
-
-// Full FFT of narr arrays (forward or inverse, unnormalised), result in the padded layout:
-// one small-radix pass first when log2 N is not a multiple of log2 R, then radix-R passes.
-// The per-pass twiddle tables are stored back to back in pass order (first pass has none).
-// Arrays go G at a time; each thread owns BPT radix-R butterflies per array per pass.
-template <int R, bool INV, int NT, int G, int BPT, bool SRC_PAD, bool SKIP_LAST = false, typename C>
-__device__ const C* fft_all(C* s, int narr, int logN, const C* tw) {
-  const int lr = R == 8 ? 3 : 2;
-  int Ns = 1;
-  const int rem = logN % lr;
-  bool from_pad = SRC_PAD;
-  if (rem == 1) {
-    if (from_pad)
-      pass_all<2, INV, NT, G * BPT * (R / 2), G, true>(s, narr, logN, Ns, tw);
-    else
-      pass_all<2, INV, NT, G * BPT * (R / 2), G, false>(s, narr, logN, Ns, tw);
-    Ns *= 2;
-    from_pad = true;
-  } else if (rem == 2) {
-    if (from_pad)
-      pass_all<4, INV, NT, G * BPT * (R / 4), G, true>(s, narr, logN, Ns, tw);
-    else
-      pass_all<4, INV, NT, G * BPT * (R / 4), G, false>(s, narr, logN, Ns, tw);
-    Ns *= 4;
-    from_pad = true;
-  }
-  const int npass = logN / lr - (SKIP_LAST ? 1 : 0);
-  for (int p = 0; p < npass; ++p) {
-    if (from_pad)
-      pass_all<R, INV, NT, G * BPT, G, true>(s, narr, logN, Ns, tw);
-    else
-      pass_all<R, INV, NT, G * BPT, G, false>(s, narr, logN, Ns, tw);
-    if (Ns > 1) tw += Ns * (R - 1);
-    from_pad = true;
-    Ns *= R;
-  }
-  return tw;
+// A single-stage transform leaves the result in shared memory: copy it out in natural order.
+template <int NT, bool SPLIT_OUT, typename C>
+__device__ __forceinline__ void copy_out(const C* s, int Pc, int N, C* const* dst, const SplitColumn* sc) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    for (int z = threadIdx.x; z < N; z += NT) {
+      const C v = s[a * Pc + pad16(z)];
+      if (!SPLIT_OUT)
+        dst[a][z] = v;
+      else
+        split_store(sc[a], z, (float)v.x, (float)v.y);
+    }
 }
 
 // Exact midpoint update of one (kz, j) point: Horner form of
@@ -396,93 +346,101 @@ __device__ __forceinline__ void rotate_point(C& x0, C& x1, C& x2, C j0, C j1, bo
   x2 = r2;
 }
 
-}  // namespace
-
-// Kernel modes: FUSED transforms the family's field and current columns together; SOURCE
-// transforms only the current columns and writes the midpoint source term (with the 1/Nz of the
-// inverse transform) in kz space; MAIN transforms the field columns and adds that precomputed
-// source (used when five columns do not fit in shared memory).
-enum { FUSED = 0, MAIN = 1, SOURCE = 2 };
-
-// T: data real type; K: coefficient type (double or df); PH / ZS: table records; R: FFT radix;
-// NT: threads; G: arrays per pass group; BPT: radix-R butterflies per thread per array;
-// TW_SMEM: twiddle tables copied to shared memory (else read through L1).
-template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT_OUT, int MODE,
-          bool TW_SMEM>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(SpectralArgs args) {
-  typedef typename cplx<T>::type C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t load_bar;
-  C* s = reinterpret_cast<C*>(smem_raw);
-  const int Nz = args.Nz, L = args.logNz, n = args.n;
-  const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
-  const bool hasJ = MODE == FUSED ? args.hasJ : false;
-  // coefficient array indices: E group (e, a, c), B group (b, d, f), J (eJ, aJ, cJ)
-  int idx[5];
-  int narr;
-  if (MODE == SOURCE) {
-    idx[0] = fam == 0 ? 6 : 8;
-    idx[1] = 7;
-    narr = fam == 0 ? 2 : 1;
-  } else if (fam == 0) {
-    idx[0] = 0; idx[1] = 1; idx[2] = 3; idx[3] = 6; idx[4] = 7;
-    narr = hasJ ? 5 : 3;
-  } else {
-    idx[0] = 2; idx[1] = 4; idx[2] = 5; idx[3] = 8; idx[4] = 8;
-    narr = hasJ ? 4 : 3;
-  }
-  const C* coef = reinterpret_cast<const C*>(args.coef);
-  const C* twg = reinterpret_cast<const C*>(args.twiddle);
-  const int P = Nz + (Nz >> 3);
-  // column slots in shared memory; must match launch_one's sizing (the twiddles follow them)
-  const int slots = MODE == FUSED ? (args.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);
-  const C* tw = TW_SMEM ? s + (size_t)slots * P : twg;
-  // the family's columns are contiguous in global memory: one bulk copy each into shared memory
-  // (unpadded; the first FFT pass re-lays them out padded), completing on one mbarrier
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&load_bar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const uint32_t col = (uint32_t)(Nz * sizeof(C));
-    const uint32_t twb = TW_SMEM ? (uint32_t)(args.tw_count * sizeof(C)) : 0u;
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
-                     smem_addr(&load_bar)),
-                 "r"(narr * col + twb)
-                 : "memory");
-    for (int a = 0; a < narr; ++a)
-      bulk_g2s(s + (size_t)a * Nz, coef + ((size_t)(md * 9 + idx[a]) * n + j) * Nz, col, &load_bar);
-    if (TW_SMEM) bulk_g2s(const_cast<C*>(tw), twg, twb, &load_bar);
-    // the rotation reads this column's phase factors (and, in MAIN mode, the source term) straight
-    // from global memory: start pulling them into L2 now, while the forward transforms run
-    const PH* ph = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
-    l2_prefetch(ph, (uint32_t)(Nz * sizeof(PH)));
-    if (MODE == MAIN && args.src)
-      for (int c = 0; c < 3; ++c)
-        l2_prefetch(reinterpret_cast<const C*>(args.src) + (((size_t)(md * 2 + fam) * 3 + c) * n + j) * Nz, col);
+// The last forward stage (radix RL, stride 1: butterfly b holds positions b RL .. b RL + RL - 1), the
+// exact rotation of those RL kz values and the first inverse stage (the adjoint of the same butterfly),
+// in registers per butterfly.  The current columns' last stage is done here too: their values at
+// these positions are needed only by this butterfly.  MAIN adds the precomputed source term instead.
+template <int RL, int MODE, int NT, typename T, typename K, typename PH, typename ZS, typename C>
+__device__ __forceinline__ void fused_last_stage(C* s, int Pc, int N, bool hasJ, int fam, const PH* phase,
+                                                 const ZS* zs, K lam, T dt, T inv, const C* src, size_t sstride) {
+  const int nb = N / RL;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int p0 = b * RL, pa = pad16(p0);
+    // up to radix 4 (FP32) the butterfly's table records are loaded first, to overlap their latency
+    // with the transforms; radix 8 or FP64 would not leave the registers for it
+    constexpr bool PRE = RL <= 4 && sizeof(T) == 4;
+    PH ph[PRE ? RL : 1];
+    ZS zr[PRE ? RL : 1];
+    if constexpr (PRE) {
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        ph[r] = phase[r * nb + b];
+        zr[r] = zs[r * nb + b];
+      }
+    }
+    C v[3][RL], jv[2][RL];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      load_run<RL>(s + a * Pc + pa, v[a]);
+      dft_small<RL, false>(v[a]);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) jv[c][r] = cmake<C>(0, 0);
+    if (hasJ) {
+      load_run<RL>(s + 3 * Pc + pa, jv[0]);
+      dft_small<RL, false>(jv[0]);
+      if (fam == 0) {
+        load_run<RL>(s + 4 * Pc + pa, jv[1]);
+        dft_small<RL, false>(jv[1]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      K spr, spi, smr, smi, A1, A2;
+      T B1, B2;
+      if constexpr (PRE) {
+        zsym_unpack(zr[r], spr, spi, smr, smi);
+        phase_unpack(ph[r], A1, A2, B1, B2);
+      } else {
+        zsym_unpack(zs[r * nb + b], spr, spi, smr, smi);
+        phase_unpack(phase[r * nb + b], A1, A2, B1, B2);
+      }
+      rotate_point<T, K, C>(v[0][r], v[1][r], v[2][r], jv[0][r], jv[1][r], hasJ, fam, lam, spr, spi, smr, smi, A1,
+                            A2, B1, B2, dt, inv);
+      if (MODE == MAIN && src) {
+        const int q = r * nb + b;
+        v[0][r] = cadd(v[0][r], src[q]);
+        v[1][r] = cadd(v[1][r], src[sstride + q]);
+        v[2][r] = cadd(v[2][r], src[2 * sstride + q]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dft_small<RL, true>(v[a]);
+      store_run<RL>(s + a * Pc + pa, v[a]);
+    }
   }
   __syncthreads();
-  if (!bar_wait(&load_bar, 0)) {
-    if (threadIdx.x == 0 && args.err) atomicCAS(args.err, 0, 8);
-    return;
-  }
-  const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
-  const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
-  const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
-  const T dt = (T)args.dt;
-  const T inv = (T)1 / (T)Nz;
-  C* src = reinterpret_cast<C*>(args.src) + ((size_t)(md * 2 + fam) * 3 * n + j) * Nz;  // [md][fam][3][n][Nz]
-  const size_t sstride = (size_t)n * Nz;
-  if (MODE == SOURCE) {
-    // the current's midpoint source term -dt exp(dt M / 2) x_J / Nz in kz space, to global memory
-    fft_all<R, false, NT, G, BPT, false>(s, narr, L, tw);
-    for (int q = threadIdx.x; q < Nz; q += NT) {
-      const int pq = padx(q);
+}
+
+// SOURCE: the current columns' last forward stage and the midpoint source term
+// -dt exp(dt M / 2) x_J / Nz per position, written to global memory in position order.
+template <int RL, int NT, typename T, typename K, typename PH, typename ZS, typename C>
+__device__ __forceinline__ void source_last_stage(const C* s, int Pc, int N, int fam, const PH* phase, const ZS* zs,
+                                                  K lam, T dt, T inv, C* src, size_t sstride) {
+  const int nb = N / RL;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int p0 = b * RL, pa = pad16(p0);
+    C j0v[RL], j1v[RL];
+    load_run<RL>(s + pa, j0v);
+    dft_small<RL, false>(j0v);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) j1v[r] = cmake<C>(0, 0);
+    if (fam == 0) {
+      load_run<RL>(s + Pc + pa, j1v);
+      dft_small<RL, false>(j1v);
+    }
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int q = r * nb + b;
       K spr, spi, smr, smi, A1, A2;
       T B1, B2;
       zsym_unpack(zs[q], spr, spi, smr, smi);
       phase_unpack(phase[q], A1, A2, B1, B2);
       C y0, y1, y2, z0, z1, z2;
-      C j0 = s[pq], j1 = cmake<C>(0, 0), j2 = cmake<C>(0, 0);
-      if (fam == 0) j1 = s[P + pq];
+      const C j0 = j0v[r], j1 = j1v[r], j2 = cmake<C>(0, 0);
       if (fam == 0) {
         apply_tm(j0, j1, j2, y0, y1, y2, lam, spr, spi, smr, smi);
         apply_tm(y0, y1, y2, z0, z1, z2, lam, spr, spi, smr, smi);
@@ -494,99 +452,145 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
       const C jj[3] = {j0, j1, j2}, yy[3] = {y0, y1, y2}, zz[3] = {z0, z1, z2};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C v = cadd(jj[c], cadd(cscale(B1, yy[c]), cscale(B2, zz[c])));
-        v.x *= f;
-        v.y *= f;
-        src[c * sstride + q] = v;
+        C w = cadd(jj[c], cadd(cscale(B1, yy[c]), cscale(B2, zz[c])));
+        w.x *= f;
+        w.y *= f;
+        src[c * sstride + q] = w;
       }
     }
+  }
+}
+
+}  // namespace
+
+// coefficient array of column a of family fam: E group (e, a, c) = 0, 1, 2; B group (b, d, f) = 3, 4, 5;
+// J (eJ, aJ, cJ) = 6, 7, 8.  TM columns: e, a, b, eJ, aJ; TE: c, d, f, cJ.  SOURCE: the J columns alone.
+__device__ __forceinline__ int column_index(int mode, int fam, int a) {
+  if (mode == SOURCE) return fam == 0 ? 6 + a : 8;
+  if (fam == 0) return a < 2 ? a : (a == 2 ? 3 : a + 3);
+  return a == 0 ? 2 : (a < 3 ? a + 3 : 8);
+}
+
+// T: data real type; K: coefficient type (double or df); PH / ZS: table records; R: radix of all
+// stages but the last; NT: threads; TW_SMEM: twiddle tables copied to shared memory (else read
+// through L1).
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT_OUT, int MODE, bool TW_SMEM>
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(SpectralArgs args) {
+  typedef typename cplx<T>::type C;
+  constexpr int LR = Log2R<R>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int Nz = args.Nz, L = args.logNz, n = args.n;
+  const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
+  const bool hasJ = MODE == FUSED ? args.hasJ : false;
+  const int narr = MODE == SOURCE ? (fam == 0 ? 2 : 1) : (hasJ ? (fam == 0 ? 5 : 4) : 3);
+  const C* coef = reinterpret_cast<const C*>(args.coef);
+  const C* twg = reinterpret_cast<const C*>(args.twiddle);
+  const int Pc = pad16(Nz);
+  // column slots in shared memory; must match launch_one's sizing (the twiddles follow them)
+  const int slots = MODE == FUSED ? (args.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);
+  const C* tw = TW_SMEM ? s + (size_t)slots * Pc : twg;
+  const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
+  if (threadIdx.x == 0) {
+    // the rotation reads this column's phase records (and, in MAIN mode, the source term) from global
+    // memory: start pulling them into L2 now, while the columns arrive and the forward stages run
+    l2_prefetch(phase, (uint32_t)(Nz * sizeof(PH)));
+    if (MODE == MAIN && args.src)
+      for (int c = 0; c < 3; ++c)
+        l2_prefetch(reinterpret_cast<const C*>(args.src) + (((size_t)(md * 2 + fam) * 3 + c) * n + j) * Nz,
+                    (uint32_t)(Nz * sizeof(C)));
+  }
+  // the family's columns (contiguous Nz values each) into the padded layout, 16 bytes per copy
+  {
+    constexpr int EPC = 16 / (int)sizeof(C);
+    const int lper = L - (EPC == 2 ? 1 : 0), per = 1 << lper;
+    for (int i = threadIdx.x; i < narr * per; i += NT) {
+      const int a = i >> lper, e = (i & (per - 1)) * EPC;
+      const C* col = coef + ((size_t)(md * 9 + column_index(MODE, fam, a)) * n + j) * Nz;
+      cp_async16(s + a * Pc + pad16(e), col + e);
+    }
+    if (TW_SMEM) {
+      C* tws = s + (size_t)slots * Pc;
+      for (int i = threadIdx.x; i < args.tw_count / EPC; i += NT) cp_async16(tws + i * EPC, twg + i * EPC);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
+  const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
+  const T dt = (T)args.dt;
+  const T inv = (T)1 / (T)Nz;
+  C* src = reinterpret_cast<C*>(args.src) + ((size_t)(md * 2 + fam) * 3 * n + j) * Nz;  // [md][fam][3][n][Nz]
+  const size_t sstride = (size_t)n * Nz;
+  // stages: the leftover factor first (radix RF = 2^(L mod LR), RF = R when that is 1), then radix R;
+  // a transform shorter than R is one stage of radix Nz
+  const int nfull = L / LR, rem = L % LR;
+  const int S = rem && nfull ? nfull + 1 : (nfull ? nfull : 1);
+  const int LRF = S == 1 ? L : (rem ? rem : LR);  // log2 of the first stage's radix
+  // forward stages but the last
+  const C* t = tw;
+  for (int st = 0; st < S - 1; ++st) {
+    const int logLs = L - LRF - LR * st;
+    if (st > 0 || LRF == LR) {
+      stage_inplace<R, false, NT>(s, Pc, narr, L, logLs, t);
+      t += (size_t)(R - 1) << logLs;
+    } else if (LRF == 1) {
+      stage_inplace<2, false, NT>(s, Pc, narr, L, logLs, t);
+      t += (size_t)1 << logLs;
+    } else {
+      stage_inplace<4, false, NT>(s, Pc, narr, L, logLs, t);
+      t += (size_t)3 << logLs;
+    }
+  }
+  // the last stage: radix R, or the single stage of a short transform
+  const int LRL = S == 1 ? L : LR;
+  if (MODE == SOURCE) {
+    if (LRL == 1)
+      source_last_stage<2, NT, T>(s, Pc, Nz, fam, phase, zs, lam, dt, inv, src, sstride);
+    else if (LRL == 2)
+      source_last_stage<4, NT, T>(s, Pc, Nz, fam, phase, zs, lam, dt, inv, src, sstride);
+    else
+      source_last_stage<R, NT, T>(s, Pc, Nz, fam, phase, zs, lam, dt, inv, src, sstride);
     return;
   }
-  // forward transforms: every pass but the last for all columns, the last pass for the current
-  // columns (their kz values are read by any butterfly of the fused step below)
-  constexpr int LR = R == 8 ? 3 : 2;
-  const int lnbf = L - LR, nbf = 1 << lnbf;
-  const C* twl = fft_all<R, false, NT, G, BPT, false, true>(s, narr, L, tw);
-  if (narr > 3) stockham_pass<R, false, NT, G * BPT, true>(s, 3, narr - 3, L, nbf, twl);
-  // fused, per butterfly jb of the last forward pass of the three field columns: the pass (in
-  // registers), the exact rotation of its R kz values jb + r Nz/R, and the first (transposed) inverse
-  // pass, which reads and writes exactly those elements - no barrier between them
-  for (int jb = threadIdx.x; jb < nbf; jb += NT) {
-    C v[3][R];
-    const C* t = twl + jb * (R - 1);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[a][r] = s[a * P + padx(jb + (r << lnbf))];
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[a][r] = cmul(v[a][r], t[r - 1]);
-      dft_small<R, false>(v[a]);
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int q = jb + (r << lnbf);
-      const int pq = padx(q);
-      K spr, spi, smr, smi, A1, A2;
-      T B1, B2;
-      zsym_unpack(zs[q], spr, spi, smr, smi);
-      phase_unpack(phase[q], A1, A2, B1, B2);
-      C j0 = cmake<C>(0, 0), j1 = cmake<C>(0, 0);
-      if (hasJ) {
-        j0 = s[3 * P + pq];
-        if (fam == 0) j1 = s[4 * P + pq];
-      }
-      rotate_point<T, K, C>(v[0][r], v[1][r], v[2][r], j0, j1, hasJ, fam, lam, spr, spi, smr, smi, A1, A2, B1, B2,
-                            dt, inv);
-      if (MODE == MAIN && args.src) {
-        v[0][r] = cadd(v[0][r], src[q]);
-        v[1][r] = cadd(v[1][r], src[sstride + q]);
-        v[2][r] = cadd(v[2][r], src[2 * sstride + q]);
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dft_small<R, true>(v[a]);
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[a][r] = cmulconj(v[a][r], t[r - 1]);
-#pragma unroll
-      for (int r = 0; r < R; ++r) s[a * P + padx(jb + (r << lnbf))] = v[a][r];
-    }
-  }
-  __syncthreads();
-  // remaining inverse passes: transposes of the forward radix-R passes in reverse order (each pass
-  // table sits before the next pass's in the forward layout), then the first forward pass's
-  // transpose, which writes the result (or its bf16 split pieces) to global memory
-  const int rem = L % LR, npass = L / LR;
-  const C* tp = twl;
-  for (int p = npass - 2; p >= (rem ? 0 : 1); --p) {
-    const int Nsp = (1 << rem) << (LR * p);
-    if (Nsp > 1) tp -= Nsp * (R - 1);
-    pass_all_T<R, NT, G * BPT, G>(s, 3, L, Nsp, tp);
+  if (LRL == 1)
+    fused_last_stage<2, MODE, NT, T>(s, Pc, Nz, hasJ, fam, phase, zs, lam, dt, inv, src, sstride);
+  else if (LRL == 2)
+    fused_last_stage<4, MODE, NT, T>(s, Pc, Nz, hasJ, fam, phase, zs, lam, dt, inv, src, sstride);
+  else
+    fused_last_stage<R, MODE, NT, T>(s, Pc, Nz, hasJ, fam, phase, zs, lam, dt, inv, src, sstride);
+  // remaining inverse stages (adjoints in reverse order), the one of stage 0 writing to global memory
+  for (int st = S - 2; st >= 1; --st) {
+    const int logLs = L - LRF - LR * st;
+    t -= (size_t)(R - 1) << logLs;
+    stage_inplace<R, true, NT>(s, Pc, 3, L, logLs, t);
   }
   C* out = reinterpret_cast<C*>(args.coef);
   C* dst[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) dst[a] = out + ((size_t)(md * 9 + idx[a]) * n + j) * Nz;
+  for (int a = 0; a < 3; ++a) dst[a] = out + ((size_t)(md * 9 + column_index(MODE, fam, a)) * n + j) * Nz;
   SplitColumn sc[3];
   if (SPLIT_OUT) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) sc[a] = split_column(args.split_out, args.npieces, md, idx[a], j, args.split_kstages, Nz);
+    for (int a = 0; a < 3; ++a)
+      sc[a] = split_column(args.split_out, args.npieces, md, column_index(MODE, fam, a), j, args.split_kstages, Nz);
   }
-  if (rem == 1)
-    last_pass_T_to_global<2, NT, SPLIT_OUT>(s, L, dst, sc);
-  else if (rem == 2)
-    last_pass_T_to_global<4, NT, SPLIT_OUT>(s, L, dst, sc);
+  if (S == 1)
+    copy_out<NT, SPLIT_OUT>(s, Pc, Nz, dst, sc);
+  else if (LRF == LR)
+    stage0_inv_to_global<R, NT, SPLIT_OUT>(s, Pc, L, tw, dst, sc);
+  else if (LRF == 1)
+    stage0_inv_to_global<2, NT, SPLIT_OUT>(s, Pc, L, tw, dst, sc);
   else
-    last_pass_T_to_global<R, NT, SPLIT_OUT>(s, L, dst, sc);
+    stage0_inv_to_global<4, NT, SPLIT_OUT>(s, Pc, L, tw, dst, sc);
 }
 
-template <typename T, typename K, typename PH, typename ZS, int R, int NT, int G, int BPT, bool SPLIT, int MODE,
-          bool TW_SMEM>
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT, int MODE, bool TW_SMEM>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
   const int arrays = MODE == FUSED ? (a.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);  // = the kernel's `slots`
-  const size_t smem = ((size_t)arrays * (a.Nz + a.Nz / 8) + (TW_SMEM ? (size_t)a.tw_count : 0)) * sizeof(C);
-  auto k = spectral_kernel<T, K, PH, ZS, R, NT, G, BPT, SPLIT, MODE, TW_SMEM>;
+  const size_t smem = ((size_t)arrays * pad16(a.Nz) + (TW_SMEM ? (size_t)a.tw_count : 0)) * sizeof(C);
+  auto k = spectral_kernel<T, K, PH, ZS, R, NT, SPLIT, MODE, TW_SMEM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.n, 2, nmodes);
@@ -594,20 +598,18 @@ static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st
   return cudaGetLastError();
 }
 
-// Configuration by transform length: NT = max(128, Nz / R) threads up to 512, groups of three arrays
-// while one butterfly per thread per array suffices; beyond that one array at a time with two.
+// Threads by transform length: Nz / R (one radix-R butterfly per thread per column and stage),
+// at least 128 and at most 512.
 template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT, int MODE, bool TW_SMEM>
 static cudaError_t launch_sized(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   const int need = a.Nz / R;
-  if (need <= 128) return launch_one<T, K, PH, ZS, R, 128, 3, 1, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
-  if (need <= 256) return launch_one<T, K, PH, ZS, R, 256, 3, 1, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
-  if (need <= 512) return launch_one<T, K, PH, ZS, R, 512, 3, 1, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
-  if (need <= 1024) return launch_one<T, K, PH, ZS, R, 512, 1, 2, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
-  return cudaErrorNotSupported;
+  if (need <= 128) return launch_one<T, K, PH, ZS, R, 128, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
+  if (need <= 256) return launch_one<T, K, PH, ZS, R, 256, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
+  return launch_one<T, K, PH, ZS, R, 512, SPLIT, MODE, TW_SMEM>(a, nmodes, st);
 }
 
 static size_t fused_bytes(int Nz, int precision, bool hasJ, int tw_count) {
-  return ((size_t)(hasJ ? 5 : 3) * (Nz + Nz / 8) + (size_t)tw_count) * (precision == 0 ? 16 : 8);
+  return ((size_t)(hasJ ? 5 : 3) * pad16(Nz) + (size_t)tw_count) * (precision == 0 ? 16 : 8);
 }
 
 template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT>
@@ -641,35 +643,64 @@ bool spectral_needs_source(int Nz, int precision, int tw_count) {
 // (padded layout, twiddles through L1).  The fused path is used whenever it fits.
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ) {
   (void)hasJ;
-  return (size_t)3 * (Nz + Nz / 8) * (precision == 0 ? 16 : 8);
+  return (size_t)3 * pad16(Nz) * (precision == 0 ? 16 : 8);
 }
 
-// Per-pass twiddle tables in the order fft_all consumes them, for radix R (8 for FP32, 4 for FP64):
-// the first (small-radix) pass needs none; pass p with sub-length Ns and radix R stores
-// exp(-2 pi i r k / (Ns R)) at k*(R-1) + r-1 for k < Ns, r = 1..R-1.
-int spectral_twiddles(int Nz, int precision, double* re, double* im) {
-  const int R = precision == 0 ? 4 : 8, lr = precision == 0 ? 2 : 3;
+// Stage radices of the transform of length Nz = 2^logN: the leftover factor 2^(logN mod log2 R) first
+// (when it is not 1), then R (8 for FP32, 4 for FP64); a transform shorter than R is a single stage.
+static std::vector<int> stage_radices(int Nz, int precision) {
+  const int LR = precision == 0 ? 2 : 3;
   int logN = 0;
   while ((1 << logN) < Nz) ++logN;
-  int Ns = 1 << (logN % lr), cnt = 0;
+  const int nfull = logN / LR, rem = logN % LR;
+  if (!nfull) return std::vector<int>(1, 1 << logN);
+  std::vector<int> r(nfull, 1 << LR);
+  if (rem) r.insert(r.begin(), 1 << rem);
+  return r;
+}
+
+// Twiddle tables of the in-place stages in stage order: stage s < S-1 (radix R_s, stride L_s,
+// length M_s = R_s L_s) holds exp(-2 pi i n1 k2 / M_s) at (k2 - 1) L_s + n1 for n1 < L_s, 1 <= k2 < R_s.
+int spectral_twiddles(int Nz, int precision, double* re, double* im) {
+  const std::vector<int> rad = stage_radices(Nz, precision);
   const double pi = 3.14159265358979323846;
-  for (int p = 0; p < logN / lr; ++p) {
-    if (Ns > 1) {
-      for (int k = 0; k < Ns; ++k)
-        for (int r = 1; r < R; ++r) {
-          // reduce the angle exactly: r k / (Ns R) of a full turn
-          const long long num = ((long long)r * k) % ((long long)Ns * R);
-          const double ang = -2.0 * pi * (double)num / ((double)Ns * R);
-          if (re) {
-            re[cnt] = cos(ang);
-            im[cnt] = sin(ang);
-          }
-          ++cnt;
+  int M = Nz, cnt = 0;
+  for (size_t s = 0; s + 1 < rad.size(); ++s) {
+    const int R = rad[s], L = M / R;
+    for (int k2 = 1; k2 < R; ++k2)
+      for (int n1 = 0; n1 < L; ++n1) {
+        // reduce the angle exactly: n1 k2 / M of a full turn
+        const long long num = ((long long)n1 * k2) % (long long)M;
+        const double ang = -2.0 * pi * (double)num / (double)M;
+        if (re) {
+          re[cnt] = cos(ang);
+          im[cnt] = sin(ang);
         }
-    }
-    Ns *= R;
+        ++cnt;
+      }
+    M = L;
   }
   return cnt;
+}
+
+// kz index of the record at table index i: position p = b RL + r for i = r (Nz / RL) + b (RL the last
+// stage's radix); the forward transform leaves at p = sum_s k2_s L_s (digit k2_s of stage s) the
+// value of kz = sum_s k2_s R_0 ... R_{s-1}.
+void spectral_positions(int Nz, int precision, int* kz) {
+  const std::vector<int> rad = stage_radices(Nz, precision);
+  const int RL = rad.back(), nb = Nz / RL;
+  for (int i = 0; i < Nz; ++i) {
+    const int p = (i % nb) * RL + i / nb;
+    int M = Nz, rest = p, k = 0, mult = 1;
+    for (int R : rad) {
+      const int L = M / R;
+      k += (rest / L) * mult;
+      rest %= L;
+      mult *= R;
+      M = L;
+    }
+    kz[i] = k;
+  }
 }
 
 }  // namespace fdetd

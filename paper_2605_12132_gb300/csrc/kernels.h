@@ -15,10 +15,10 @@ int set_error(int code, const std::string& msg);
 // ---------------------------------------------------------------- spectral kernel
 struct SpectralArgs {
   void* coef;            // [nmodes][9][n][Nz] complex<T>; first 6 arrays updated in place
-  const void* phase;     // [nmodes][2][n][Nz] PhaseD / PhaseF
-  const void* zsym;      // [Nz] ZSymD / ZSymF
+  const void* phase;     // [nmodes][2][n][Nz] PhaseD / PhaseF, Nz in position order (spectral_positions)
+  const void* zsym;      // [Nz] ZSymD / ZSymF, position order
   const void* lam;       // [nmodes][2][n] double / df (lambda for TM, mu for TE)
-  const void* twiddle;   // per-pass twiddle tables (spectral_twiddles), complex<T>
+  const void* twiddle;   // per-stage twiddle tables (spectral_twiddles), complex<T>
   int tw_count;          // entries in `twiddle`
   __nv_bfloat16* split_out;  // tensor-core path: pre-tiled pieces, see split_store
   int npieces;
@@ -33,6 +33,8 @@ struct SpectralArgs {
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ);
 int spectral_twiddles(int Nz, int precision, double* re, double* im);
+// kz index held at each position of the forward transform's output (the order of the phase and z tables)
+void spectral_positions(int Nz, int precision, int* kz);
 bool spectral_needs_source(int Nz, int precision, int tw_count);
 
 // bf16 split of FP32 values into npieces (2 or 3) terms whose sum reproduces them to 16 / 24
