@@ -391,13 +391,21 @@ def run_current(args, w):
     out = torch.empty_like(J)
     ms = _time_calls(lambda: fd.fdetd_current_correct(plan, J, rho, out), args.steps, args.warmup)
     cells = w.Nz * w.Nr * nm
+    # algorithmic bytes: J (3 components) and rho_xy read, the corrected J written
+    algo = cells * 7 * J.element_size()
+    peaks, src = _peaks()
+    roof = {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"traffic": None, "algorithmic": algo, "kernel": "current_kernel", "peak_source": src,
+                 "note": "latency-bound: the banded solve is a serial recurrence over Nr per (mode, z row)"})
     line = {"metric": "current-corrected cell*mode/s (stagger + planar current correction)",
             "value": cells / (ms / 1e3), "unit": "cell*mode/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32 data / double-float solve",
             "data": "synthetic (seeded random deposited current and density)",
             "config": {"workload": w.name, "precision": prec, "launches": 1,
-                       "l2": "flushed between timed calls (256 MiB write)"}}
+                       "l2": "flushed between timed calls (256 MiB write)"},
+            "roofline": roof}
     print(json.dumps(line), flush=True)
 
 

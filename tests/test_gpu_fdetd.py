@@ -42,15 +42,23 @@ def _oracle(F, J, Nz, Nr, modes, order, dz, dr, dt, nsteps):
                      for i, m in enumerate(modes)])
 
 
-@pytest.mark.parametrize("prec", ALL)
-def test_parity_small_ragged(prec):
-    # several z tiles, a ragged radial tail (70 = 64 + 6), modes 0..3, current on
+@pytest.fixture(scope="module")
+def ragged_case():
+    # several z tiles, a ragged radial tail (70 = 64 + 6), modes 0..3, current on; the oracle runs once
+    # for all precisions
     rng = np.random.default_rng(1)
     Nz, Nr, modes, order, dz, dr, dt = 128, 70, [0, 1, 2, 3], 8, 1 / 16, 1 / 4, 1 / 16
     F = zero_axis(rng.standard_normal((4, 6, Nz, Nr)) + 1j * rng.standard_normal((4, 6, Nz, Nr)))
     J = 0.3 * (rng.standard_normal((4, 3, Nz, Nr)) + 1j * rng.standard_normal((4, 3, Nz, Nr)))
-    got = _run(prec, F, J, Nz, Nr, modes, order, dz, dr, dt, 3)
-    ref = _oracle(F, J, Nz, Nr, modes, order, dz, dr, dt, 3)
+    args = (Nz, Nr, modes, order, dz, dr, dt, 3)
+    return F, J, args, _oracle(F, J, *args)
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_parity_small_ragged(prec, ragged_case):
+    F, J, args, ref = ragged_case
+    modes = args[2]
+    got = _run(prec, F, J, *args)
     for i in range(len(modes)):
         err = field_errors(got[i], ref[i], floor_for(prec))
         assert err.max() < TOL[prec] * 3, (modes[i], err)
