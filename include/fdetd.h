@@ -282,6 +282,16 @@ int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, double dr, do
 int fdetd_host_coeffs(int kind, int order, double* out);
 
 /*
+ * fdetd_host_spectral_order - host-only: the order in which the spectral kernel stores its per-kz
+ * tables (phase records and z symbols).  Its in-place z transform (radix 8 for FP32 and the split-bf16
+ * precisions, radix 4 for FP64, the leftover factor as the first stage, decimation in frequency)
+ * leaves kz digit-reversed; the record of output position b * RL + r (RL the last stage's radix) sits
+ * at table index r * (Nz / RL) + b.  kz: Nz ints, kz[i] = the kz index of table entry i.
+ * precision: FDETD_PREC_*.  FDETD_ERR_ARG unless Nz is a power of two >= 2 and kz is non-null.
+ */
+int fdetd_host_spectral_order(int Nz, int precision, int* kz);
+
+/*
  * envelope_plan - exponential laser-envelope propagator of Sec. 4.2, mode m = 0:
  *     da/dt = a~,  da~/dt = (L_rho + L_z - chi) a + 2 i k0 D_z^(C) a + 2 i k0 a~
  * (complex form of Eq. spatialAM_envelope_H; L_rho = D^2_rho + rho^-1 D^(C)_rho with

@@ -24,6 +24,7 @@ from ._native import (  # noqa: F401
     fdetd_current_host_bands,
     fdetd_destagger,
     fdetd_host_coeffs,
+    fdetd_host_spectral_order,
     fdetd_host_tables,
     fdetd_plan,
     fdetd_plan_modes,

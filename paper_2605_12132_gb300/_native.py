@@ -49,6 +49,7 @@ def lib():
     L.fdetd_host_tables.argtypes = [c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, dp, dp, dp, dp, dp, dp,
                                     u8p, u8p, dp, dp, dp]
     L.fdetd_host_coeffs.argtypes = [c_int, c_int, dp]
+    L.fdetd_host_spectral_order.argtypes = [c_int, c_int, c_vp]
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_step_absorbing.argtypes = [c_vp, c_vp, c_vp, c_vp, c_int, c_vp]
@@ -333,6 +334,13 @@ def fdetd_probe_mma_rounding(reps=1, stream=None):
     out = (ctypes.c_float * 24)()
     _check(lib().fdetd_probe_mma_rounding(out, reps, _stream_handle(stream)))
     return np.array(out, dtype=np.float32).reshape(12, 2)
+
+
+def fdetd_host_spectral_order(Nz, precision="bf16x6"):
+    """kz index of each entry of the spectral kernel's per-kz tables (see include/fdetd.h)."""
+    out = np.zeros(Nz, dtype=np.int32)
+    _check(lib().fdetd_host_spectral_order(Nz, PRECISIONS[precision], out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def fdetd_host_coeffs(kind, order):

@@ -673,6 +673,12 @@ extern "C" int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, do
   return FDETD_OK;
 }
 
+extern "C" int fdetd_host_spectral_order(int Nz, int precision, int* kz) {
+  if (!kz || !is_pow2(Nz) || Nz < 2) return fail(FDETD_ERR_ARG, "Nz must be a power of two >= 2");
+  spectral_positions(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, kz);
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_host_coeffs(int kind, int order, double* out) {
   if (order < 2 || order > 32 || (order & 1) || !out) return fail(FDETD_ERR_ARG, "bad order or null out");
   std::vector<double> v;

@@ -170,3 +170,41 @@ def test_taylor_bands_reproduce_oracle_radial_operators(m, order):
     ND = order // 2
     assert np.allclose(axis[0], rad.axis_polar[:ND]) and np.all(rad.axis_polar[ND:] == 0)
     assert np.allclose(axis[1], rad.axis_scalar[:ND]) and np.all(rad.axis_scalar[ND:] == 0)
+
+
+def _dif_model(x, LR):
+    """In-place decimation-in-frequency FFT with the leftover radix as the first stage (numpy model of the
+    spectral kernel's stage structure): returns the array of output positions."""
+    N = len(x)
+    logN = N.bit_length() - 1
+    nfull, rem = divmod(logN, LR)
+    rad = [1 << logN] if not nfull else ([1 << rem] if rem else []) + [1 << LR] * nfull
+    y = x.astype(complex).copy()
+    M = N
+    for R in rad:
+        L = M // R
+        for blk in range(N // M):
+            for n1 in range(L):
+                idx = blk * M + n1 + L * np.arange(R)
+                v = np.fft.fft(y[idx])
+                v[1:] *= np.exp(-2j * np.pi * n1 * np.arange(1, R) / M)
+                y[idx] = v
+        M = L
+    return y, rad[-1]
+
+
+@pytest.mark.parametrize("Nz", [2, 4, 8, 16, 64, 128, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_spectral_table_order_is_the_transform_output_order(Nz, prec):
+    # the per-kz tables must list, entry by entry, the kz the in-place forward transform leaves at the
+    # position that reads the entry: position b RL + r reads entry r (Nz / RL) + b
+    _lib_or_skip()
+    kz = native.fdetd_host_spectral_order(Nz, prec)
+    assert sorted(kz.tolist()) == list(range(Nz))
+    x = np.random.default_rng(Nz).standard_normal(Nz) + 1j * np.random.default_rng(Nz + 1).standard_normal(Nz)
+    y, RL = _dif_model(x, 2 if prec == "fp64" else 3)
+    X = np.fft.fft(x)
+    nb = Nz // RL
+    for i in range(Nz):
+        p = (i % nb) * RL + i // nb
+        assert abs(y[p] - X[kz[i]]) < 1e-9 * np.abs(X).max(), (i, p, kz[i])
