@@ -26,7 +26,7 @@ struct SpectralArgs {
   int Nz, logNz, n;
   double dt;
   int hasJ;
-  int* err;              // device failure flag (bounded waits)
+  int* err;              // the plan's device failure flag (the spectral kernel has no waits that could set it)
   void* src;             // [nmodes][2][3][n][Nz] complex<T>: kz-space source term (two-kernel path)
 };
 
