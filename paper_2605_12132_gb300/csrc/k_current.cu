@@ -15,7 +15,7 @@
 // out rather than amplifies; it runs in the data type.
 //
 // The solve runs on one warp per 16 rows: lane (row, re/im component) carries a real banded
-// substitution, specialised by the band width.  The stencil phases run one thread per radius over the CTA's rows,
+// substitution, specialised by the band width, with the band rows prefetched across the warp.  The stencil phases run one thread per radius over the CTA's rows,
 // from rows staged in shared memory.
 #include "common.cuh"
 #include "kernels.h"
@@ -104,59 +104,96 @@ struct CurArgs {
 __device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
 
+__device__ __forceinline__ float2 shfl(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ void kzero(float2& c) { c = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void kzero(double& c) { c = 0.0; }
+
 // Banded forward and back substitution of one real system of length n at x[0], x[2], ... (shared
-// memory), ND sub- and super-diagonals.  The last ND values sit in registers, the next row's
-// coefficients are loaded while the current row is reduced, and the terms are added farthest first,
-// so only the last one waits for the value just computed.
+// memory), ND sub- and super-diagonals, run by a whole warp (lanes with live == false follow along
+// without touching x).  The last ND values sit in registers and the terms are added farthest first, so
+// only the last one waits for the value just computed.  The band rows are uniform across the warp:
+// lane l loads element l % ND of row k0 + l / ND for a group of G = 32 / ND rows, two groups ahead,
+// and each step takes its coefficients from the lanes by shuffles, so no step waits on memory.
 template <int ND, typename A, typename K>
-__device__ __forceinline__ void solve_rows(A* x, int n, const K* L, const K* U, const K* ip) {
+__device__ __forceinline__ void solve_rows(A* x, bool live, int n, const K* L, const K* U, const K* ip) {
+  constexpr int G = 32 / ND;
+  const int lane = threadIdx.x & 31, gr = lane / ND, gd = lane - gr * ND;
+  auto fetch = [&](const K* B, int row) {  // this lane's element of row `row` (zero outside)
+    K c;
+    kzero(c);
+    if (gr < G && row >= 0 && row < n) c = B[(size_t)row * ND + gd];
+    return c;
+  };
   A win[ND];  // win[d - 1] = the value d places back
-  K c[ND], cn[ND];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    lift(win[d], 0.f);
-    c[d] = L[d];  // row 0 (zero: no earlier values)
-  }
-  for (int k = 0; k < n; ++k) {
-    if (k + 1 < n) {
+  for (int d = 0; d < ND; ++d) lift(win[d], 0.f);
+  K cur = fetch(L, gr), nxt = fetch(L, G + gr);
+  for (int k0 = 0; k0 < n; k0 += G) {
+    const K nn = fetch(L, k0 + 2 * G + gr);
 #pragma unroll
-      for (int d = 0; d < ND; ++d) cn[d] = L[(size_t)(k + 1) * ND + d];
+    for (int i = 0; i < G; ++i) {
+      const int k = k0 + i;
+      if (k < n) {  // uniform
+        A s;
+        lift(s, 0.f);
+        if (live) s = x[2 * k];
+#pragma unroll
+        for (int d = ND; d >= 1; --d) mac(s, shfl(cur, i * ND + d - 1), win[d - 1]);
+        s = norm(s);
+        if (live) x[2 * k] = s;
+#pragma unroll
+        for (int d = ND - 1; d >= 1; --d) win[d] = win[d - 1];
+        win[0] = s;
+      }
     }
-    A s = x[2 * k];
-#pragma unroll
-    for (int d = ND; d >= 1; --d) mac(s, c[d - 1], win[d - 1]);
-    s = norm(s);
-    x[2 * k] = s;
-#pragma unroll
-    for (int d = ND - 1; d >= 1; --d) win[d] = win[d - 1];
-    win[0] = s;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) c[d] = cn[d];
+    cur = nxt;
+    nxt = nn;
   }
+  // back substitution from row n - 1 down: group g holds rows n - 1 - (g G + i)
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    lift(win[d], 0.f);
-    c[d] = U[(size_t)(n - 1) * ND + d];  // last row (zero: no later values)
-  }
-  K pv = ip[n - 1];
-  for (int k = n - 1; k >= 0; --k) {
-    K pn = pv;
-    if (k > 0) {
+  for (int d = 0; d < ND; ++d) lift(win[d], 0.f);
+  auto fetchU = [&](int g) {
+    K c;
+    kzero(c);
+    const int row = n - 1 - (g * G + gr);
+    if (gr < G && row >= 0) c = U[(size_t)row * ND + gd];
+    return c;
+  };
+  auto fetchP = [&](int g) {  // 1 / U(k, k) for the group's rows, on lanes 0 .. G-1
+    K c;
+    kzero(c);
+    const int row = n - 1 - (g * G + lane);
+    if (lane < G && row >= 0) c = ip[row];
+    return c;
+  };
+  cur = fetchU(0);
+  nxt = fetchU(1);
+  K pc = fetchP(0), pnx = fetchP(1);
+  for (int g = 0; g * G < n; ++g) {
+    const K nn = fetchU(g + 2), pnn = fetchP(g + 2);
 #pragma unroll
-      for (int d = 0; d < ND; ++d) cn[d] = U[(size_t)(k - 1) * ND + d];
-      pn = ip[k - 1];
+    for (int i = 0; i < G; ++i) {
+      const int k = n - 1 - (g * G + i);
+      if (k >= 0) {  // uniform
+        A s;
+        lift(s, 0.f);
+        if (live) s = x[2 * k];
+#pragma unroll
+        for (int d = ND; d >= 1; --d) mac(s, shfl(cur, i * ND + d - 1), win[d - 1]);
+        s = mul(s, shfl(pc, i));
+        if (live) x[2 * k] = s;
+#pragma unroll
+        for (int d = ND - 1; d >= 1; --d) win[d] = win[d - 1];
+        win[0] = s;
+      }
     }
-    A s = x[2 * k];
-#pragma unroll
-    for (int d = ND; d >= 1; --d) mac(s, c[d - 1], win[d - 1]);
-    s = mul(s, pv);
-    x[2 * k] = s;
-#pragma unroll
-    for (int d = ND - 1; d >= 1; --d) win[d] = win[d - 1];
-    win[0] = s;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) c[d] = cn[d];
-    pv = pn;
+    cur = nxt;
+    nxt = nn;
+    pc = pnx;
+    pnx = pnn;
   }
 }
 
@@ -253,16 +290,17 @@ __global__ void __launch_bounds__(256) current_kernel(CurArgs<T> a) {
   }
   __syncthreads();
 
-  // 3. forward (unit lower) and back (upper) substitution, one real system per lane
-  if ((int)threadIdx.x < 2 * rows) {
-    A* x = ph + (size_t)(threadIdx.x >> 1) * P * 2 + (threadIdx.x & 1);  // element k at x[2 k]
+  // 3. forward (unit lower) and back (upper) substitution, one real system per lane of warp 0
+  if (threadIdx.x < 32) {
+    const bool live = (int)threadIdx.x < 2 * rows;
+    A* x = ph + (size_t)(live ? threadIdx.x >> 1 : 0) * P * 2 + (threadIdx.x & 1);  // element k at x[2 k]
     const K* L = a.lo + (size_t)md * n * N;
     const K* U = a.up + (size_t)md * n * N;
     const K* ip = a.ipiv + (size_t)md * n;
     switch (N) {
 #define FDETD_SOLVE_CASE(ND) \
   case ND:                   \
-    solve_rows<ND>(x, n, L, U, ip); \
+    solve_rows<ND>(x, live, n, L, U, ip); \
     break;
       FDETD_SOLVE_CASE(1) FDETD_SOLVE_CASE(2) FDETD_SOLVE_CASE(3) FDETD_SOLVE_CASE(4)
       FDETD_SOLVE_CASE(5) FDETD_SOLVE_CASE(6) FDETD_SOLVE_CASE(7) FDETD_SOLVE_CASE(8)
