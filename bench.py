@@ -87,6 +87,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(loaded)}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over the ranks of the process group (x itself without one): every timed region of a
+    replica run is reported as its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, seconds, world):
+    """Whole-job throughput of `world` independent replicas that each processed units_per_rank units, timed
+    by the slowest rank (seconds = max over ranks)."""
+    return units_per_rank * world / seconds
+
+
 STAGE_SOURCE = {"projection": "k_tc.cu", "spectral": "k_spectral.cu", "backprojection": "k_tc.cu"}
 
 
@@ -542,13 +559,9 @@ def main():
     clk = clocks.stop()
     ktimes = plan.kernel_times()
     plan.set_profiling(False)
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
     cells = w.Nz * w.Nr * len(w.modes)
-    value = cells * args.steps * world / (ms / 1e3)
+    value = replica_rate(cells * args.steps, ms / 1e3, world)
 
     # end-to-end through the host entry point: h2d of fields + J, the step, d2h of the fields
     hf = torch.from_numpy(F).to(cdt).pin_memory()
@@ -559,11 +572,11 @@ def main():
     for _ in range(args.e2e_steps):
         fd.fdetd_step_host(plan, hf, hJ, 1)
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     elt = hf.element_size()
     h2d = hf.numel() * elt + (hJ.numel() * elt if hJ is not None else 0)
     d2h = hf.numel() * elt
-    e2e_val = cells * args.e2e_steps * world / e2e_s
+    e2e_val = replica_rate(cells * args.e2e_steps, e2e_s, world)
 
     # FP64 single-instance path on the same workload (the plain baseline the split path must beat)
     fp64_value = rel_err = None
