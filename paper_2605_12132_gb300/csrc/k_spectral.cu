@@ -15,7 +15,7 @@
 // z stencil D_z^(+/-) (Eq. spatial_derivativeSt along z).
 //
 // The z transform is an in-place mixed-radix FFT in shared memory (radix 8 for FP32,
-// radix 4 for FP64, the remaining factor last): decimation in frequency forward, so
+// radix 4 for FP64, the leftover factor as the first stage): decimation in frequency forward, so
 // kz comes out digit-reversed and the per-kz tables are stored in that order, and the
 // adjoint stages in reverse order for the inverse, which restores natural z order.
 // Each butterfly writes back where it read, so a stage needs one barrier.  The last
