@@ -300,6 +300,14 @@ def run_taylor(args, w):
             "config": {"workload": w.name, "taylor_order": args.taylor_order, "substeps": args.substeps,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "error_vs_exact_step": err, "launches_per_step": plan.launches_per_step + 1}}
+    # roofline of the term kernel: per term and cell*mode it reads the previous term and the running sum and
+    # writes the new term and the sum, 6 complex64 fields each (192 B)
+    algo = cells * 192 * plan.launches_per_step
+    peaks, src = _peaks()
+    roof = {"bound": "hbm", "achieved": algo / (ms / args.steps / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"traffic": None, "algorithmic": algo, "kernel": "taylor_term_kernel", "peak_source": src})
+    line["roofline"] = roof
     print(json.dumps(line), flush=True)
 
 
