@@ -180,7 +180,7 @@ def run_reference(args, w, rank, world):
 
 
 def uneven_instances(count, seed=0):
-    """The uneven-instance mix: Nz in {512, 1024, 2048, 4096} (powers of two: this build's z transform),
+    """The uneven-instance mix: Nz in {512, 1024, 2048, 4096} (powers of two: what the library's z transform takes),
     even Nr in [64, 512], M in {1, 2, 3}, order 8 or 16, m = 1 pulse with waist 10-40 dr, seeded current."""
     from paper_2605_12132_gb300 import inputs
     rng = np.random.default_rng(seed)

@@ -50,7 +50,7 @@ enum {
   FDETD_ERR_OOM = 2,         /* device or host allocation failed */
   FDETD_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   FDETD_ERR_EIG = 4,         /* radial eigen-decomposition failed (complex or singular spectrum) */
-  FDETD_ERR_UNSUPPORTED = 5, /* valid request this build does not implement (e.g. Nz not a power of 2) */
+  FDETD_ERR_UNSUPPORTED = 5, /* valid request the library does not implement (e.g. Nz not a power of 2) */
   FDETD_ERR_TIMEOUT = 6      /* a kernel's bounded pipeline wait expired; it stopped early and freed its resources */
 };
 
@@ -75,7 +75,7 @@ typedef struct fdetd_taylor_s* fdetd_taylor_t;
  * (even, 2..32) in z and rho (Eq. spatial_derivativeSt), the parity-dependent
  * axis extensions of Eqs. spatialAM_derivativeS/A, the B_z axis value of
  * Sec. 2.4, taps beyond the outer radius dropped (Sec. 2.2), periodic z.
- * Nz >= 2 (this build: a power of two, 64..8192), Nr >= order/2 + 2, M >= 0.
+ * Nz >= 2 (the z transform takes a power of two, 64..8192), Nr >= order/2 + 2, M >= 0.
  * The radial eigen-decompositions, the omega table and the phase factors are
  * computed in FP64 on the host; device tables are allocated here and owned by
  * the plan.  Blocking; not stream-ordered.

@@ -110,7 +110,7 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   if (!modes || nmodes < 1 || nmodes > 64) return fail(FDETD_ERR_ARG, "need 1..64 modes");
   if (precision < FDETD_PREC_FP64 || precision > FDETD_PREC_BF16X6) return fail(FDETD_ERR_ARG, "unknown precision");
   if (!is_pow2(Nz) || Nz < 64 || Nz > 8192)
-    return fail(FDETD_ERR_UNSUPPORTED, "this build needs Nz a power of two in 64..8192");
+    return fail(FDETD_ERR_UNSUPPORTED, "the z transform needs Nz a power of two in 64..8192");
   const bool hasJ_max = true;
   if (spectral_smem_bytes(Nz, precision, hasJ_max) > 227 * 1024)
     return fail(FDETD_ERR_UNSUPPORTED, "Nz too long for the single-pass z transform at this precision");
