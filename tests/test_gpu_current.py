@@ -12,7 +12,8 @@ if not torch.cuda.is_available():
 
 import paper_2605_12132_gb300 as fd  # noqa: E402
 
-# FP32 inputs and outputs (the solve itself is FP64): a few e-7 relative; FP64 end to end
+# FP32 inputs and outputs (divergence, solve and gradient in double-float arithmetic): a few e-7 relative;
+# FP64 end to end
 TOL = {"fp64": 1e-11, "fp32": 2e-6}
 
 
