@@ -1,5 +1,7 @@
 """Pins of the current-pipeline oracle (Sec. 2.5 current stagger, Sec. 3 planar current correction) and of
 the host-built bands and LU factors the GPU kernels use."""
+import math
+
 import numpy as np
 import pytest
 import scipy.linalg
@@ -18,7 +20,8 @@ def test_downstagger_parity_at_the_axis(order):
     Nr, dr, a = 24, 0.1, 1.7
     rp, rm = (np.arange(Nr) + 0.5) * dr, np.arange(Nr) * dr
     inner = slice(0, Nr - order)
-    tol = 30 * (a * dr) ** order
+    N = order // 2   # twice the Lagrange remainder bound of the half-point value, |f^(2N)| <= a^(2N)
+    tol = 2 * np.prod([abs(0.5 - t) for t in range(-N + 1, N + 1)]) / math.factorial(order) * (a * dr) ** order
     ge = cur.s_rho_minus(np.cos(a * rp)[None, :], order, True)[0]
     go = cur.s_rho_minus(np.sin(a * rp)[None, :], order, False)[0]
     assert np.abs(ge - np.cos(a * rm))[inner].max() < tol
@@ -48,6 +51,32 @@ def test_consistent_current_is_left_unchanged(m):
     out, phi = cur.current_pipeline(J, rho_xy, m, order, dr)
     assert np.abs(phi).max() < 1e-12 * np.abs(rho_xy).max()
     assert np.allclose(out[1], J[1]) and np.array_equal(out[2], J[2])
+
+
+def _gradient_residual(m, order, Nr, dr):
+    # J_perp = grad_perp psi = (d psi / d rho, (i sigma m / rho) psi), sigma = -1, for psi = rho^m exp(-(rho / w)^2)
+    # (parity m, decayed long before the outer radius), J_z arbitrary, rho_xy = 0
+    Nz, w = 8, 0.2 * Nr * dr
+    rp = (np.arange(Nr) + 0.5) * dr
+    ez = np.exp(2j * np.pi * np.arange(Nz) / Nz)[:, None]
+    g = np.exp(-(rp / w) ** 2)
+    psi = rp ** m * g
+    dpsi = (m * rp ** (m - 1) if m else 0.0) * g - 2 * rp ** (m + 1) / w ** 2 * g
+    J = np.stack([ez * dpsi, ez * (-1j) * m * psi / rp, ez * psi])
+    out, _ = cur.current_pipeline(J, np.zeros((Nz, Nr), complex), m, order, dr)
+    return max(np.abs(out[c]).max() for c in range(2)) / max(np.abs(J[c]).max() for c in range(2))
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_gradient_current_without_density_is_removed(m):
+    # A planar gradient current with no density is pure divergence error: the correction phi = -psi removes
+    # J_rho and J_theta entirely, up to the difference between the centred L_rho - m^2 rho^-2 of the solve and
+    # the staggered composite Div+ D- of the divergence (both order 2 N_D): halving dr divides the residual by
+    # about 2^8 at order 8.
+    order = 8
+    coarse, fine = _gradient_residual(m, order, 48, 0.1), _gradient_residual(m, order, 96, 0.05)
+    assert fine < 1e-8, (coarse, fine)
+    assert np.log2(coarse / fine) > order - 1, (coarse, fine)
 
 
 @pytest.mark.parametrize("m", [0, 1, 2])

@@ -2,6 +2,8 @@
 import os
 from fractions import Fraction
 
+import math
+
 import numpy as np
 import pytest
 import scipy.interpolate
@@ -43,6 +45,14 @@ def test_z_upstagger_converges_at_its_order(order):
     assert rate > order - 0.7, (errs, rate)
 
 
+def _lagrange_bound(order, h):
+    """Twice the Lagrange remainder bound of the half-point value from the 2 N_D nodes t = -N_D+1 .. N_D
+    for cos(a x) or sin(a x) sampled at spacing dr (|f^(2 N_D)| <= a^(2 N_D)), h = a dr."""
+    N = order // 2
+    prod = np.prod([abs(0.5 - t) for t in range(-N + 1, N + 1)])
+    return 2 * prod / math.factorial(order) * h ** order
+
+
 @pytest.mark.parametrize("order", [4, 8])
 def test_radial_upstagger_parity_at_the_axis(order):
     # even function with the symmetric extension, odd function with the antisymmetric one: high-order
@@ -54,7 +64,7 @@ def test_radial_upstagger_parity_at_the_axis(order):
     inner = slice(0, Nr - order)            # away from the dropped outer taps
     ge = ds.s_rho_plus(even, order, True)[0]
     go = ds.s_rho_plus(odd, order, False)[0]
-    tol = 30 * (a * dr) ** order     # interpolation error ~ h^order
+    tol = _lagrange_bound(order, a * dr)
     assert np.abs(ge - np.cos(a * rp))[inner].max() < tol
     assert np.abs(go - np.sin(a * rp))[inner].max() < tol
     assert np.abs(ds.s_rho_plus(even, order, False)[0] - np.cos(a * rp))[:2].max() > 1e-3
