@@ -175,6 +175,28 @@ def _full_step_uses_the_half_step(mp):
     mp.setattr(mx, "_propagators", bad)
 
 
+def _realspace_faraday_sign(mp):
+    # dB_theta/dt = +D_z^- E_rho + D^- E_z instead of -D_z^- E_rho + D^- E_z in the real-space operator
+    orig = mx.apply_H
+
+    def bad(F, rad, order, dz):
+        out = orig(F, rad, order, dz)
+        out[4, :, 1:] += 2 * mx.dz_minus(F[0], order, dz)[:, 1:]
+        return out
+    mp.setattr(mx, "apply_H", bad)
+
+
+def _absorbing_damping_once(mp):
+    # exp(-sigma dt / 4) applied once per step instead of on both sides of the Taylor step
+    def bad(a, at, chi, sigma, order, taylor_order, dz, dr, dt, nsteps=1, k0=ev.K0, m=0):
+        damp = np.exp(-sigma * dt / 4)
+        for _ in range(nsteps):
+            a, at = a * damp, at * damp
+            a, at = ev.envelope_step(a, at, chi + sigma ** 2, order, taylor_order, dz, dr, dt, 1, k0, m)
+        return a, at
+    mp.setattr(ev, "envelope_step_absorbing", bad)
+
+
 CASES = [
     ("staggered c_2 sign", _c2_sign_flipped, lambda: P.test_staggered_textbook_values()),
     ("D- mirror sign ignored", _dminus_parity_ignored, lambda: P.test_radial_derivative_convergence_near_axis(1, 4)),
@@ -196,6 +218,9 @@ CASES = [
     ("E_rho / B_theta axis value dropped for m = 1", _polar_axis_value_dropped, lambda: P.test_axis_output_values()),
     ("full step advanced by the half-step exponential", _full_step_uses_the_half_step,
      lambda: P.test_three_evaluators_agree(2)),
+    ("Faraday sign in the real-space operator", _realspace_faraday_sign, lambda: P.test_three_evaluators_agree(0)),
+    ("absorbing-layer damping on one side only", _absorbing_damping_once,
+     lambda: PE.test_absorbing_step_with_a_uniform_layer_factorises()),
 ]
 
 
