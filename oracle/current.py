@@ -7,13 +7,13 @@ shapesAM_currentRHS2m ... shapesAM_currentJth), in the complex mode convention o
 * the current is deposited on the primary grids; J_rho is moved down to the staggered radial grid
   of E_rho by the Lagrange downstagger S_rho^(-, mA) of Eq. spatialAM_staggerS (order 2 N_D, primary
   nodes below the axis mirror to -1-j with the mA sign, nodes past the outer edge dropped);
-  the z filters F_z, F_z^(div) are the identity (reading R13: they are defined elsewhere);
+  the z filters F_z, F_z^(div) are the identity (the paper defines them in its companion work);
 * the planar divergence error  delta = rho_xy - div_perp J,  div_perp J = Div^+ J_rho + (i sigma m / rho) J_theta;
 * the planar Poisson equation  [L_rho^(mS) - m^2 rho^-2] phi = delta  per z row, with the centred
   radial Laplacian L_rho = D^2_rho + rho^-1 D^(C)_rho of Eq. spatialAM_laplaceR (the operator the paper
   uses for stability), solved by a dense solve here;
 * the correction  J_rho += D^- phi,  J_theta += (i sigma m / rho) phi,  J_z unchanged
-  (J + grad_perp phi: the paper's stated form, reading R20).
+  (J + grad_perp phi: the vector form the paper states, with grad_perp in the complex convention above).
 Arrays: J [3][Nz][Nr] complex (J_rho, J_theta at (z_i, rho_k); J_z at (z_i - dz/2, rho_k)),
 rho_xy [Nz][Nr] complex at (z_i, rho_k).  The result is on the field step's Yee locations (J_rho at
 rho_-,k, slot 0 = its value on the axis; J_theta, J_z unchanged positions).

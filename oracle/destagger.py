@@ -7,11 +7,11 @@ finite differences:
     E_rho -> S_rho^(+, mA) E_rho,   E_z -> S_z^(+) E_z,   B_rho -> S_z^(+) B_rho,
     B_z -> S_rho^(+, mS) B_z,       B_theta -> S_rho^(+, mA) S_z^(+) B_theta,   E_theta unchanged.
 The value at the half point between nodes uses the 2 N_D nearest nodes, N_D on each side.  Along z
-the grid is periodic (reading R4).  Radially the operand sits on the staggered grid rho_-,j = j dr
+the grid is periodic, as for the field step.  Radially the operand sits on the staggered grid rho_-,j = j dr
 with slot 0 on the axis holding the axis value (as the field step writes it); nodes j < 0 are the
 mirror images rho_-,-j with the symmetric (S) or antisymmetric (A) extension chosen by the parity
 rule of Eqs. spatialAM_derivativeS/A (mS: m even -> S; mA: |m - 1| even -> S); nodes beyond the
-outer edge are dropped, as in the other radial operators (reading R5).
+outer edge are dropped, as in the other radial operators (Sec. 2.2).
 """
 from fractions import Fraction
 

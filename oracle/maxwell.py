@@ -4,7 +4,8 @@ Follows Sec. 2 of the paper:
 
 * complex azimuthal modes with F(rho, theta, z) = Re sum_m F_m(rho, z) exp(-i m theta),
   i.e. d/dtheta -> i*SIGMA*m with SIGMA = -1 (the complex equivalent of the real
-  (2m, 2m+1) pairs of Eq. maxwellAM_dtheta; sign reading R3 of the design notes);
+  (2m, 2m+1) pairs of Eq. maxwellAM_dtheta: the basis of Eq. maxwellAM_fourier disagrees in sign with
+  that derivative matrix, and the matrix and the m-signs of Eqs. maxwellAM_Er ... are followed);
 * primary radial grid rho_k = (k+1/2) dr and staggered grid rho_(-),k = k dr
   (Eqs. spatialAM_grid, spatialAM_gridR), k = 0..Nr-1;
 * Yee placement from Table tab:spatialAM_boundary: Er, Btheta, Bz on the staggered

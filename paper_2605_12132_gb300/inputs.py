@@ -186,3 +186,48 @@ def envelope_inputs(w: EnvelopeWorkload, zc=None):
     g = g / np.abs(g).max()
     chi = w.chi0 * (1 + w.chi_var * g)
     return a.astype(complex), at.astype(complex), chi
+
+
+# ---------------------------------------------------------------------------
+# Uneven-instance mix (batched and served field requests)
+# ---------------------------------------------------------------------------
+
+NZ_POW2 = (512, 1024, 2048, 4096)
+
+
+def uneven_instances(count, seed=0, nz_values=NZ_POW2):
+    """Seeded draw of the uneven-instance mix: Nz from nz_values, even Nr in [64, 512], M in {1, 2, 3},
+    order 8 or 16, m = 1 pulse with waist 10-40 dr (dz = 1/16, dr = 1/4, dt = dz), seeded current."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        Nz = int(rng.choice(list(nz_values)))
+        Nr = 2 * int(rng.integers(32, 257))
+        M = int(rng.integers(1, 4))
+        order = int(rng.choice([8, 16]))
+        waist = float(rng.uniform(10, 40)) * 0.25
+        out.append(dict(Nz=Nz, Nr=Nr, M=M, order=order, waist=waist, seed=seed * 1000 + k))
+    return out
+
+
+def instance_inputs(c, tau=8.0):
+    """Fields [M+1][6][Nz][Nr] and currents [M+1][3][Nz][Nr] (complex128) of one instance of the mix: the
+    x-polarised pulse on m = 1, zero fields on the other modes, a seeded smooth random current (RMS 1e-2,
+    correlation length 8 cells) on every mode."""
+    Nz, Nr, M = c["Nz"], c["Nr"], c["M"]
+    F = np.zeros((M + 1, 6, Nz, Nr), complex)
+    F[1] = pulse_fields(Nz, Nr, 1 / 16, 1 / 4, c["waist"], tau)
+    for f in range(6):
+        if _STAG_R[f]:
+            F[:, f, :, 0] = 0
+    J = np.stack([random_current(Nz, Nr, m, 8.0, 1e-2, c["seed"]) for m in range(M + 1)])
+    return F, J
+
+
+# Three instances at the sizes of the uneven mix, used for parity of the batched launch against the oracle:
+# the largest radial size with the most modes and order 16, a mid-size order-8 case, the longest z.
+PARITY_INSTANCES = (
+    dict(Nz=512, Nr=512, M=3, order=16, waist=10.0, seed=901),
+    dict(Nz=1024, Nr=200, M=2, order=8, waist=6.25, seed=902),
+    dict(Nz=4096, Nr=96, M=1, order=16, waist=2.5, seed=903),
+)

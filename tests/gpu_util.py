@@ -1,26 +1,91 @@
-"""Helpers shared by the GPU tests (error metric of the parity checks)."""
+"""Helpers shared by the GPU tests: the per-field error metrics of the parity checks.
+
+Every parity check reports, per mode and field, against the FP64 oracle:
+  l2    ||X - X_ref||_2 / max(||X_ref||_2, 1e-12 ||Psi_ref||_2)       (relative L2 per field)
+  elem  max |X - X_ref| / max(max |X_ref|, 1e-12 max |Psi_ref|)      (element-wise, so that an error
+                                                                       localised in a few rows cannot
+                                                                       hide in a norm over the grid)
+  share ||X_ref|| / ||Psi_ref||                                      (how much of the state the field carries)
+and, for full grids, the element-wise error of three radial regions measured against the field's own
+maximum: the axis slot (k = 0), the first N_D radii and the last N_D radii.
+
+Fields that carry under 10% of the state (E_z and B_z of a paraxial pulse, the azimuthal fields of a mode
+driven only by the current) are 'weak': on every FP32-class path each output component mixes all the
+components of its family through the radial transforms, so its absolute error scales with the state's
+norm, not its own.  The tests assert strong fields against the per-step tolerance and weak fields against
+separately stated, measured bounds; both are printed.
+"""
 import numpy as np
 
+FLOOR = 1e-12
+WEAK_SHARE = 0.1
 
-def field_errors(got, ref, floor=1e-12):
-    """Per-field relative L2 error ||X - X_ref|| / max(||X_ref||, floor ||Psi_ref||) of one mode.
 
-    got, ref: [6][Nz][Nr].  floor = 1e-12 for the FP64 path (a field below 1e-12 of the
-    state's norm, e.g. Ez, Bz early in a vacuum run, is measured against the state).  The
-    reduced-precision paths use floor = 0.1: every output component mixes all components of
-    its group through the radial transforms, so its absolute error scales with the state's
-    norm, and a field carrying under 10% of that norm is measured against 10% of it.
-    """
-    tot = np.linalg.norm(ref)
+STAGGERED_R = (True, False, False, False, True, True)   # fields whose radial slot 0 is the axis
+
+
+def _report(gs, rs, nd=None):
+    tot = np.sqrt(sum(np.linalg.norm(r) ** 2 for r in rs))
+    tmax = max(np.abs(r).max() for r in rs)
+    rows = []
+    for g, r in zip(gs, rs):
+        d = np.abs(g - r)
+        den_max = max(np.abs(r).max(), FLOOR * tmax)
+        row = {"l2": float(np.linalg.norm(g - r) / max(np.linalg.norm(r), FLOOR * tot)),
+               "elem": float(d.max() / den_max),
+               "share": float(np.linalg.norm(r) / tot) if tot > 0 else 0.0}
+        if nd is not None:
+            row["axis"] = float(d[..., 0].max() / den_max)
+            row["near"] = float(d[..., 1:nd + 1].max() / den_max)
+            row["edge"] = float(d[..., -nd:].max() / den_max)
+        rows.append(row)
+    return rows
+
+
+def field_report(got, ref, nd=None):
+    """Per-field metrics of one mode on the full grid: got, ref [6][Nz][Nr]; nd = N_D adds the radial
+    regions (axis slot, first N_D radii, last N_D radii)."""
+    return _report(list(got), list(ref), nd)
+
+
+def column_report(got, ref):
+    """Per-field metrics of one mode on sampled kz columns: got, ref [nq][6][Nr] spectral columns, compared
+    on the unknowns (the axis slot of the staggered-grid fields is not part of the state)."""
+    gs = [np.stack([c[f][1:] if STAGGERED_R[f] else c[f] for c in got]) for f in range(6)]
+    rs = [np.stack([c[f][1:] if STAGGERED_R[f] else c[f] for c in ref]) for f in range(6)]
+    return _report(gs, rs)
+
+
+def format_report(rows, label=""):
+    names = ("Er", "Et", "Ez", "Br", "Bt", "Bz")
     out = []
-    for f in range(ref.shape[0]):
-        den = max(np.linalg.norm(ref[f]), floor * tot)
-        out.append(np.linalg.norm(got[f] - ref[f]) / den)
-    return np.array(out)
+    for n, r in zip(names, rows):
+        extra = "".join(f" {k}={r[k]:.2e}" for k in ("axis", "near", "edge") if k in r)
+        out.append(f"{label} {n}: l2={r['l2']:.2e} elem={r['elem']:.2e}{extra} share={r['share']:.3f}")
+    return "\n".join(out)
 
 
-def floor_for(prec):
-    return 1e-12 if prec == "fp64" else 0.1
+def check_report(rows, tol, tol_weak, elem_factor=3.0, label=""):
+    """Strong fields: l2 <= tol and every element-wise figure <= elem_factor * tol; weak fields (share under
+    10%) the same against tol_weak.  Raises AssertionError with the full report on failure."""
+    bad = []
+    for f, r in enumerate(rows):
+        t = tol if r["share"] >= WEAK_SHARE else tol_weak
+        if not r["l2"] <= t:
+            bad.append((f, "l2", r["l2"], t))
+        for k in ("elem", "axis", "near", "edge"):
+            if k in r and not r[k] <= elem_factor * t:
+                bad.append((f, k, r[k], elem_factor * t))
+    assert not bad, f"{label}: {bad}\n" + format_report(rows, label)
+
+
+def kz_columns(G, qs):
+    """DFT along z (axis -2) of G [..][Nz][Nr] at the kz indices qs only (numpy's sign convention):
+    returns [..][len(qs)][Nr]."""
+    Nz = G.shape[-2]
+    z = np.arange(Nz)
+    W = np.exp(-2j * np.pi * np.outer(qs, z) / Nz)     # [nq][Nz]
+    return np.einsum("qz,...zr->...qr", W, G)
 
 
 def zero_axis(F):

@@ -5,7 +5,7 @@ import pytest
 from oracle import diagnostics as dg
 from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
-from tests.gpu_util import field_errors, floor_for, zero_axis
+from tests.gpu_util import check_report, column_report, field_report, format_report, kz_columns, zero_axis
 
 pytestmark = pytest.mark.gpu
 
@@ -15,15 +15,22 @@ if not torch.cuda.is_available():
 
 import paper_2605_12132_gb300 as fd  # noqa: E402
 
-# Per-step relative error budget per field (R18 metric) of each precision against the FP64 oracle:
+# Per-step relative error budget of each precision against the FP64 oracle, for fields that carry at
+# least 10% of the state (relative L2 per field, floor 1e-12 of the state's norm):
 #  fp64   - FP64 round trip: single-step agreement ~1e-13; the projection/back-projection pair
 #           reproduces the identity only to ~1e-14 entrywise (it divides by the small radial
 #           eigenvalues), so over many steps the difference grows ~1e-13 per step;
 #  fp32   - FP32 storage + FP32 CUDA-core GEMMs + FP32 FFT: ~5e-7 per step;
 #  bf16x6 - 3-piece bf16 operands (24 bits); the leading product and the correction products in separate
-#           tensor-core accumulators (each MMA truncates its FP32 sum toward zero): <= 1e-6 per step;
+#           tensor-core accumulators (each MMA truncates its FP32 sum toward zero): <= 1e-6 per step up
+#           to Nr = 256 (2e-6 at Nr = 512: the leading accumulation chain is twice as long);
 #  bf16x3 - 2-piece bf16 operands (16 bits): representation error 2^-17 per operand, ~1e-5 per step.
 TOL = {"fp64": 1e-12, "fp32": 1e-6, "bf16x6": 1e-6, "bf16x3": 2.5e-5}
+# Fields under 10% of the state carry the state-scale absolute error of the radial transforms: measured on
+# the 256 x 64 vacuum pulse, whose E_z and B_z hold 0.8% of the state, after one step (true relative
+# error): fp32 1.2e-6, bf16x6 1.0e-6, bf16x3 1.2e-4 (element-wise at the axis slot, where the axis
+# extrapolation adds its own amplification: 5e-6, 4.9e-6, 6.3e-4).
+TOL_WEAK = {"fp64": 1e-12, "fp32": 3e-6, "bf16x6": 3e-6, "bf16x3": 3e-4}
 ALL = ["fp64", "fp32", "bf16x3", "bf16x6"]
 
 
@@ -56,12 +63,15 @@ def ragged_case():
 
 @pytest.mark.parametrize("prec", ALL)
 def test_parity_small_ragged(prec, ragged_case):
+    # random fields on every component (all fields strong), 3 steps: per-field L2, element-wise, and the
+    # axis slot, the first N_D radii and the last N_D radii separately
     F, J, args, ref = ragged_case
-    modes = args[2]
+    modes, order, nsteps = args[2], args[3], args[7]
     got = _run(prec, F, J, *args)
     for i in range(len(modes)):
-        err = field_errors(got[i], ref[i], floor_for(prec))
-        assert err.max() < TOL[prec] * 3, (modes[i], err)
+        rows = field_report(got[i], ref[i], nd=order // 2)
+        print("\n" + format_report(rows, f"{prec} m={modes[i]}"))
+        check_report(rows, TOL[prec] * nsteps, TOL_WEAK[prec] * nsteps, label=f"{prec} m={modes[i]}")
 
 
 @pytest.fixture(scope="module")
@@ -77,13 +87,17 @@ def vacuum_ref():
 def test_parity_vacuum_pulse_256x64(prec, vacuum_ref):
     # the 256 x 64 vacuum pulse (m = 1, order 8, dt = dz): after 1 step and after 200 steps
     w, F, r1, r200 = vacuum_ref
+    nd = w.order // 2
     g1 = _run(prec, F, None, w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, 1)
-    e1 = field_errors(g1[0], r1, floor_for(prec))
-    rel = [np.linalg.norm(r1[f]) / np.linalg.norm(r1) for f in range(6)]
-    assert e1.max() < TOL[prec], (e1, rel)
+    rows = field_report(g1[0], r1, nd=nd)
+    print("\n" + format_report(rows, f"{prec} 1 step"))
+    check_report(rows, TOL[prec], TOL_WEAK[prec], label=f"{prec} 1 step")
     g200 = _run(prec, F, None, w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, w.steps)
-    err = field_errors(g200[0], r200, floor_for(prec))
-    assert err.max() < TOL[prec] * (0.25 if prec == "fp64" else 1) * w.steps, err
+    rows = field_report(g200[0], r200, nd=nd)
+    print(format_report(rows, f"{prec} {w.steps} steps"))
+    # error grows at most linearly with the step count (fp64: a quarter of that, ~1e-13 per step)
+    t = TOL[prec] * (0.25 if prec == "fp64" else 1) * w.steps
+    check_report(rows, t, t, label=f"{prec} {w.steps} steps")
 
 
 def test_zero_steps_and_null_current():
@@ -129,6 +143,12 @@ def test_host_entry_point_matches_device():
     assert np.abs(host.numpy() - dev.cpu().numpy()).max() < 1e-14
 
 
+# The 2048 x 256 current-driven workload after 2 steps, on sampled kz columns: mode 0 starts at zero and is
+# driven by the current alone, so its B_r and B_theta carry well under 1% of its state; their true
+# relative error is bounded separately (measured levels x 3).
+TOL_WEAK_2048 = {"fp64": 1e-11, "fp32": 6e-5, "bf16x6": 3e-5, "bf16x3": 1e-3}
+
+
 @pytest.mark.parametrize("prec", ALL)
 def test_full_size_2048x256_sampled_kz(prec):
     # the 2048 x 256, modes 0-1, order 16 current-driven workload: compare sampled kz columns
@@ -142,15 +162,10 @@ def test_full_size_2048x256_sampled_kz(prec):
     for i, m in enumerate(w.modes):
         ref = mx.step_spectral(F[i], J[i], w.Nz, w.Nr, m, w.order, w.dz, w.dr, w.dt, nsteps=nsteps,
                                kz_subset=qs, method="eig")
-        Gh = np.fft.fft(got[i], axis=1)
-        # a column whose reference is small (Nyquist of a smooth field, or mode 0 that starts at
-        # zero and is driven by J) is measured against the RMS column norm of the whole state
-        col_scale = np.linalg.norm(Gh) / np.sqrt(w.Nz)
-        for q in qs:
-            colg = mx.gather(Gh[:, q, :])
-            colr = mx.gather(ref[q])
-            err = np.linalg.norm(colg - colr) / max(np.linalg.norm(colr), col_scale)
-            assert err < TOL[prec] * nsteps * 2, (m, q, err)
+        Gq = kz_columns(got[i], qs)                           # [6][nq][Nr]
+        rows = column_report([Gq[:, k, :] for k in range(len(qs))], [ref[q] for q in qs])
+        print("\n" + format_report(rows, f"{prec} m={m}"))
+        check_report(rows, TOL[prec] * nsteps, TOL_WEAK_2048[prec], label=f"{prec} m={m}")
 
 
 @pytest.mark.parametrize("prec", ALL)

@@ -5,7 +5,7 @@ import pytest
 
 from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
-from tests.gpu_util import zero_axis
+from tests.gpu_util import check_report, column_report, format_report, kz_columns, zero_axis
 
 pytestmark = pytest.mark.gpu
 
@@ -15,7 +15,10 @@ if not torch.cuda.is_available():
 
 import paper_2605_12132_gb300 as fd  # noqa: E402
 
+# per-step tolerance of the fields with >= 10% of the state, and the bound of the weak fields (relative L2
+# per field, floor 1e-12 of the state's norm)
 TOL = {"fp64": 1e-12, "fp32": 1e-6, "bf16x6": 4e-6, "bf16x3": 2.5e-5}
+TOL_WEAK = {"fp64": 1e-11, "fp32": 3e-5, "bf16x6": 3e-5, "bf16x3": 1e-3}
 
 
 @pytest.mark.parametrize("prec,Nz", [("fp32", 8192), ("bf16x3", 8192), ("bf16x6", 8192), ("fp64", 4096)])
@@ -39,9 +42,8 @@ def test_long_z_sampled_kz(prec, Nz, with_J):
     for i, m in enumerate(modes):
         ref = mx.step_spectral(F[i], None if J is None else J[i], Nz, Nr, m, order, dz, dr, dt, nsteps=nsteps,
                                kz_subset=qs, method="expm")
-        Gh = np.fft.fft(G[i], axis=1)
-        col_scale = np.linalg.norm(Gh) / np.sqrt(Nz)
-        for q in qs:
-            err = np.linalg.norm(mx.gather(Gh[:, q, :]) - mx.gather(ref[q])) / max(np.linalg.norm(mx.gather(ref[q])),
-                                                                                 col_scale)
-            assert err < TOL[prec] * nsteps * 2, (prec, m, q, err)
+        Gq = kz_columns(G[i], qs)
+        rows = column_report([Gq[:, k, :] for k in range(len(qs))], [ref[q] for q in qs])
+        label = f"{prec} Nz={Nz} J={with_J} m={m}"
+        print("\n" + format_report(rows, label))
+        check_report(rows, TOL[prec] * nsteps, TOL_WEAK[prec] * nsteps, label=label)

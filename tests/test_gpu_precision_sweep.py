@@ -2,14 +2,17 @@
 two-mode current-driven workload (per field, on kz columns inside and outside the pulse band).
 
 The oracle evaluates the sampled kz columns exactly (per-kz expm, 1e-14 over thousands of steps);
-the GPU result is transformed along z and compared on the same columns.  Bounds are the measured
-levels with margin; the table is printed (pytest -s) and recorded in the design notes.
+the GPU result is transformed along z at those columns and compared.  Per mode and field: relative L2
+with a floor of 1e-12 of the state's norm, and the element-wise error; fields under 10% of the state
+(the magnetic fields of mode 0, driven by the current alone; E_z and B_z of the pulse mode) have their
+own bound.  Bounds are the measured levels with margin; the table is printed (pytest -s).
 """
 import numpy as np
 import pytest
 
 from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
+from tests.gpu_util import check_report, column_report, format_report, kz_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -20,12 +23,14 @@ if not torch.cuda.is_available():
 import paper_2605_12132_gb300 as fd  # noqa: E402
 
 COUNTS = [1, 100, 1000]
-# Measured levels x ~3 (GB300).  Errors grow about linearly with the step count: the rounding of the
-# fixed projection / back-projection matrices and the tensor cores' FP32 accumulation make the round
-# trip differ from the identity by the same small operator every step (coherent), on top of the
-# random rounding of the FP32 state.  None of the FP32-state paths reaches 1e-6 after 1000 steps.
-BOUND = {"fp64": [3e-12, 3e-10, 3e-9], "fp32": [1e-6, 1.5e-5, 2e-4],
-         "bf16x6": [1e-6, 2.5e-4, 2.5e-3], "bf16x3": [3e-5, 1.2e-3, 1.2e-2]}
+# Measured levels x ~3 (GB300), (strong, weak) per count.  Errors grow about linearly with the step count:
+# the rounding of the fixed projection / back-projection matrices and the tensor cores' FP32 accumulation
+# make the round trip differ from the identity by the same small operator every step (coherent), on top
+# of the random rounding of the FP32 state.  None of the FP32-state paths reaches 1e-6 after 1000 steps.
+BOUND = {"fp64": [(3e-12, 3e-11), (3e-10, 3e-9), (3e-9, 3e-8)],
+         "fp32": [(1e-6, 1e-4), (1.5e-5, 1e-4), (1.5e-4, 3e-4)],
+         "bf16x6": [(1e-6, 1e-4), (3e-4, 1e-3), (2.5e-3, 5e-3)],
+         "bf16x3": [(3e-5, 3e-3), (1.2e-3, 5e-3), (1.2e-2, 3e-2)]}
 W = inputs.workload("lwfa_m01_2048x256")
 QS = [128, 120, 140, 1, 700]   # q = Nz dz = 128 is the carrier kz = 2 pi; 1 and 700 lie outside the band
 
@@ -37,18 +42,6 @@ def oracle_cols():
                                    kz_subset=QS, method="expm") for i, m in enumerate(W.modes)]
 
 
-def _errors(G, ref):
-    """per-field error on the sampled columns, fields under 10% of the state measured against 10% of it"""
-    Gh = np.fft.fft(G, axis=1)
-    err = np.zeros(6)
-    tot = np.sqrt(sum(np.linalg.norm(ref[q]) ** 2 for q in QS))
-    for f in range(6):
-        num = np.sqrt(sum(np.linalg.norm(mx.gather_field(Gh[:, q, :], f) - mx.gather_field(ref[q], f)) ** 2 for q in QS))
-        den = np.sqrt(sum(np.linalg.norm(mx.gather_field(ref[q], f)) ** 2 for q in QS))
-        err[f] = num / max(den, 0.1 * tot)
-    return err
-
-
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16x6", "fp32", "fp64"])
 def test_precision_sweep(prec, oracle_cols):
     F, J, refs = oracle_cols
@@ -56,16 +49,18 @@ def test_precision_sweep(prec, oracle_cols):
     f = torch.from_numpy(F).to(plan.complex_dtype).cuda()
     j = torch.from_numpy(J).to(plan.complex_dtype).cuda()
     done = 0
-    rows = []
+    failures = []
     for ci, n in enumerate(COUNTS):
         fd.fdetd_step(plan, f, j, n - done)
         done = n
         plan.status()
-        G = f.cpu().numpy().astype(np.complex128)
+        G = kz_columns(f.cpu().numpy().astype(np.complex128), QS)
         for i, m in enumerate(W.modes):
-            e = _errors(G[i], refs[i][ci])
-            rows.append((n, m, e))
-            assert e.max() < BOUND[prec][ci], (prec, n, m, e)
-    print(f"\n{prec}: steps, mode, per-field error (Er, Et, Ez, Br, Bt, Bz)")
-    for n, m, e in rows:
-        print(f"  {prec} {n:5d} m={m} " + " ".join(f"{x:.2e}" for x in e))
+            rows = column_report([G[i][:, k, :] for k in range(len(QS))], [refs[i][ci][q] for q in QS])
+            label = f"{prec} {n:5d} steps m={m}"
+            print("\n" + format_report(rows, label))
+            try:
+                check_report(rows, *BOUND[prec][ci], label=label)
+            except AssertionError as e:
+                failures.append(str(e))
+    assert not failures, "\n".join(failures)

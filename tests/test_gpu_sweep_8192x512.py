@@ -4,21 +4,21 @@ the pulse band.  The oracle's columns are precomputed by tests/golden/make_sweep
 exponential per column takes minutes) and read from tests/golden/sweep_8192x512_ref.npz.  FP64 is absent: its
 single-pass z transform stops at Nz = 4096.
 
-Opt-in (several minutes of device and host time): FDETD_FULL_SWEEP=1 pytest -m gpu -s tests/test_gpu_sweep_8192x512.py
-The bounds are ten times the measured 2048 x 256 levels until this size has been measured.
+Per mode and field: relative L2 with a floor of 1e-12 of the state's norm, and the element-wise error.  Fields
+carrying at least 10% of the state are checked against the strong bound, the others (the radial and
+azimuthal magnetic fields of mode 0, which the current alone drives, and E_z, B_z of the pulse mode) against
+the weak bound.  Bounds are the measured levels (GB300) x 2-3; the table is printed (pytest -s).
 """
 import os
 
 import numpy as np
 import pytest
 
-from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
+from tests.gpu_util import check_report, column_report, format_report, kz_columns
 
 pytestmark = pytest.mark.gpu
 
-if os.environ.get("FDETD_FULL_SWEEP") != "1":
-    pytest.skip("full-size sweep is opt-in (FDETD_FULL_SWEEP=1)", allow_module_level=True)
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
@@ -26,7 +26,10 @@ if not torch.cuda.is_available():
 import paper_2605_12132_gb300 as fd  # noqa: E402
 
 REF = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_8192x512_ref.npz")
-BOUND = {"fp32": [1e-5, 1.5e-4, 2e-3], "bf16x6": [1e-5, 2.5e-3, 2.5e-2], "bf16x3": [3e-4, 1.2e-2, 1.2e-1]}
+# (strong, weak) per step count 1, 100, 1000
+BOUND = {"fp32": [(1e-6, 6e-5), (1.5e-5, 3e-5), (1.5e-4, 1.5e-4)],
+         "bf16x6": [(3e-6, 3e-5), (5e-4, 5e-4), (4e-3, 4e-3)],
+         "bf16x3": [(3e-5, 1e-3), (1.5e-3, 1.5e-3), (1.2e-2, 1.2e-2)]}
 W = inputs.workload("sweep_m012_8192x512")
 
 
@@ -37,38 +40,25 @@ def case():
     return F, J, d["ref"], list(d["counts"]), list(d["qs"])
 
 
-def _errors(G, ref, qs):
-    """per-field error on the sampled columns, fields under 10% of the state measured against 10% of it"""
-    Gh = np.fft.fft(G, axis=1)
-    err = np.zeros(6)
-    tot = np.sqrt(sum(np.linalg.norm(ref[k]) ** 2 for k in range(len(qs))))
-    for f in range(6):
-        num = np.sqrt(sum(np.linalg.norm(mx.gather_field(Gh[:, q, :], f) - mx.gather_field(ref[k], f)) ** 2
-                          for k, q in enumerate(qs)))
-        den = np.sqrt(sum(np.linalg.norm(mx.gather_field(ref[k], f)) ** 2 for k in range(len(qs))))
-        err[f] = num / max(den, 0.1 * tot)
-    return err
-
-
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x6", "fp32", "bf16x3"])
 def test_sweep_8192x512(prec, case):
     F, J, ref, counts, qs = case
     plan = fd.fdetd_plan_modes(W.Nz, W.Nr, W.modes, W.order, W.dz, W.dr, W.dt, precision=prec)
     f = torch.from_numpy(F).to(plan.complex_dtype).cuda()
     j = torch.from_numpy(J).to(plan.complex_dtype).cuda()
     done = 0
-    rows = []
+    failures = []
     for ci, n in enumerate(counts):
         fd.fdetd_step(plan, f, j, int(n) - done)
         done = int(n)
         plan.status()
-        G = f.cpu().numpy()
+        G = kz_columns(f.cpu().numpy().astype(np.complex128), qs)      # [modes][6][nq][Nr]
         for i, m in enumerate(W.modes):
-            e = _errors(G[i].astype(np.complex128), ref[ci, i], qs)
-            rows.append((n, m, e))
-    print(f"\n{prec}: steps, mode, per-field error (Er, Et, Ez, Br, Bt, Bz)")
-    for n, m, e in rows:
-        print(f"  {prec} {n:5d} m={m} " + " ".join(f"{x:.2e}" for x in e))
-    for ci, n in enumerate(counts):
-        worst = max(e.max() for nn, _, e in rows if nn == n)
-        assert worst < BOUND[prec][ci], (prec, n, worst)
+            rows = column_report([G[i][:, k, :] for k in range(len(qs))], list(ref[ci, i]))
+            label = f"{prec} {int(n):5d} steps m={m}"
+            print("\n" + format_report(rows, label))
+            try:
+                check_report(rows, *BOUND[prec][ci], label=label)
+            except AssertionError as e:
+                failures.append(str(e))
+    assert not failures, "\n".join(failures)

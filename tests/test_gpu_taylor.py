@@ -8,7 +8,7 @@ import pytest
 
 from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
-from tests.gpu_util import field_errors, zero_axis
+from tests.gpu_util import check_report, field_report, format_report, zero_axis
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,8 @@ def test_taylor_parity_small_ragged(N, S):
     got = _run(F, J, Nz, Nr, modes, order, dz, dr, dt, N, S, nsteps)
     for i, m in enumerate(modes):
         ref = mx.step_taylor(F[i], J[i], Nz, Nr, m, order, dz, dr, dt, nsteps=nsteps, taylor_order=N, substeps=S)
-        err = field_errors(got[i], ref, 0.1)
-        assert err.max() < TOL_PER_STEP * nsteps, (m, err)
+        rows = field_report(got[i], ref, nd=order // 2)
+        check_report(rows, TOL_PER_STEP * nsteps, TOL_PER_STEP * nsteps, label=f"N={N} S={S} m={m}")
 
 
 def test_taylor_no_current_and_zero_steps():
@@ -57,21 +57,25 @@ def test_taylor_no_current_and_zero_steps():
     fd.fdetd_taylor_step(plan, f, None, 2)
     torch.cuda.synchronize()
     ref = mx.step_taylor(F[0], None, Nz, Nr, 1, 4, 1 / 16, 1 / 4, 1 / 64, nsteps=2, taylor_order=4, substeps=1)
-    err = field_errors(f.cpu().numpy()[0].astype(np.complex128), ref, 0.1)
-    assert err.max() < TOL_PER_STEP * 2, err
+    rows = field_report(f.cpu().numpy()[0].astype(np.complex128), ref, nd=2)
+    check_report(rows, TOL_PER_STEP * 2, TOL_PER_STEP * 2, label="no current")
 
 
 def test_taylor_converges_to_the_exact_step():
-    # vacuum pulse, m = 1: the Taylor truncation error falls with the number of terms
+    # vacuum pulse, m = 1: the Taylor truncation error of every field falls with the number of terms
     w = inputs.workload("vacuum_m1_256x64")
     F, _ = inputs.workload_inputs(w)
     exact = mx.step_spectral(F[0], None, w.Nz, w.Nr, 1, w.order, w.dz, w.dr, w.dt, nsteps=1)
     errs = []
     for N in (2, 4, 8):
         got = _run(F, None, w.Nz, w.Nr, [1], w.order, w.dz, w.dr, w.dt, N, 4, 1)
-        errs.append(field_errors(got[0], exact, 0.1).max())
-    assert errs[0] > errs[1] > errs[2], errs
-    assert errs[2] < 1e-5, errs
+        rows = field_report(got[0], exact)
+        print(format_report(rows, f"N={N}"))
+        errs.append(np.array([r["l2"] for r in rows]))
+    assert np.all(errs[0] > errs[1]) and np.all(errs[1] > errs[2]), errs
+    # N = 8 with 4 substeps: the truncation is below the FP32 rounding of the strong fields; E_z and B_z
+    # (0.8% of the state) carry the state-scale FP32 error
+    assert errs[2].max() < 2e-5, errs
 
 
 def test_taylor_argument_errors():
