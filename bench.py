@@ -1,14 +1,17 @@
 """Throughput benchmark of the exact exponential field step (cell*mode*steps/s).
 
-Default workload: the current-driven 2048 x 256 case (modes 0 and 1, order 16,
-seeded Gaussian pulse on m = 1 plus a seeded smooth random current on both
-modes), one real-space round trip per step (projection, z transform + exact
-rotation with the current, inverse transform, back-projection), inputs resident
-in HBM, L2 flushed (a 256 MiB write) between timed steps.
+Default line: the uneven-instance batch - 64 seeded simulations (Nz from {512, 1024, 2048, 4096}, Nr in
+[64, 512], M in {1, 2, 3}, order 8 or 16, m = 1 pulse with waist 10-40 dr, seeded smooth current on every
+mode) advanced together by one captured CUDA graph per step (one persistent grouped projection launch, every
+instance's spectral kernel on its own branch, one grouped back-projection launch), split-BF16 (BF16x6, FP32
+accumulation), against the plain FP64 path on the same mix, with the per-field error of one step against
+that FP64 step, the per-step latency percentiles, the stage roofline, the host-buffer end-to-end rate and
+two single-instance legs (the 2048 x 256 two-mode and the 8192 x 512 three-mode workloads).  Inputs (8 GB
+resident) are far larger than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16x6|fp32|fp64]
-    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
-    python bench.py --mode batch ...       # 64 seeded uneven instances under one captured CUDA graph
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, same mix
+    python bench.py --mode step ...        # one instance (--workload), L2 flushed between steps
     python bench.py --mode serve ...       # Poisson request stream through the continuous-batching server
 
 N > 1 (torchrun, one process per GPU) runs independent replicas: the step has no
@@ -28,8 +31,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "cell*mode*steps/s (exact exponential field step, one real-space round trip per step)"
+METRIC = "cell\u00b7mode\u00b7steps/s split-BF16 batched vs plain FP64 at \u22641e-6 rel err; p50/p99 latency"
+STEP_METRIC = "cell*mode*steps/s (exact exponential field step, one real-space round trip per step)"
 UNIT = "cell*mode*steps/s"
+BATCH_WORKLOAD = "uneven_mix_64: 64 seeded instances, Nz in {512,1024,2048,4096}, Nr in [64,512], M in {1,2,3}, " \
+                 "order 8/16, 100-step batches advanced one step per graph replay"
 
 
 def _peaks():
@@ -136,12 +142,13 @@ def spectral_bytes(w, hasJ, elt):
     return ((9 if hasJ else 6) + 6) * w.Nz * w.Nr * len(w.modes) * elt
 
 
-def cpu_oracle_rate(w, F, J, kz_count):
-    """The FP64 oracle (per-kz dense eigendecomposition evaluator) on a bounded sample of kz columns."""
+def cpu_oracle_rate(w, F, J, kz_count, mode_index=None, seed=123):
+    """The FP64 oracle (per-kz dense eigendecomposition evaluator) on a bounded sample of kz columns of one
+    mode of workload w (an object with Nz, Nr, modes, order, dz, dr, dt)."""
     from oracle import maxwell as mx
-    rng = np.random.default_rng(123)
+    rng = np.random.default_rng(seed)
     qs = list(rng.choice(w.Nz, size=kz_count, replace=False))
-    m_i = len(w.modes) - 1
+    m_i = len(w.modes) - 1 if mode_index is None else mode_index
     t0 = time.perf_counter()
     mx.step_spectral(F[m_i], None if J is None else J[m_i], w.Nz, w.Nr, w.modes[m_i], w.order, w.dz, w.dr, w.dt,
                      nsteps=1, kz_subset=qs, method="eig")
@@ -149,113 +156,264 @@ def cpu_oracle_rate(w, F, J, kz_count):
     return kz_count * w.Nr / dt, dt
 
 
-def run_reference(args, w, rank, world):
-    """--impl reference: the oracle as it stands, on the host cores (rank 0 only)."""
+class _Inst:
+    """One instance of the uneven mix seen as a workload (sizes and spacings)."""
+
+    def __init__(self, c):
+        self.Nz, self.Nr, self.order = c["Nz"], c["Nr"], c["order"]
+        self.modes = list(range(c["M"] + 1))
+        self.dz, self.dr, self.dt = 1 / 16, 1 / 4, 1 / 16
+        self.name = f"mix instance Nz={self.Nz} Nr={self.Nr} M={c['M']} order={self.order}"
+
+
+def _oracle_sample(cfgs):
+    """The mix instance the CPU oracle samples: the one at the lower quartile of the radial sizes (a dense
+    (6 Nr - 3)^2 eigendecomposition per kz column keeps a step of the oracle to a few seconds)."""
+    from paper_2605_12132_gb300 import inputs
+    c = sorted(cfgs, key=lambda c: c["Nr"])[len(cfgs) // 4]
+    F, J = inputs.instance_inputs(c)
+    return _Inst(c), F, J
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle as it stands, on the host cores (rank 0 only), on the default line's
+    workload: per step one kz column of one mode of the lower-quartile-size instance of the uneven mix."""
     if rank != 0:
         return
     from paper_2605_12132_gb300 import inputs
-    F, J = inputs.workload_inputs(w)
-    kz_per_step = 1
-    for _ in range(args.warmup):
-        cpu_oracle_rate(w, F, J, kz_per_step)
+    cfgs = inputs.uneven_instances(args.instances, seed=0)
+    w, F, J = _oracle_sample(cfgs)
+    for k in range(args.warmup):
+        cpu_oracle_rate(w, F, J, 1, mode_index=1, seed=100 + k)
     tot, cells = 0.0, 0
-    for _ in range(args.steps):
-        r, dt = cpu_oracle_rate(w, F, J, kz_per_step)
+    for k in range(args.steps):
+        _, dt = cpu_oracle_rate(w, F, J, 1, mode_index=1, seed=200 + k)
         tot += dt
-        cells += kz_per_step * w.Nr
+        cells += w.Nr
     value = cells / tot
     cores = os.cpu_count()
+    sample = (f"one kz column ({w.Nr} cells) of mode 1 of the lower-quartile-size instance of the mix ({w.name}) per step, "
+              "per-kz dense eigendecomposition evaluator, FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded pulse + smooth random current)",
-            "config": {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order,
-                       "precision": "fp64-oracle", "l2": "cpu"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"one kz column ({w.Nr} cells) of mode {w.modes[-1]} per step, "
-                                       "per-kz dense eigendecomposition evaluator, FP64"},
+            "data": "synthetic (seeded uneven instances: Gaussian pulse + smooth random current)",
+            "config": {"workload": BATCH_WORKLOAD, "precision": "fp64-oracle", "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
 
 
-def uneven_instances(count, seed=0):
-    """The uneven-instance mix: Nz in {512, 1024, 2048, 4096} (powers of two: what the library's z transform takes),
-    even Nr in [64, 512], M in {1, 2, 3}, order 8 or 16, m = 1 pulse with waist 10-40 dr, seeded current."""
-    from paper_2605_12132_gb300 import inputs
-    rng = np.random.default_rng(seed)
-    out = []
-    for k in range(count):
-        Nz = int(rng.choice([512, 1024, 2048, 4096]))
-        Nr = 2 * int(rng.integers(32, 257))
-        M = int(rng.integers(1, 4))
-        order = int(rng.choice([8, 16]))
-        waist = float(rng.uniform(10, 40)) * 0.25
-        out.append(dict(Nz=Nz, Nr=Nr, M=M, order=order, waist=waist, seed=seed * 1000 + k))
-    return out
+def _field_error_stats(torch, got, ref):
+    """Largest relative L2 error per field (floor 1e-12 of the mode's norm) over the modes of one instance,
+    split into fields carrying at least 10% of their mode's state and the rest: (strong, weak)."""
+    d = got.to(torch.complex128) - ref
+    num = torch.linalg.vector_norm(d, dim=(2, 3))
+    den = torch.linalg.vector_norm(ref, dim=(2, 3))
+    tot = torch.linalg.vector_norm(ref, dim=(1, 2, 3))[:, None]
+    rel = num / torch.maximum(den, 1e-12 * tot)
+    share = den / tot
+    strong = rel[share >= 0.1]
+    weak = rel[share < 0.1]
+    return (float(strong.max()) if strong.numel() else 0.0, float(weak.max()) if weak.numel() else 0.0)
 
 
-def _instance_arrays(c):
-    from paper_2605_12132_gb300 import inputs
-    Nz, Nr, M = c["Nz"], c["Nr"], c["M"]
-    F = np.zeros((M + 1, 6, Nz, Nr), np.complex64)
-    F[1] = inputs.pulse_fields(Nz, Nr, 1 / 16, 1 / 4, c["waist"], 8.0)
-    for f in (0, 4, 5):
-        F[:, f, :, 0] = 0
-    J = np.stack([inputs.random_current(Nz, Nr, m, 8.0, 1e-2, c["seed"]) for m in range(M + 1)]).astype(np.complex64)
-    return F, J
-
-
-def run_batch(args):
-    """Uneven instances advanced by one captured CUDA graph; value = total cell*mode*steps/s."""
+def _build_plans(fd, cfgs, prec):
     import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        return list(ex.map(lambda c: fd.fdetd_plan(c["Nz"], c["Nr"], c["M"], c["order"], 1 / 16, 1 / 4, 1 / 16,
+                                                    precision=prec), cfgs))
+
+
+def batch_gemm_flops(cfgs, hasJ=True):
+    """Algorithmic FLOPs of one step's radial transforms over the mix (the survey's count: per cell and
+    mode, 9 products of a real Nr x Nr matrix with a complex column forward including the current, 6 back,
+    4 Nr flops each), and the dense-equivalent count the tensor-core kernels execute per bf16 product
+    (15 / 10 nonzero Nr x Nr blocks of the folded projection / back-projection matrices)."""
+    fa = ba = fe = be = 0.0
+    for c in cfgs:
+        cm = c["Nz"] * c["Nr"] * (c["M"] + 1)
+        fa += (9 if hasJ else 6) * 4.0 * c["Nr"] * cm
+        ba += 6 * 4.0 * c["Nr"] * cm
+        fe += (15 if hasJ else 10) * 4.0 * c["Nr"] * cm
+        be += 10 * 4.0 * c["Nr"] * cm
+    return fa, ba, fe, be
+
+
+def run_batch(args, rank, world, dist):
+    """The default line: the uneven mix advanced by one captured graph per step."""
     import torch
     import paper_2605_12132_gb300 as fd
-    prec = args.precision or "bf16x3"
-    cfgs = uneven_instances(args.instances)
+    from paper_2605_12132_gb300 import inputs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prec = args.precision or "bf16x6"
+    cfgs = inputs.uneven_instances(args.instances, seed=0)
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
-        plans = list(ex.map(lambda c: fd.fdetd_plan(c["Nz"], c["Nr"], c["M"], c["order"], 1 / 16, 1 / 4, 1 / 16,
-                                                     precision=prec), cfgs))
+    plans = _build_plans(fd, cfgs, prec)
     plan_s = time.perf_counter() - t0
-    batch = fd.FdetdBatch()
-    keep = []
+    host, dev = [], []
     cells = 0
     for c, p in zip(cfgs, plans):
-        F, J = _instance_arrays(c)
-        f, j = torch.from_numpy(F).cuda(), torch.from_numpy(J).cuda()
-        keep.append((f, j))
-        batch.add(p, f, j)
+        F, J = inputs.instance_inputs(c)
+        host.append((F, J))
+        dev.append((torch.from_numpy(F).to(p.complex_dtype).cuda(), torch.from_numpy(J).to(p.complex_dtype).cuda()))
         cells += c["Nz"] * c["Nr"] * (c["M"] + 1)
+    batch = fd.FdetdBatch()
+    for p, (f, j) in zip(plans, dev):
+        batch.add(p, f, j)
+    batch.set_profiling(True)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     batch.capture(1)
     capture_s = time.perf_counter() - t0
     groups = batch.groups()
-    for _ in range(max(args.warmup, 3)):
-        batch.launch()
+    # one step from the initial state, kept for the accuracy check against the FP64 path
+    batch.launch()
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(args.steps):
+    one_step = [f.clone() for f, _ in dev]
+    for _ in range(args.warmup - 1):
         batch.launch()
-    b.record(stream)
-    torch.cuda.synchronize()
+    barrier()
+    # timed region: K graph replays, each bracketed by events on the launching stream
+    clocks = ClockSampler()
+    clocks.start()
+    batch.set_profiling(True) if False else None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        batch.launch()
+        evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        batch.collect_stage_times()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
     for p in plans:
         p.status()
-    ms = a.elapsed_time(b)
-    line = {"metric": METRIC + " [uneven instances, one CUDA graph]", "value": cells * args.steps / (ms / 1e3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": prec + "-split/f32-accumulate" if prec.startswith("bf16") else prec,
-            "data": "synthetic (seeded uneven instances)",
-            "config": {"workload": f"{len(cfgs)} uneven instances", "cells_modes": cells, "precision": prec,
-                       "plan_build_s": plan_s, "capture_s": capture_s,
-                       "graph": "per step: one persistent grouped projection and back-projection launch per "
-                                "precision group, per-instance spectral kernels on parallel branches; replayed",
-                       "groups": [{k: g[k] for k in ("instances", "tn_proj", "tn_back", "sched_proj", "sched_back",
-                                                     "proj_tiles", "back_tiles", "tuned_ms")} for g in groups]}}
-    print(json.dumps(line), flush=True)
+    lat = np.array([a.elapsed_time(b) for a, b in evs])
+    ms = max_over_ranks(float(lat.sum()), dist, "cuda")
+    value = replica_rate(cells * args.steps, ms / 1e3, world)
+    st = batch.stage_times()
+
+    # plain FP64 path on the same mix: its one-step result is the accuracy reference, its rate the baseline
+    fp64_value = err = None
+    if not args.no_fp64 and prec != "fp64":
+        plans64 = _build_plans(fd, cfgs, "fp64")
+        dev64 = [(torch.from_numpy(F).cuda(), torch.from_numpy(J).cuda()) for F, J in host]
+        b64 = fd.FdetdBatch()
+        for p, (f, j) in zip(plans64, dev64):
+            b64.add(p, f, j)
+        b64.capture(1)
+        b64.launch()
+        torch.cuda.synchronize()
+        strong = weak = 0.0
+        for g, (r, _) in zip(one_step, dev64):
+            s_, w_ = _field_error_stats(torch, g, r)
+            strong, weak = max(strong, s_), max(weak, w_)
+        err = {"strong_fields_max": strong, "weak_fields_max": weak,
+               "definition": "one step from the same state, per mode and field ||X - X_fp64|| / ||X_fp64|| (floor "
+                             "1e-12 of the mode's norm), largest over the 64 instances; strong = fields with at least "
+                             "10% of their mode's norm"}
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b64.launch()
+        b.record(stream)
+        torch.cuda.synchronize()
+        for p in plans64:
+            p.status()
+        fp64_value = cells / (a.elapsed_time(b) / 1e3)
+        b64.close()
+        for p in plans64:
+            p.close()
+        del dev64, plans64
+        torch.cuda.empty_cache()
+
+    # end to end through the host-buffer form of the batch: every step copies every instance's fields and
+    # current in from pinned host memory and the fields back out
+    hf = [torch.from_numpy(F).to(torch.complex64).pin_memory() for F, _ in host]
+    hj = [torch.from_numpy(J).to(torch.complex64).pin_memory() for _, J in host]
+    batch.step_host(hf, hj, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        batch.step_host(hf, hj, 1)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    h2d = sum(t.numel() * t.element_size() for t in hf) + sum(t.numel() * t.element_size() for t in hj)
+    d2h = sum(t.numel() * t.element_size() for t in hf)
+    e2e_val = replica_rate(cells * args.e2e_steps, e2e_s, world)
+
+    # roofline of the dominant stage, from the stage times recorded inside the timed graph replays
+    peaks, src = _peaks()
+    fa, ba, fe, be = batch_gemm_flops(cfgs)
+    products = {"bf16x3": 3, "bf16x6": 6}.get(prec, 1)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in st.items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    tsec = stage_ms[dom] / 1e3
+    if dom == "spectral":
+        algo = sum(15 * c["Nz"] * c["Nr"] * (c["M"] + 1) * 8 for c in cfgs)
+        roof = {"bound": "hbm", "achieved": algo / tsec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        algo, execd = (fa, fe) if dom == "projection" else (ba, be)
+        pk = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": algo * products / tsec / 1e12, "peak": pk, "unit": "TFLOP/s",
+                "executed_tflops": execd * products / tsec / 1e12, "executed_frac": execd * products / tsec / 1e12 / pk,
+                "note": f"achieved = the survey's algorithmic flops x {products} bf16 products per FP32-accurate "
+                        "product; executed = the folded dense blocks the kernel multiplies"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["algorithmic"] = algo
+    roof["kernel"] = {"projection": "tcg_project_kernel (grouped, persistent)", "spectral": "spectral32_kernel",
+                      "backprojection": "tcg_backproject_kernel (grouped, persistent)"}[dom]
+    roof["peak_source"] = src
+    roof["stage_ms_per_step"] = stage_ms
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        w, F, J = _oracle_sample(cfgs)
+        rate, secs = cpu_oracle_rate(w, F, J, 2, mode_index=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"2 kz columns ({2 * w.Nr} cells) of mode 1 of the lower-quartile-size instance ({w.name}), one "
+                         f"step, per-kz dense eigendecomposition evaluator, FP64 ({secs:.1f} s)"}
+
+    legs = {}
+    if not args.no_legs:
+        for name in ("lwfa_m01_2048x256", "sweep_m012_8192x512"):
+            legs[name] = run_step(args, inputs.workload(name), prec, leg=True)
+
+    if rank == 0:
+        launches_per_step = 2 * len(groups) + len(cfgs)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": prec + "-split/f32-accumulate" if prec.startswith("bf16") else prec,
+                "data": "synthetic (seeded uneven instances: Gaussian pulse + smooth random current)",
+                "config": {"workload": BATCH_WORKLOAD, "instances": len(cfgs), "cells_modes": cells,
+                           "precision": prec, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": f"inputs larger than L2 ({sum(f.numel() * f.element_size() + j.numel() * j.element_size() for f, j in dev) / 1e9:.1f} GB resident)",
+                           "fp64_value": fp64_value, "speedup_vs_fp64": value / world / fp64_value if fp64_value else None,
+                           "rel_err_vs_fp64_1step": err, "plan_build_s": plan_s, "capture_s": capture_s,
+                           "wall_s": t_wall,
+                           "graph": "per step: one persistent grouped projection launch, every instance's spectral "
+                                    "kernel on its own branch, one grouped back-projection launch",
+                           "groups": [{k: g[k] for k in ("instances", "tn_proj", "tn_back", "sched_proj",
+                                                         "sched_back", "proj_tiles", "back_tiles", "tuned_ms")}
+                                      for g in groups],
+                           "legs": legs},
+                "latency": {"unit": "ms per step (one graph replay)", "p50": float(np.percentile(lat, 50)),
+                            "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "api": "fdetd_batch_step_host"},
+                "gpu_launches": launches_per_step * args.steps, "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
 
 
 def run_taylor(args, w):
@@ -439,14 +597,14 @@ def run_serve(args):
     import torch
     from paper_2605_12132_gb300 import inputs, serve
     prec = args.precision or "bf16x3"
-    cfgs = uneven_instances(2000, seed=5)
+    cfgs = inputs.uneven_instances(2000, seed=5)
     ew = inputs.envelope_workload("envelope_4096x256")
     ea, eat, echi = inputs.envelope_inputs(ew)
 
     def make(i, rng):
         if rng.random() < 0.5:
             c = cfgs[i % len(cfgs)]
-            F, J = _instance_arrays(c)
+            F, J = inputs.instance_inputs(c)
             return serve.FieldRequest(c["Nz"], c["Nr"], list(range(c["M"] + 1)), c["order"], 1 / 16, 1 / 4, 1 / 16,
                                       int(rng.integers(10, 501)), F, J, prec)
         return serve.EnvelopeRequest(ew.Nz, ew.Nr, ew.order, ew.taylor_order, ew.dz, ew.dr, ew.dt,
@@ -473,6 +631,152 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_step(args, w, prec, leg=False, dist=None, rank=0, world=1):
+    """One instance of workload w stepped through fdetd_step, L2 flushed between timed steps.  As a leg of
+    the default line it returns a summary dict; with --mode step it prints the full line."""
+    import torch
+    import paper_2605_12132_gb300 as fd
+    from paper_2605_12132_gb300 import inputs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    F, J = inputs.workload_inputs(w)
+    plan = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision=prec)
+    cdt = plan.complex_dtype
+    fields = torch.from_numpy(F).to(cdt).cuda()
+    Jd = torch.from_numpy(J).to(cdt).cuda() if J is not None else None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    tiles = tuned = None
+    if prec in ("bf16x3", "bf16x6"):
+        tuned = plan.autotune(fields, Jd)       # tile shapes / schedules, timed on these arrays (read only)
+        tiles = dict(zip(("tn_proj", "tn_back", "sched_proj", "sched_back"), plan.tile_config))
+    # one step from the initial state for the accuracy check, then the warm-up steps
+    fd.fdetd_step(plan, fields, Jd, 1)
+    torch.cuda.synchronize()
+    one_step = fields.clone()
+    for _ in range(args.warmup - 1):
+        fd.fdetd_step(plan, fields, Jd, 1)
+    barrier()
+    steps = args.steps if not leg else min(args.steps, 10)
+    clocks = ClockSampler()
+    if not leg:
+        clocks.start()
+    plan.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        fd.fdetd_step(plan, fields, Jd, 1)
+        evs[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = None if leg else clocks.stop()
+    ktimes = plan.kernel_times()
+    plan.set_profiling(False)
+    plan.status()
+    lat = np.array([a.elapsed_time(b) for a, b in evs])
+    ms = max_over_ranks(float(lat.sum()), dist, "cuda")
+    cells = w.Nz * w.Nr * len(w.modes)
+    value = replica_rate(cells * steps, ms / 1e3, world)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in ktimes.items()}
+
+    # FP64 single-instance path on the same workload (where its z transform reaches: Nz <= 4096)
+    fp64_value = err = None
+    if not args.no_fp64 and prec != "fp64" and w.Nz <= 4096:
+        p64 = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision="fp64")
+        f64 = torch.from_numpy(F).cuda()
+        J64 = torch.from_numpy(J).cuda() if J is not None else None
+        fd.fdetd_step(p64, f64, J64, 1)
+        barrier()
+        strong, weak = _field_error_stats(torch, one_step, f64)
+        err = {"strong_fields_max": strong, "weak_fields_max": weak}
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = 2
+        a.record(stream)
+        fd.fdetd_step(p64, f64, J64, n64)
+        b.record(stream)
+        barrier()
+        fp64_value = cells * n64 / (a.elapsed_time(b) / 1e3)
+        p64.close()
+        del f64, J64
+
+    summary = {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order, "precision": prec,
+               "steps": steps, "ms_per_step": ms / steps, "value": value, "stage_ms_per_step": stage_ms,
+               "fp64_value": fp64_value, "rel_err_vs_fp64_1step": err, "tiles": tiles,
+               "l2": "flushed between timed steps (256 MiB write)"}
+    launches = plan.launches_per_step * steps
+    plan.close()
+    if leg:
+        return summary
+
+    # end-to-end through the host entry point: h2d of fields + J, the step, d2h of the fields
+    plan = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision=prec)
+    hf = torch.from_numpy(F).to(cdt).pin_memory()
+    hJ = torch.from_numpy(J).to(cdt).pin_memory() if J is not None else None
+    fd.fdetd_step_host(plan, hf, hJ, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        fd.fdetd_step_host(plan, hf, hJ, 1)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    elt = hf.element_size()
+    h2d = hf.numel() * elt + (hJ.numel() * elt if hJ is not None else 0)
+    d2h = hf.numel() * elt
+    e2e_val = replica_rate(cells * args.e2e_steps, e2e_s, world)
+    plan.close()
+
+    peaks, src = _peaks()
+    hasJ = J is not None
+    fwd_flops, bwd_flops = gemm_flops(w, hasJ)
+    elt_c = 16 if prec == "fp64" else 8
+    dom = max(stage_ms, key=stage_ms.get)
+    per_launch_s = stage_ms[dom] / 1e3
+    products = {"bf16x3": 3, "bf16x6": 6}.get(prec, 1)
+    if dom == "spectral":
+        algo = spectral_bytes(w, hasJ, elt_c)
+        roof = {"bound": "hbm", "achieved": algo / per_launch_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        algo = fwd_flops if dom == "projection" else bwd_flops
+        if prec in ("bf16x3", "bf16x6"):
+            roof = {"bound": "tensor", "achieved": algo * products / per_launch_s / 1e12,
+                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        else:
+            # CUDA-core FMA peak: 152 SMs x 128 FP32 lanes (FP64: nominal 1.25 TFLOP/s) x 2 flops x max clock
+            pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if prec == "fp32" else 1.25
+            roof = {"bound": "alu", "achieved": algo / per_launch_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = recorded_traffic(dom, w.name, prec)
+    roof["algorithmic"] = algo
+    roof["kernel"] = dom
+    roof["peak_source"] = src
+    roof["stage_ms_per_step"] = stage_ms
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs = cpu_oracle_rate(w, F, J, 4)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"4 kz columns ({4 * w.Nr} cells) of mode {w.modes[-1]}, one step, per-kz dense "
+                         f"eigendecomposition evaluator, FP64 ({secs:.1f} s)"}
+    if rank == 0:
+        summary.update({"parallelism": "replicas" if world > 1 else "single", "wall_s": t_wall, "autotune_ms": tuned})
+        line = {"metric": STEP_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec + "-split/f32-accumulate"),
+                "data": "synthetic (seeded Gaussian pulse + seeded smooth random current)", "config": summary,
+                "latency": {"unit": "ms per step", "p50": float(np.percentile(lat, 50)),
+                            "p99": float(np.percentile(lat, 99))},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,8 +787,10 @@ def main():
     ap.add_argument("--workload", default="lwfa_m01_2048x256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "taylor", "destagger", "envelope", "current"])
+    ap.add_argument("--no-legs", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--mode", default="batch",
+                    choices=["batch", "step", "serve", "taylor", "destagger", "envelope", "current"])
     ap.add_argument("--taylor-order", type=int, default=4)
     ap.add_argument("--substeps", type=int, default=1)
     ap.add_argument("--instances", type=int, default=64)
@@ -500,9 +806,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        return run_reference(args, w, rank, world)
-    if args.mode == "batch":
-        return run_batch(args)
+        return run_reference(args, rank, world)
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "taylor":
@@ -521,150 +825,17 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    prec = args.precision
-    if prec is None:
-        # the split-BF16 precision that stays within 1e-6 relative per step (BF16x3: ~1e-5)
-        prec = "bf16x6"
+    if args.precision is None:
+        # the split-BF16 precision that stays within 1e-6 relative per step on the strong fields (BF16x3: ~1e-5)
+        args.precision = "bf16x6"
         try:
             fd.fdetd_plan_modes(64, 16, [0], 4, 0.1, 0.1, 0.1, precision="bf16x6").close()
         except fd.FdetdError:
-            prec = "fp32"
-
-    F, J = inputs.workload_inputs(w)
-    plan = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision=prec)
-    cdt = plan.complex_dtype
-    fields = torch.from_numpy(F).to(cdt).cuda()
-    Jd = torch.from_numpy(J).to(cdt).cuda() if J is not None else None
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-    tiles = tuned = None
-    if prec in ("bf16x3", "bf16x6"):
-        tuned = plan.autotune(fields, Jd)       # tile shapes / schedules, timed on these arrays (read only)
-        tiles = dict(zip(("tn_proj", "tn_back", "sched_proj", "sched_back"), plan.tile_config))
-
-    for _ in range(args.warmup):
-        fd.fdetd_step(plan, fields, Jd, 1)
-    barrier()
-    clocks = ClockSampler()
-    clocks.start()
-    plan.set_profiling(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        fd.fdetd_step(plan, fields, Jd, 1)
-        evs[k][1].record(stream)
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    ktimes = plan.kernel_times()
-    plan.set_profiling(False)
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
-    cells = w.Nz * w.Nr * len(w.modes)
-    value = replica_rate(cells * args.steps, ms / 1e3, world)
-
-    # end-to-end through the host entry point: h2d of fields + J, the step, d2h of the fields
-    hf = torch.from_numpy(F).to(cdt).pin_memory()
-    hJ = torch.from_numpy(J).to(cdt).pin_memory() if J is not None else None
-    fd.fdetd_step_host(plan, hf, hJ, 1)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        fd.fdetd_step_host(plan, hf, hJ, 1)
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    elt = hf.element_size()
-    h2d = hf.numel() * elt + (hJ.numel() * elt if hJ is not None else 0)
-    d2h = hf.numel() * elt
-    e2e_val = replica_rate(cells * args.e2e_steps, e2e_s, world)
-
-    # FP64 single-instance path on the same workload (the plain baseline the split path must beat)
-    fp64_value = rel_err = None
-    if not args.no_fp64 and prec != "fp64":
-        p64 = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision="fp64")
-        f64 = torch.from_numpy(F).cuda()
-        J64 = torch.from_numpy(J).cuda() if J is not None else None
-        fd.fdetd_step(p64, f64, J64, 1)
-        barrier()
-        # accuracy of one step of the timed precision against the FP64 path from the same state
-        # (per mode and field, relative L2 with a floor of 0.1 of the mode's norm)
-        fx = torch.from_numpy(F).to(cdt).cuda()
-        fd.fdetd_step(plan, fx, Jd, 1)
-        barrier()
-        a_np, b_np = fx.cpu().numpy().astype(np.complex128), f64.cpu().numpy()
-        rel_err = max(float(np.linalg.norm(a_np[i, c] - b_np[i, c]) /
-                            max(np.linalg.norm(b_np[i, c]), 0.1 * np.linalg.norm(b_np[i])))
-                      for i in range(len(w.modes)) for c in range(6))
-        del fx
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n64 = 2
-        a.record(stream)
-        fd.fdetd_step(p64, f64, J64, n64)
-        b.record(stream)
-        barrier()
-        fp64_value = cells * n64 / (a.elapsed_time(b) / 1e3)
-        p64.close()
-        del f64, J64
-
-    # roofline of the dominant stage
-    peaks, src = _peaks()
-    hasJ = J is not None
-    fwd_flops, bwd_flops = gemm_flops(w, hasJ)
-    elt_c = 16 if prec == "fp64" else 8
-    stage = max(ktimes, key=lambda k: ktimes[k][0])
-    tms, calls = ktimes[stage]
-    per_launch_s = tms / 1e3 / max(calls, 1)
-    products = {"bf16x3": 3, "bf16x6": 6}.get(prec, 1)
-    if stage == "spectral":
-        algo = spectral_bytes(w, hasJ, elt_c)
-        roof = {"bound": "hbm", "achieved": algo / per_launch_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+            args.precision = "fp32"
+    if args.mode == "batch":
+        run_batch(args, rank, world, dist)
     else:
-        algo = fwd_flops if stage == "projection" else bwd_flops
-        if prec in ("bf16x3", "bf16x6"):
-            roof = {"bound": "tensor", "achieved": algo * products / per_launch_s / 1e12,
-                    "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
-        else:
-            # CUDA-core FMA peak: 152 SMs x 128 FP32 lanes (FP64: nominal 1.25 TFLOP/s) x 2 flops x max clock
-            pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if prec == "fp32" else 1.25
-            roof = {"bound": "alu", "achieved": algo / per_launch_s / 1e12, "peak": pk, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = recorded_traffic(stage, w.name, prec)
-    roof["algorithmic"] = algo
-    roof["kernel"] = stage
-    roof["peak_source"] = src
-    roof["stage_ms_per_step"] = {k: v[0] / max(v[1], 1) for k, v in ktimes.items()}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        kz = 4
-        rate, secs = cpu_oracle_rate(w, F, J, kz)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{kz} kz columns ({kz * w.Nr} cells) of mode {w.modes[-1]}, one step, per-kz dense "
-                         f"eigendecomposition evaluator, FP64 ({secs:.1f} s)"}
-
-    if rank == 0:
-        launches = plan.launches_per_step * args.steps
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None,
-                "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec + "-split/f32-accumulate"),
-                "data": "synthetic (seeded Gaussian pulse + seeded smooth random current)",
-                "config": {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order,
-                           "precision": prec, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "flushed between timed steps (256 MiB write)", "fp64_value": fp64_value,
-                           "wall_s": t_wall, "tiles": tiles, "autotune_ms": tuned,
-                           "rel_err_vs_fp64_1step": rel_err},
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
-        print(json.dumps(line), flush=True)
+        run_step(args, w, args.precision, dist=dist, rank=rank, world=world)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -255,6 +255,21 @@ int fdetd_taylor_host_bands(int Nr, int order, double dr, int m, double* bands, 
  * back-projection tile order, instances, projection tiles, back-projection tiles}, ms = the
  * tuned times per launch (0 when not tuned); returns the number of groups (0 if none; info
  * is left untouched when g is out of range), or -FDETD_ERR_ARG for a NULL batch or info.
+ *
+ * Stage timing: fdetd_batch_set_profiling(batch, 1) before fdetd_batch_capture records CUDA
+ * events into the graph around each captured step's grouped projections, the join of the
+ * spectral branches and the grouped back-projections (setting it drops the captured graph).
+ * After a replay has completed (the caller synchronizes), fdetd_batch_collect_stage_times
+ * adds that replay's three stage times to running sums, which fdetd_batch_stage_times copies
+ * to ms[3] (projection, spectral, back-projection, milliseconds) with the number of steps
+ * summed in *steps (may be NULL).
+ *
+ * fdetd_batch_step_host(batch, host_fields, host_J, nlaunch, stream): the batch with host
+ * buffers.  host_fields[k] / host_J[k] are instance k's fields and current in host memory, in
+ * the layouts of fdetd_step (pinned memory gives asynchronous copies); host_J may be NULL when
+ * no instance was added with a current.  Copies every instance's inputs to the registered device
+ * buffers, replays the graph nlaunch times, copies the fields back into host_fields, and
+ * synchronizes `stream` before returning.  FDETD_ERR_ARG for a missing graph or buffer.
  */
 int fdetd_batch_create(fdetd_batch_t* out);
 int fdetd_batch_add(fdetd_batch_t batch, fdetd_plan_t plan, void* fields, const void* J, int* index);
@@ -262,7 +277,94 @@ int fdetd_batch_set_autotune(fdetd_batch_t batch, int on);
 int fdetd_batch_capture(fdetd_batch_t batch, int nsteps, void* stream);
 int fdetd_batch_group_info(fdetd_batch_t batch, int group, int* info, double* ms);
 int fdetd_batch_launch(fdetd_batch_t batch, void* stream);
+int fdetd_batch_set_profiling(fdetd_batch_t batch, int on);
+int fdetd_batch_collect_stage_times(fdetd_batch_t batch);
+int fdetd_batch_stage_times(fdetd_batch_t batch, double* ms, long* steps);
+int fdetd_batch_step_host(fdetd_batch_t batch, void* const* host_fields, const void* const* host_J, int nlaunch,
+                          void* stream);
 int fdetd_batch_destroy(fdetd_batch_t batch);
+
+/*
+ * Continuous-batching request server (no counterpart in the paper).
+ *
+ * fdetd_server_create(out, hbm_budget_bytes, chunk_steps, plan_threads, flags) starts a server
+ * with one scheduler thread and plan_threads plan-builder threads on the calling thread's current
+ * device.  A submitted request is admitted first-come first-served as soon as its device
+ * footprint (fdetd_request_device_bytes) fits the budget next to the requests already admitted
+ * (later requests never overtake a waiting one); a request larger than the whole budget is
+ * refused at submission with FDETD_ERR_OOM.  Admitted requests get their plan built on a builder
+ * thread and their state copied to the device, then stay resident until they finish.  All ready
+ * field requests advance together as the instances of one batch (fdetd_batch_*: one CUDA graph per
+ * step with grouped tensor-core launches), re-captured whenever a request joins or leaves and
+ * replayed in chunks of at most chunk_steps steps, never past the end of the shortest request;
+ * envelope requests advance chunk by chunk on their own streams, overlapping with the field
+ * batch.  A finished request's result is copied to its host `out` buffer and its device memory
+ * returned to the budget.  flags: FDETD_SERVER_DRY_RUN makes no CUDA call at all (plans are
+ * only checked on the host, a chunk takes 0.1 ms of host time per step, no result is written):
+ * the scheduling can then be exercised on machines without a GPU.
+ *
+ * fdetd_server_submit(server, request, &ticket): the request is copied (its modes array too);
+ * the host buffers it points to (fields or the envelope state, J, chi, out) must stay valid
+ * until the ticket is done or failed.  Field request: fields/out = [nmodes][6][Nz][Nr] in the
+ * layout and complex type of fdetd_step, J = [nmodes][3][Nz][Nr] or NULL.  Envelope request:
+ * fields/out = [2][Nz][Nr] complex64 (a, a~), chi = [Nz][Nr] float.  out may be NULL (no copy
+ * back) or equal to fields.
+ * fdetd_server_poll(server, ticket, &state, &latency_s): state = FDETD_TICKET_*; latency_s =
+ * completion - submission time in seconds once done (else -1); returns the request's error
+ * code (with its message in fdetd_last_error) for a failed request.
+ * fdetd_server_wait(server, ticket, timeout_s, &latency_s): blocks until the ticket is done or
+ * failed, or FDETD_ERR_TIMEOUT after timeout_s.
+ * fdetd_server_ticket_times(server, ticket, times[3]): submission, admission and completion
+ * times (seconds on a monotonic clock; 0 where not reached yet).
+ * fdetd_server_stats(server, &stats): budget, bytes in use and their peak, request counts,
+ * graph re-captures, scheduling rounds, served cell*mode*steps.
+ * fdetd_server_destroy(server): stops accepting requests, finishes every request already
+ * submitted, then joins the threads and frees everything.
+ */
+enum { FDETD_REQUEST_FIELD = 0, FDETD_REQUEST_ENVELOPE = 1 };
+enum {
+  FDETD_TICKET_QUEUED = 0,   /* waiting for budget */
+  FDETD_TICKET_ADMITTED = 1, /* budget reserved, plan under construction */
+  FDETD_TICKET_RUNNING = 2,  /* resident on the device */
+  FDETD_TICKET_DONE = 3,
+  FDETD_TICKET_FAILED = 4
+};
+#define FDETD_SERVER_DRY_RUN 1ull
+
+typedef struct {
+  int kind;                 /* FDETD_REQUEST_FIELD or FDETD_REQUEST_ENVELOPE */
+  int Nz, Nr;
+  int nmodes;               /* field: number of modes in `modes` */
+  const int* modes;         /* field: the azimuthal modes */
+  int order;                /* finite-difference order */
+  int precision;            /* field: FDETD_PREC_* */
+  int taylor_order;         /* envelope: N_T */
+  int steps;                /* time steps to advance */
+  double dz, dr, dt, k0;    /* k0: envelope carrier wave number */
+  const void* fields;       /* host input state */
+  const void* J;            /* field: host current or NULL */
+  const float* chi;         /* envelope: host susceptibility */
+  void* out;                /* host result buffer or NULL */
+} fdetd_request;
+
+typedef struct {
+  size_t budget_bytes, used_bytes, peak_bytes;
+  size_t queued, building, running;
+  uint64_t completed, failed, recaptures, rounds;
+  double served_cell_steps;
+} fdetd_server_stats_t;
+
+typedef struct fdetd_server_s* fdetd_server_t;
+
+size_t fdetd_request_device_bytes(const fdetd_request* request);
+int fdetd_server_create(fdetd_server_t* out, size_t hbm_budget_bytes, int chunk_steps, int plan_threads,
+                        uint64_t flags);
+int fdetd_server_submit(fdetd_server_t server, const fdetd_request* request, uint64_t* ticket);
+int fdetd_server_poll(fdetd_server_t server, uint64_t ticket, int* state, double* latency_s);
+int fdetd_server_wait(fdetd_server_t server, uint64_t ticket, double timeout_s, double* latency_s);
+int fdetd_server_ticket_times(fdetd_server_t server, uint64_t ticket, double* times);
+int fdetd_server_stats(fdetd_server_t server, fdetd_server_stats_t* stats);
+int fdetd_server_destroy(fdetd_server_t server);
 
 /*
  * fdetd_host_tables - host-only (no GPU needed) export of the FP64 plan tables of
@@ -337,6 +439,7 @@ int envelope_step_static(void* a, const float* chi, int Nz, int Nr, int order, i
                          double dr, double dt, double k0, int nsteps, void* stream);
 
 /* Number of kernels one envelope step launches. */
+size_t envelope_plan_device_bytes(envelope_plan_t plan);  /* device bytes the plan holds */
 int envelope_plan_launches_per_step(envelope_plan_t plan);
 
 /*

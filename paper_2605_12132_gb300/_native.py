@@ -54,6 +54,8 @@ def lib():
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_step_absorbing.argtypes = [c_vp, c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_plan_launches_per_step.argtypes = [c_vp]
+    L.envelope_plan_device_bytes.argtypes = [c_vp]
+    L.envelope_plan_device_bytes.restype = ctypes.c_size_t
     L.fdetd_batch_create.argtypes = [ctypes.POINTER(c_vp)]
     L.fdetd_batch_add.argtypes = [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_int)]
     L.fdetd_batch_capture.argtypes = [c_vp, c_int, c_vp]
@@ -70,6 +72,10 @@ def lib():
     L.fdetd_taylor_destroy.argtypes = [c_vp]
     L.fdetd_taylor_host_bands.argtypes = [c_int, c_int, c_dbl, c_int, dp, dp]
     L.fdetd_batch_launch.argtypes = [c_vp, c_vp]
+    L.fdetd_batch_set_profiling.argtypes = [c_vp, c_int]
+    L.fdetd_batch_collect_stage_times.argtypes = [c_vp]
+    L.fdetd_batch_stage_times.argtypes = [c_vp, dp, ctypes.POINTER(ctypes.c_long)]
+    L.fdetd_batch_step_host.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
     L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
                                        c_vp]
@@ -361,6 +367,10 @@ class EnvelopePlan:
     def launches_per_step(self):
         return lib().envelope_plan_launches_per_step(self.handle)
 
+    @property
+    def device_bytes(self):
+        return lib().envelope_plan_device_bytes(self.handle)
+
     def close(self):
         if self.handle:
             lib().envelope_plan_destroy(self.handle)
@@ -463,6 +473,31 @@ class FdetdBatch:
 
     def launch(self, stream=None):
         _check(lib().fdetd_batch_launch(self.handle, _stream_handle(stream)))
+
+    def set_profiling(self, on=True):
+        """Record stage-timing events into the graph at the next capture (drops the captured graph)."""
+        _check(lib().fdetd_batch_set_profiling(self.handle, int(on)))
+
+    def collect_stage_times(self):
+        """Add the last completed replay's stage times to the running sums (caller synchronizes first)."""
+        _check(lib().fdetd_batch_collect_stage_times(self.handle))
+
+    def stage_times(self):
+        """{'projection', 'spectral', 'backprojection'}: (summed ms, steps summed)."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_long(0)
+        _check(lib().fdetd_batch_stage_times(self.handle, ms, ctypes.byref(n)))
+        return {k: (ms[i], n.value) for i, k in enumerate(("projection", "spectral", "backprojection"))}
+
+    def step_host(self, host_fields, host_J=None, nlaunch=1, stream=None):
+        """Host-buffer form: copy every instance's fields (and J) in, replay the graph nlaunch times, copy the
+        fields back into host_fields; host tensors in instance order (pinned for asynchronous copies)."""
+        n = len(host_fields)
+        hf = (ctypes.c_void_p * n)(*[t.data_ptr() for t in host_fields])
+        hj = None
+        if host_J is not None:
+            hj = (ctypes.c_void_p * n)(*[None if t is None else t.data_ptr() for t in host_J])
+        _check(lib().fdetd_batch_step_host(self.handle, hf, hj, nlaunch, _stream_handle(stream)))
 
     def close(self):
         if self.handle:

@@ -48,6 +48,8 @@ struct PhaseF { df A1, A2; };  // B1, B2 follow from A1, A2 (half-angle identiti
 // z symbol per q: s+ = i kappa e^{+i th/2} (complex); s- = i kappa e^{-i th/2} = (-Re s+, Im s+)
 struct ZSymD { double spr, spi; };
 struct ZSymF { df spr, spi; };
+// z symbol with kappa^2 = |s+|^2 (FP32-data kernel specialised on Nz), 32 bytes
+struct ZSymK { df spr, spi, k2, pad; };
 
 __device__ __forceinline__ unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
 

@@ -39,6 +39,7 @@ struct fdetd_plan_s {
   void* d_Q = nullptr;
   void* d_phase = nullptr;
   void* d_zsym = nullptr;
+  void* d_zsymk = nullptr;   // z symbols with kappa^2 (FP32 data, Nz up to 4096)
   void* d_lam = nullptr;
   void* d_tw = nullptr;
   void* d_coef = nullptr;
@@ -85,8 +86,8 @@ static void prof_collect(fdetd_plan_s* p) {
 static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
-  void* ptrs[] = {p->d_P,  p->d_Q,    p->d_phase,  p->d_zsym, p->d_lam,      p->d_tw,
-                  p->d_coef, p->d_src, p->d_hostio, p->d_err,  p->d_cur};
+  void* ptrs[] = {p->d_P,    p->d_Q,   p->d_phase,  p->d_zsym, p->d_zsymk, p->d_lam,
+                  p->d_tw,   p->d_coef, p->d_src,   p->d_hostio, p->d_err,  p->d_cur};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -225,6 +226,17 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
       if ((e = upload(&p->d_zsym, zd.data(), Nz * sizeof(ZSymD), p->bytes)) != cudaSuccess) goto cuda_fail;
     } else {
       if ((e = upload(&p->d_zsym, zf.data(), Nz * sizeof(ZSymF), p->bytes)) != cudaSuccess) goto cuda_fail;
+      if (spectral32_supported(Nz)) {
+        std::vector<ZSymK> zk(Nz);
+        for (int q = 0; q < Nz; ++q) {
+          const int k = kz_at[q];
+          zk[q].spr = to_df(hp.sp_re[k]);
+          zk[q].spi = to_df(hp.sp_im[k]);
+          zk[q].k2 = to_df(hp.kappa2[k]);
+          zk[q].pad = to_df(0.0);
+        }
+        if ((e = upload(&p->d_zsymk, zk.data(), Nz * sizeof(ZSymK), p->bytes)) != cudaSuccess) goto cuda_fail;
+      }
     }
     const int prec_k = fp64 ? 0 : 1;
     p->tw_count = spectral_twiddles(Nz, prec_k, nullptr, nullptr);
@@ -273,6 +285,7 @@ static SpectralArgs spectral_args(fdetd_plan_s* p, bool hasJ) {
   sa.coef = p->d_coef;
   sa.phase = p->d_phase;
   sa.zsym = p->d_zsym;
+  sa.zsymk = p->d_zsymk;
   sa.lam = p->d_lam;
   sa.twiddle = p->d_tw;
   sa.tw_count = p->tw_count;
@@ -309,7 +322,9 @@ static int stage_spectral(fdetd_plan_s* p, bool hasJ, cudaStream_t st) {
   const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
   const SpectralArgs sa = spectral_args(p, hasJ);
   prof_mark(p, 1, true, st);
-  cudaError_t e = launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
+  // FP32 data with Nz up to 4096: the kernel specialised on Nz; otherwise the general one
+  cudaError_t e = prec == 1 && sa.zsymk ? launch_spectral32(sa, p->nmodes, p->tc != nullptr, st)
+                                        : launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
   prof_mark(p, 1, false, st);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("spectral: ") + cudaGetErrorString(e));
   return FDETD_OK;
@@ -719,7 +734,18 @@ struct fdetd_batch_s {
     float tuned_ms[2] = {0, 0};
   };
   std::vector<Group> groups;
+  // stage timing: per captured step, events before the grouped projections, after them, after the
+  // spectral branches have joined, after the grouped back-projections (recorded as graph nodes)
+  int profiling = 0;
+  std::vector<cudaEvent_t> stage_ev;
+  double stage_ms[3] = {0, 0, 0};
+  long stage_calls = 0;
 };
+
+static void batch_release_events(fdetd_batch_s* b) {
+  for (auto e : b->stage_ev) cudaEventDestroy(e);
+  b->stage_ev.clear();
+}
 
 static void batch_release_graph(fdetd_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -818,6 +844,19 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
     if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return fail(FDETD_ERR_CUDA, "stream");
     cap = own;
   }
+  batch_release_events(b);
+  if (b->profiling) {
+    b->stage_ev.resize((size_t)4 * nsteps, nullptr);
+    for (auto& ev : b->stage_ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        if (own) cudaStreamDestroy(own);
+        batch_release_events(b);
+        return fail(FDETD_ERR_CUDA, "batch: timing event creation failed");
+      }
+  }
+  auto mark = [&](int step, int k) -> cudaError_t {
+    return b->profiling ? cudaEventRecord(b->stage_ev[(size_t)4 * step + k], cap) : cudaSuccess;
+  };
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = FDETD_OK;
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
@@ -830,10 +869,12 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
     if (e == cudaSuccess) rc = fdetd_step(b->inst[k].plan, b->inst[k].fields, b->inst[k].J, nsteps, b->side[k]);
   }
   for (int s = 0; s < nsteps && e == cudaSuccess && rc == FDETD_OK; ++s) {
+    e = mark(s, 0);
     for (auto& G : b->groups) {
-      e = tc_group_project(G.g, cap);
       if (e != cudaSuccess) break;
+      e = tc_group_project(G.g, cap);
     }
+    if (e == cudaSuccess) e = mark(s, 1);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
     for (auto& G : b->groups)
       for (int k : G.members) {
@@ -843,10 +884,12 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
         if (e == cudaSuccess && rc == FDETD_OK) e = cudaEventRecord(b->join[k], b->side[k]);
         if (e == cudaSuccess && rc == FDETD_OK) e = cudaStreamWaitEvent(cap, b->join[k], 0);
       }
+    if (e == cudaSuccess && rc == FDETD_OK) e = mark(s, 2);
     for (auto& G : b->groups) {
       if (e != cudaSuccess || rc != FDETD_OK) break;
       e = tc_group_backproject(G.g, cap);
     }
+    if (e == cudaSuccess && rc == FDETD_OK) e = mark(s, 3);
   }
   for (int k : simt) {
     if (e != cudaSuccess || rc != FDETD_OK) break;
@@ -904,9 +947,70 @@ extern "C" int fdetd_batch_launch(fdetd_batch_t b, void* stream) {
   return FDETD_OK;
 }
 
+extern "C" int fdetd_batch_set_profiling(fdetd_batch_t b, int on) {
+  if (!b) return fail(FDETD_ERR_ARG, "batch is null");
+  b->profiling = on != 0;
+  b->stage_ms[0] = b->stage_ms[1] = b->stage_ms[2] = 0;
+  b->stage_calls = 0;
+  batch_release_graph(b);
+  batch_release_events(b);
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_collect_stage_times(fdetd_batch_t b) {
+  if (!b || !b->exec || !b->profiling) return fail(FDETD_ERR_ARG, "batch not captured with profiling on");
+  for (size_t s = 0; s + 3 < b->stage_ev.size(); s += 4) {
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&ms, b->stage_ev[s + k], b->stage_ev[s + k + 1]);
+      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("batch stage timing: ") + cudaGetErrorString(e));
+      b->stage_ms[k] += ms;
+    }
+    ++b->stage_calls;
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_stage_times(fdetd_batch_t b, double* ms, long* steps) {
+  if (!b || !ms) return fail(FDETD_ERR_ARG, "null argument");
+  for (int k = 0; k < 3; ++k) ms[k] = b->stage_ms[k];
+  if (steps) *steps = b->stage_calls;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_step_host(fdetd_batch_t b, void* const* host_fields, const void* const* host_J,
+                                     int nlaunch, void* stream) {
+  if (!b || !b->exec || !host_fields) return fail(FDETD_ERR_ARG, "batch has no captured graph or null fields");
+  if (nlaunch < 0) return fail(FDETD_ERR_ARG, "nlaunch < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < b->inst.size() && e == cudaSuccess; ++k) {
+    const fdetd_plan_s* p = b->inst[k].plan;
+    const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
+    const size_t plane = (size_t)p->nmodes * p->Nz * p->Nr * elt;
+    if (!host_fields[k]) return fail(FDETD_ERR_ARG, "null host fields");
+    e = cudaMemcpyAsync(b->inst[k].fields, host_fields[k], 6 * plane, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && b->inst[k].J) {
+      if (!host_J || !host_J[k]) return fail(FDETD_ERR_ARG, "instance was added with a current: host J needed");
+      e = cudaMemcpyAsync((void*)b->inst[k].J, host_J[k], 3 * plane, cudaMemcpyHostToDevice, st);
+    }
+  }
+  for (int s = 0; s < nlaunch && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->exec, st);
+  for (size_t k = 0; k < b->inst.size() && e == cudaSuccess; ++k) {
+    const fdetd_plan_s* p = b->inst[k].plan;
+    const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
+    e = cudaMemcpyAsync(host_fields[k], b->inst[k].fields, 6 * (size_t)p->nmodes * p->Nz * p->Nr * elt,
+                        cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("batch host step: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_batch_destroy(fdetd_batch_t b) {
   if (!b) return FDETD_OK;
   batch_release_graph(b);
+  batch_release_events(b);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -922,6 +1026,7 @@ struct envelope_plan_s {
   float* d_lr = nullptr;
   float2* d_buf = nullptr;  // T0 (a, a~), T1 (a, a~), ACC (a, a~)
   float* d_chit = nullptr;  // chi + sigma^2 of the absorbing-layer step
+  size_t bytes = 0;         // device bytes held
   EnvArgs base;
 };
 
@@ -968,6 +1073,7 @@ extern "C" int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, in
   cudaError_t e = upload((void**)&p->d_lr, bandf.data(), bandf.size() * 4, tot);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_buf, (size_t)6 * Nz * Nr * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_chit, (size_t)Nz * Nr * sizeof(float));
+  p->bytes = tot + (size_t)6 * Nz * Nr * sizeof(float2) + (size_t)Nz * Nr * sizeof(float);
   if (e != cudaSuccess) {
     if (p->d_lr) cudaFree(p->d_lr);
     if (p->d_buf) cudaFree(p->d_buf);
@@ -1060,6 +1166,8 @@ extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* 
 }
 
 extern "C" int envelope_plan_launches_per_step(envelope_plan_t p) { return p ? p->NT : 0; }
+
+extern "C" size_t envelope_plan_device_bytes(envelope_plan_t p) { return p ? p->bytes : 0; }
 
 extern "C" int envelope_plan_destroy(envelope_plan_t p) {
   if (!p) return FDETD_OK;

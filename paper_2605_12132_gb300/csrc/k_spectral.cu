@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fft_small.cuh"
 #include "kernels.h"
 
 namespace fdetd {
@@ -92,62 +93,17 @@ __device__ __forceinline__ void l2_prefetch(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((uint64_t)src), "r"(bytes) : "memory");
 }
 
-// multiply by -i (forward) / +i (inverse)
-template <bool INV, typename C>
-__device__ __forceinline__ C rot90(C a) {
-  C r;
-  if (INV) {
-    r.x = -a.y;
-    r.y = a.x;
-  } else {
-    r.x = a.y;
-    r.y = -a.x;
-  }
-  return r;
-}
-
-// In-register DFT of RR points, natural order in and out (W = exp(-+2 pi i / RR)).
-template <int RR, bool INV, typename C>
-__device__ __forceinline__ void dft_small(C* v) {
-  if (RR == 2) {
-    const C t = v[1];
-    v[1] = csub(v[0], t);
-    v[0] = cadd(v[0], t);
-  } else if (RR == 4) {
-    const C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), a2 = cadd(v[1], v[3]);
-    const C a3 = rot90<INV>(csub(v[1], v[3]));
-    v[0] = cadd(a0, a2);
-    v[2] = csub(a0, a2);
-    v[1] = cadd(a1, a3);
-    v[3] = csub(a1, a3);
-  } else {  // 8: two 4-point DFTs (even / odd samples) and one radix-2 stage
-    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
-    dft_small<4, INV>(e);
-    dft_small<4, INV>(o);
-    typedef decltype(e[0].x) R;
-    const R h = (R)0.70710678118654752440;
-    C w1, w3;  // W8^1, W8^3 (forward), conjugates for the inverse
-    w1.x = h;
-    w1.y = INV ? h : -h;
-    w3.x = -h;
-    w3.y = INV ? h : -h;
-    const C t0 = o[0], t1 = cmul(w1, o[1]), t2 = rot90<INV>(o[2]), t3 = cmul(w3, o[3]);
-    v[0] = cadd(e[0], t0);
-    v[4] = csub(e[0], t0);
-    v[1] = cadd(e[1], t1);
-    v[5] = csub(e[1], t1);
-    v[2] = cadd(e[2], t2);
-    v[6] = csub(e[2], t2);
-    v[3] = cadd(e[3], t3);
-    v[7] = csub(e[3], t3);
-  }
-}
-
 // Kernel modes: FUSED transforms the family's field and current columns together; SOURCE
 // transforms only the current columns and writes the midpoint source term (with the 1/Nz of the
 // inverse transform) in kz space; MAIN transforms the field columns and adds that precomputed
 // source (used when five columns do not fit in shared memory).
 enum { FUSED = 0, MAIN = 1, SOURCE = 2 };
+
+// Column slots a kernel of the given mode keeps in shared memory (the twiddles follow them when they are
+// staged): the one count both the kernel's layout and the launcher's sizing use.
+__host__ __device__ __forceinline__ constexpr int spectral_slots(int mode, bool hasJ) {
+  return mode == FUSED ? (hasJ ? 5 : 3) : (mode == MAIN ? 3 : 2);
+}
 
 // ---------------------------------------------------------------- in-place transforms
 // N = 2^logN = RF R^(S-1): a first stage of radix RF (the factor left over by radix R), then radix-R
@@ -160,12 +116,8 @@ enum { FUSED = 0, MAIN = 1, SOURCE = 2 };
 // order.  The twiddle table of stage s holds W_{M_s}^{n1 k2} at (k2 - 1) L_s + n1 (k2 >= 1), stages
 // back to back, so the threads of a warp (consecutive n1) read consecutive entries.  The per-kz
 // tables hold the record of position b RL + r (last stage of radix RL) at r (N / RL) + b, so the
-// threads of a warp (consecutive b) read consecutive records.
-//
-// Shared-memory layout of one column: element p at pad16(p) = p + 2 floor(p / 16), two pad slots
-// after every 16 elements, so 16-byte pairs stay aligned for the asynchronous copies and the strided
-// butterflies of every stage fall on distinct banks.
-__host__ __device__ __forceinline__ int pad16(int p) { return p + ((p >> 4) << 1); }
+// threads of a warp (consecutive b) read consecutive records.  Columns sit in shared memory in the
+// padded layout pad16 (fft_small.cuh).
 
 // 16-byte asynchronous global -> shared copy, and the wait for all of a thread's copies
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -487,8 +439,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
   const C* coef = reinterpret_cast<const C*>(args.coef);
   const C* twg = reinterpret_cast<const C*>(args.twiddle);
   const int Pc = pad16(Nz);
-  // column slots in shared memory; must match launch_one's sizing (the twiddles follow them)
-  const int slots = MODE == FUSED ? (args.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);
+  const int slots = spectral_slots(MODE, args.hasJ);
   const C* tw = TW_SMEM ? s + (size_t)slots * Pc : twg;
   const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * Nz;
   if (threadIdx.x == 0) {
@@ -588,8 +539,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT, int MODE, bool TW_SMEM>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
-  const int arrays = MODE == FUSED ? (a.hasJ ? 5 : 3) : (MODE == MAIN ? 3 : 2);  // = the kernel's `slots`
-  const size_t smem = ((size_t)arrays * pad16(a.Nz) + (TW_SMEM ? (size_t)a.tw_count : 0)) * sizeof(C);
+  const size_t smem = ((size_t)spectral_slots(MODE, a.hasJ) * pad16(a.Nz) + (TW_SMEM ? (size_t)a.tw_count : 0)) *
+                      sizeof(C);
   auto k = spectral_kernel<T, K, PH, ZS, R, NT, SPLIT, MODE, TW_SMEM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -609,7 +560,7 @@ static cudaError_t launch_sized(const SpectralArgs& a, int nmodes, cudaStream_t 
 }
 
 static size_t fused_bytes(int Nz, int precision, bool hasJ, int tw_count) {
-  return ((size_t)(hasJ ? 5 : 3) * pad16(Nz) + (size_t)tw_count) * (precision == 0 ? 16 : 8);
+  return ((size_t)spectral_slots(FUSED, hasJ) * pad16(Nz) + (size_t)tw_count) * (precision == 0 ? 16 : 8);
 }
 
 template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT>
@@ -643,8 +594,9 @@ bool spectral_needs_source(int Nz, int precision, int tw_count) {
 // (padded layout, twiddles through L1).  The fused path is used whenever it fits.
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ) {
   (void)hasJ;
-  return (size_t)3 * pad16(Nz) * (precision == 0 ? 16 : 8);
+  return (size_t)spectral_slots(MAIN, false) * pad16(Nz) * (precision == 0 ? 16 : 8);
 }
+
 
 // Stage radices of the transform of length Nz = 2^logN: the leftover factor 2^(logN mod log2 R) first
 // (when it is not 1), then R (8 for FP32, 4 for FP64); a transform shorter than R is a single stage.

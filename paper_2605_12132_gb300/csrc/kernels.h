@@ -28,6 +28,7 @@ struct SpectralArgs {
   int hasJ;
   int* err;              // the plan's device failure flag (the spectral kernel has no waits that could set it)
   void* src;             // [nmodes][2][3][n][Nz] complex<T>: kz-space source term (two-kernel path)
+  const void* zsymk;     // [Nz] ZSymK, position order (FP32 data: the kernel specialised on Nz)
 };
 
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);
@@ -36,6 +37,11 @@ int spectral_twiddles(int Nz, int precision, double* re, double* im);
 // kz index held at each position of the forward transform's output (the order of the phase and z tables)
 void spectral_positions(int Nz, int precision, int* kz);
 bool spectral_needs_source(int Nz, int precision, int tw_count);
+// FP32 data, Nz = 2^k in 64..4096: the kernel specialised on Nz (k_spectral32.cu); cudaErrorNotSupported
+// for other lengths
+bool spectral32_supported(int Nz);
+size_t spectral32_smem_bytes(int Nz, bool hasJ);
+cudaError_t launch_spectral32(const SpectralArgs& a, int nmodes, bool split_out, cudaStream_t st);
 
 // bf16 split of FP32 values into npieces (2 or 3) terms whose sum reproduces them to 16 / 24
 // significant bits, stored in the pre-tiled operand layout of the back-projection: 16 KB blocks

@@ -1,22 +1,60 @@
-"""Continuous-batching server for field-advance and envelope-advance requests.
+"""Continuous-batching server for field-advance and envelope-advance requests: the Python face of the
+library's fdetd_server_* calls (include/fdetd.h).
 
-Requests of different sizes arrive over time; each is admitted when its device footprint
-(plan tables + scratch + resident state) fits the HBM budget, gets its own CUDA stream and
-stays resident on the device until it completes.  Work advances in chunks of a few steps per
-request per scheduling round, so requests that arrive while others run are admitted as soon as
-memory frees up and their chunks interleave with the running ones on the device.  Plans are
-built on worker threads (the host eigen-solve runs in C++ and releases the GIL).  All device
-work is done by the C-ABI library; this module only schedules it.
+The scheduling lives in the library (one scheduler thread and plan-builder threads in C++): requests are
+admitted first-come first-served by HBM budget, field requests that are resident on the device advance
+together as the instances of one batch (one CUDA graph per step with grouped tensor-core launches,
+re-captured when a request joins or leaves), envelope requests advance on their own streams alongside,
+and each result is copied back to a host buffer when its request finishes.  This module only marshals
+requests, keeps their host buffers alive until they finish, and feeds Poisson arrivals.
 """
-import concurrent.futures as cf
-import itertools
+import ctypes
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import List, Optional
 
 import numpy as np
 
 from . import _native as nat
+
+REQUEST_FIELD, REQUEST_ENVELOPE = 0, 1
+QUEUED, ADMITTED, RUNNING, DONE, FAILED = range(5)
+DRY_RUN = 1
+_PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("Nz", ctypes.c_int), ("Nr", ctypes.c_int), ("nmodes", ctypes.c_int),
+                ("modes", ctypes.POINTER(ctypes.c_int)), ("order", ctypes.c_int), ("precision", ctypes.c_int),
+                ("taylor_order", ctypes.c_int), ("steps", ctypes.c_int), ("dz", ctypes.c_double),
+                ("dr", ctypes.c_double), ("dt", ctypes.c_double), ("k0", ctypes.c_double),
+                ("fields", ctypes.c_void_p), ("J", ctypes.c_void_p), ("chi", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("queued", ctypes.c_size_t), ("building", ctypes.c_size_t), ("running", ctypes.c_size_t),
+                ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("recaptures", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("served_cell_steps", ctypes.c_double)]
+
+
+def _bind():
+    L = nat.lib()
+    if getattr(L, "_server_bound", False):
+        return L
+    vp, u64 = ctypes.c_void_p, ctypes.c_uint64
+    L.fdetd_request_device_bytes.argtypes = [ctypes.POINTER(_Request)]
+    L.fdetd_request_device_bytes.restype = ctypes.c_size_t
+    L.fdetd_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, u64]
+    L.fdetd_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(u64)]
+    L.fdetd_server_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.fdetd_server_wait.argtypes = [vp, u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.fdetd_server_ticket_times.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_double)]
+    L.fdetd_server_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    L.fdetd_server_destroy.argtypes = [vp]
+    L._server_bound = True
+    return L
 
 
 @dataclass
@@ -31,7 +69,7 @@ class FieldRequest:
     steps: int
     F: np.ndarray                 # [nmodes][6][Nz][Nr] complex
     J: Optional[np.ndarray] = None
-    precision: str = "bf16x3"
+    precision: str = "bf16x6"
     kind: str = "field"
 
 
@@ -51,190 +89,138 @@ class EnvelopeRequest:
     kind: str = "envelope"
 
 
-@dataclass
 class Ticket:
-    id: int
-    request: object
-    arrival: float
-    admitted: Optional[float] = None
-    completed: Optional[float] = None
-    result: Optional[np.ndarray] = None
-    bytes: int = 0
-    # device-side state while active
-    _plan: object = None
-    _state: object = None
-    _aux: object = None
-    _stream: object = None
-    _done_steps: int = 0
-    _event: object = None
-    _host: object = None
-    _future: object = None
+    """A submitted request: its id, the host buffers the library reads and writes, and its result."""
+
+    def __init__(self, server, request, c_req, keep):
+        self.server, self.request, self._c_req, self._keep = server, request, c_req, keep
+        self.id = None
+        self.arrival = None
+
+    @property
+    def state(self):
+        st = ctypes.c_int(0)
+        _bind().fdetd_server_poll(self.server.handle, self.id, ctypes.byref(st), None)
+        return st.value
 
     @property
     def latency(self):
-        return None if self.completed is None else self.completed - self.arrival
+        """Completion minus submission time in seconds, None until done."""
+        lat = ctypes.c_double(-1.0)
+        st = ctypes.c_int(0)
+        _bind().fdetd_server_poll(self.server.handle, self.id, ctypes.byref(st), ctypes.byref(lat))
+        return lat.value if st.value == DONE else None
+
+    def times(self):
+        t = (ctypes.c_double * 3)()
+        nat._check(_bind().fdetd_server_ticket_times(self.server.handle, self.id, t))
+        return tuple(t)
+
+    @property
+    def result(self):
+        return self._keep["out"] if self.state == DONE else None
+
+    def wait(self, timeout=600.0):
+        lat = ctypes.c_double(-1.0)
+        nat._check(_bind().fdetd_server_wait(self.server.handle, self.id, timeout, ctypes.byref(lat)))
+        return lat.value
 
 
-def _pad(x, m):
-    return (x + m - 1) // m * m
+def _c_request(req):
+    """The C request and the host arrays it points into (kept alive by the ticket)."""
+    keep = {}
+    r = _Request()
+    r.Nz, r.Nr, r.order, r.steps = req.Nz, req.Nr, req.order, req.steps
+    r.dz, r.dr, r.dt = req.dz, req.dr, req.dt
+    if req.kind == "envelope":
+        r.kind = REQUEST_ENVELOPE
+        r.taylor_order, r.k0 = req.taylor_order, req.k0
+        keep["fields"] = np.ascontiguousarray(req.a, dtype=np.complex64)
+        keep["chi"] = np.ascontiguousarray(req.chi, dtype=np.float32)
+        r.chi = keep["chi"].ctypes.data
+    else:
+        r.kind = REQUEST_FIELD
+        r.precision = _PREC[req.precision]
+        cdt = np.complex128 if req.precision == "fp64" else np.complex64
+        keep["modes"] = (ctypes.c_int * len(req.modes))(*req.modes)
+        r.nmodes = len(req.modes)
+        r.modes = keep["modes"]
+        keep["fields"] = np.ascontiguousarray(req.F, dtype=cdt)
+        if req.J is not None:
+            keep["J"] = np.ascontiguousarray(req.J, dtype=cdt)
+            r.J = keep["J"].ctypes.data
+    keep["out"] = np.empty_like(keep["fields"])
+    r.fields = keep["fields"].ctypes.data
+    r.out = keep["out"].ctypes.data
+    return r, keep
 
 
 def estimate_bytes(req):
-    """Device bytes a request holds while admitted (plan tables, scratch, resident state)."""
-    if req.kind == "envelope":
-        cells = req.Nz * req.Nr
-        return cells * (2 * 8 + 4 + 6 * 8) + req.Nr * (req.order + 2) * 4
-    n, Nz, nm = req.Nr, req.Nz, len(req.modes)
-    cells = nm * Nz * n
-    elt = 16 if req.precision == "fp64" else 8
-    state = cells * 6 * elt + (cells * 3 * elt if req.J is not None else 0)
-    coef = cells * 9 * elt
-    phase = nm * 2 * n * Nz * (32 if req.precision == "fp64" else 16)
-    tables = phase + Nz * 16 * 2 + nm * 2 * n * 16 + 64
-    if req.precision in ("bf16x3", "bf16x6"):
-        npc = 2 if req.precision == "bf16x3" else 3
-        kp = _pad(n, 64)
-        mats = nm * 2 * npc * (3 * _pad(n, 256) + 3 * _pad(n, 128)) * 3 * kp * 2
-        split = nm * npc * 6 * kp * 2 * Nz * 2
-        tables += mats + split
-    else:
-        tables += 2 * nm * 2 * (3 * n) ** 2 * (8 if req.precision == "fp64" else 4)
-    return state + coef + tables
+    """Device bytes the server reserves for a request while it is admitted (fdetd_request_device_bytes)."""
+    r, _ = _c_request(req)
+    return int(_bind().fdetd_request_device_bytes(ctypes.byref(r)))
 
 
 class Server:
-    def __init__(self, hbm_budget, chunk_steps=16, plan_workers=4):
-        import torch
-        self.torch = torch
+    def __init__(self, hbm_budget, chunk_steps=16, plan_workers=4, dry_run=False):
+        L = _bind()
+        h = ctypes.c_void_p()
+        nat._check(L.fdetd_server_create(ctypes.byref(h), int(hbm_budget), int(chunk_steps), int(plan_workers),
+                                         DRY_RUN if dry_run else 0))
+        self.handle = h
         self.budget = int(hbm_budget)
-        self.used = 0
-        self.peak_used = 0
-        self.chunk = chunk_steps
-        self.queue: List[Ticket] = []      # arrived, not admitted
-        self.building: List[Ticket] = []   # admitted, plan under construction
-        self.active: List[Ticket] = []     # on the device
-        self.finishing: List[Ticket] = []  # last chunk launched, waiting for its event
-        self.done: List[Ticket] = []
-        self.ids = itertools.count()
-        self.pool = cf.ThreadPoolExecutor(max_workers=plan_workers)
-        self.streams = []
+        self.tickets = []
 
-    # ------------------------------------------------------------- API
     def submit(self, req, arrival=None):
-        t = Ticket(next(self.ids), req, time.perf_counter() if arrival is None else arrival)
-        t.bytes = estimate_bytes(req)
-        if t.bytes > self.budget:
-            raise nat.FdetdError(f"request {t.id} needs {t.bytes} bytes, more than the whole budget {self.budget}")
-        self.queue.append(t)
+        r, keep = _c_request(req)
+        t = Ticket(self, req, r, keep)
+        tid = ctypes.c_uint64(0)
+        nat._check(_bind().fdetd_server_submit(self.handle, ctypes.byref(r), ctypes.byref(tid)))
+        t.id = tid.value
+        t.arrival = time.perf_counter() if arrival is None else arrival
+        self.tickets.append(t)
         return t
 
-    def pending(self):
-        return len(self.queue) + len(self.building) + len(self.active) + len(self.finishing)
+    def stats(self):
+        s = _Stats()
+        nat._check(_bind().fdetd_server_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
 
-    def pump(self):
-        """One scheduling round: admit, start plans, launch chunks, reap completions."""
-        self._admit()
-        self._start_ready()
-        self._launch_chunks()
-        self._reap()
+    @property
+    def used(self):
+        return self.stats()["used_bytes"]
+
+    @property
+    def peak_used(self):
+        return self.stats()["peak_bytes"]
+
+    def pending(self):
+        s = self.stats()
+        return s["queued"] + s["building"] + s["running"]
 
     def drain(self, timeout=600.0):
         t0 = time.perf_counter()
-        while self.pending():
-            self.pump()
-            if time.perf_counter() - t0 > timeout:
+        for t in self.tickets:
+            left = max(0.0, timeout - (time.perf_counter() - t0))
+            lat = ctypes.c_double(-1.0)
+            rc = _bind().fdetd_server_wait(self.handle, t.id, left, ctypes.byref(lat))
+            if rc == 6:
                 raise TimeoutError("server did not drain in time")
-            time.sleep(0)
 
     def close(self):
-        self.pool.shutdown(wait=True)
+        if self.handle:
+            _bind().fdetd_server_destroy(self.handle)
+            self.handle = None
 
-    # ------------------------------------------------------------- internals
-    def _admit(self):
-        # first-come first-served; a request that does not fit waits (no overtaking, no starvation)
-        while self.queue and self.used + self.queue[0].bytes <= self.budget:
-            t = self.queue.pop(0)
-            self.used += t.bytes
-            self.peak_used = max(self.peak_used, self.used)
-            t.admitted = time.perf_counter()
-            t._future = self.pool.submit(self._build_plan, t.request)
-            self.building.append(t)
-
-    @staticmethod
-    def _build_plan(req):
-        if req.kind == "envelope":
-            return nat.envelope_plan(req.Nz, req.Nr, req.order, req.taylor_order, req.dz, req.dr, req.dt, req.k0)
-        return nat.fdetd_plan_modes(req.Nz, req.Nr, req.modes, req.order, req.dz, req.dr, req.dt,
-                                    precision=req.precision)
-
-    def _stream(self):
-        if self.streams:
-            return self.streams.pop()
-        return self.torch.cuda.Stream()
-
-    def _start_ready(self):
-        torch = self.torch
-        still = []
-        for t in self.building:
-            if not t._future.done():
-                still.append(t)
-                continue
-            t._plan = t._future.result()
-            t._stream = self._stream()
-            req = t.request
-            with torch.cuda.stream(t._stream):
-                if req.kind == "envelope":
-                    t._state = torch.from_numpy(req.a).to(torch.complex64).to("cuda", non_blocking=True)
-                    t._aux = torch.from_numpy(np.ascontiguousarray(req.chi, dtype=np.float32)).to("cuda", non_blocking=True)
-                else:
-                    cdt = t._plan.complex_dtype
-                    t._state = torch.from_numpy(req.F).to(cdt).to("cuda", non_blocking=True)
-                    t._aux = (torch.from_numpy(req.J).to(cdt).to("cuda", non_blocking=True)
-                              if req.J is not None else None)
-            self.active.append(t)
-        self.building = still
-
-    def _launch_chunks(self):
-        torch = self.torch
-        still = []
-        for t in self.active:
-            req = t.request
-            n = min(self.chunk, req.steps - t._done_steps)
-            if req.kind == "envelope":
-                nat.envelope_step(t._plan, t._state, t._aux, n, stream=t._stream)
-            else:
-                nat.fdetd_step(t._plan, t._state, t._aux, n, stream=t._stream)
-            t._done_steps += n
-            if t._done_steps >= req.steps:
-                with torch.cuda.stream(t._stream):
-                    t._host = t._state.to("cpu", non_blocking=True)
-                    t._event = torch.cuda.Event()
-                    t._event.record(t._stream)
-                self.finishing.append(t)
-            else:
-                still.append(t)
-        self.active = still
-
-    def _reap(self):
-        still = []
-        for t in self.finishing:
-            if t._event.query():
-                t.completed = time.perf_counter()
-                t.result = t._host.numpy().copy()
-                if t.request.kind == "field":
-                    t._plan.status(t._stream)
-                t._plan.close()
-                self.streams.append(t._stream)
-                t._plan = t._state = t._aux = t._host = t._event = None
-                self.used -= t.bytes
-                self.done.append(t)
-            else:
-                still.append(t)
-        self.finishing = still
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def run_poisson(server, make_request, rate_hz, duration_s, seed=0, max_requests=None):
-    """Feed requests with Poisson arrivals (rate_hz over duration_s) and serve them; returns tickets."""
+    """Submit requests with Poisson arrivals (rate_hz over duration_s); returns the tickets (not waited for)."""
     rng = np.random.default_rng(seed)
     times = []
     t = 0.0
@@ -246,19 +232,17 @@ def run_poisson(server, make_request, rate_hz, duration_s, seed=0, max_requests=
     reqs = [make_request(i, rng) for i in range(len(times))]
     t0 = time.perf_counter()
     tickets = []
-    k = 0
-    while k < len(times) or server.pending():
-        now = time.perf_counter() - t0
-        while k < len(times) and times[k] <= now:
-            tickets.append(server.submit(reqs[k], arrival=t0 + times[k]))
-            k += 1
-        server.pump()
+    for k, at in enumerate(times):
+        delay = t0 + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(server.submit(reqs[k], arrival=t0 + at))
     return tickets
 
 
 def latency_stats(tickets):
-    lat = np.array([t.latency for t in tickets if t.latency is not None])
+    lat = np.array([x for x in (t.latency for t in tickets) if x is not None])
     if lat.size == 0:
-        return {}
+        return {"count": 0}
     return {"count": int(lat.size), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "max_s": float(lat.max())}

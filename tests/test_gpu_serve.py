@@ -1,9 +1,15 @@
-"""Continuous-batching server: requests admitted under an HBM budget, interleaved on the device,
-each result identical (bitwise) to the same request run alone."""
+"""The library's continuous-batching server on the GPU: requests of different sizes and precisions admitted
+under an HBM budget, the resident field requests advanced together as one batch (grouped launches under a
+CUDA graph, re-captured as requests join and leave), envelope requests alongside.  Each result equals the
+same request run alone (bitwise: the batch runs the same kernels on the same data), the served field results
+match the FP64 oracle on sampled kz columns, and the server's device-footprint estimate covers what the
+plans and resident state actually hold."""
 import numpy as np
 import pytest
 
+from oracle import maxwell as mx
 from paper_2605_12132_gb300 import inputs
+from tests.gpu_util import check_report, column_report, format_report, kz_columns
 
 pytestmark = pytest.mark.gpu
 
@@ -14,12 +20,15 @@ if not torch.cuda.is_available():
 import paper_2605_12132_gb300 as fd  # noqa: E402
 from paper_2605_12132_gb300 import serve  # noqa: E402
 
+# per-step tolerance of the strong fields and the weak-field bound, relative L2 per field
+TOL = {"bf16x3": (3e-5, 1e-3), "bf16x6": (3e-6, 1e-4), "fp32": (1e-6, 1e-4), "fp64": (1e-12, 1e-10)}
+
 
 def _requests():
-    rng = np.random.default_rng(11)
     reqs = []
     for k, (Nz, Nr, M, prec, steps) in enumerate([(256, 64, 1, "bf16x3", 20), (128, 96, 2, "fp32", 13),
-                                                   (512, 40, 1, "bf16x6", 9), (64, 32, 0, "fp64", 7)]):
+                                                   (512, 40, 1, "bf16x6", 9), (64, 32, 0, "fp64", 7),
+                                                   (256, 128, 2, "bf16x6", 6)]):
         F = np.zeros((M + 1, 6, Nz, Nr), complex)
         F[min(1, M)] = inputs.pulse_fields(Nz, Nr, 1 / 16, 1 / 4, 2.5, 2.0)
         for f in (0, 4, 5):
@@ -48,21 +57,37 @@ def _alone(req):
     return st.cpu().numpy()
 
 
-def test_mix_equals_alone_under_budget():
+def test_mix_equals_alone_and_oracle_under_budget():
     reqs = _requests()
     alone = [_alone(r) for r in reqs]
     need = [serve.estimate_bytes(r) for r in reqs]
     budget = int(max(need) * 1.6)          # forces queueing: not everything fits at once
     srv = serve.Server(budget, chunk_steps=4)
     tickets = [srv.submit(r) for r in reqs]
-    srv.drain(timeout=300)
-    srv.close()
-    assert srv.peak_used <= budget and srv.used == 0
+    for t in tickets:
+        t.wait(300)
+    st = srv.stats()
+    assert st["peak_bytes"] <= budget and st["used_bytes"] == 0 and st["completed"] == len(reqs)
+    assert st["recaptures"] >= 2           # the batch changed membership while requests were served
     for t, ref in zip(tickets, alone):
-        assert t.completed is not None and t.latency >= 0
+        assert t.state == serve.DONE and t.latency >= 0
         assert np.array_equal(t.result, ref), t.id
-    stats = serve.latency_stats(tickets)
-    assert stats["count"] == len(reqs) and stats["p99_s"] >= stats["p50_s"]
+    srv.close()
+    # the served field results against the oracle (kz = 0, the carrier, one outside the band)
+    for t in tickets:
+        r = t.request
+        if r.kind != "field":
+            continue
+        qs = [0, r.Nz // 16, r.Nz // 3]
+        G = kz_columns(t.result.astype(np.complex128), qs)
+        for i, m in enumerate(r.modes):
+            ref = mx.step_spectral(r.F[i], r.J[i], r.Nz, r.Nr, m, r.order, r.dz, r.dr, r.dt, nsteps=r.steps,
+                                   kz_subset=qs, method="expm")
+            rows = column_report([G[i][:, k, :] for k in range(len(qs))], [ref[q] for q in qs])
+            label = f"served {r.precision} {r.Nz}x{r.Nr} m={m} after {r.steps}"
+            print("\n" + format_report(rows, label))
+            tol, weak = TOL[r.precision]
+            check_report(rows, tol * r.steps, weak * r.steps, label=label)
 
 
 def test_request_larger_than_budget_is_rejected():
@@ -71,3 +96,25 @@ def test_request_larger_than_budget_is_rejected():
     with pytest.raises(fd.FdetdError):
         srv.submit(reqs[0])
     srv.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16x6"])
+def test_footprint_estimate_covers_plan_and_state(prec):
+    for Nz, Nr, M in [(256, 64, 1), (512, 200, 2), (8192, 48, 1)]:
+        if prec == "fp64" and Nz > 4096:
+            continue
+        F = np.zeros((M + 1, 6, Nz, Nr), complex)
+        J = np.zeros((M + 1, 3, Nz, Nr), complex)
+        req = serve.FieldRequest(Nz, Nr, list(range(M + 1)), 8, 1 / 16, 1 / 4, 1 / 16, 5, F, J, prec)
+        plan = fd.fdetd_plan(Nz, Nr, M, 8, 1 / 16, 1 / 4, 1 / 16, precision=prec)
+        elt = 16 if prec == "fp64" else 8
+        state = (M + 1) * 9 * Nz * Nr * elt
+        assert serve.estimate_bytes(req) >= plan.device_bytes + state, (prec, Nz, Nr, M)
+        plan.close()
+    ew = inputs.envelope_workload("envelope_4096x256")
+    a, at, chi = inputs.envelope_inputs(ew)
+    req = serve.EnvelopeRequest(ew.Nz, ew.Nr, ew.order, ew.taylor_order, ew.dz, ew.dr, ew.dt, 10,
+                                np.stack([a, at]), chi)
+    plan = fd.envelope_plan(ew.Nz, ew.Nr, ew.order, ew.taylor_order, ew.dz, ew.dr, ew.dt)
+    assert serve.estimate_bytes(req) >= plan.device_bytes + ew.Nz * ew.Nr * (16 + 4)
+    plan.close()

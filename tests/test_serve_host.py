@@ -1,65 +1,23 @@
-"""Host-side logic of the continuous-batching server (CPU only): the device work is replaced by a fake that
-completes a chunk per scheduling round, so admission, ordering, memory accounting and the latency statistics
-are checked without a GPU."""
-import time
-
+"""Host-side logic of the library's continuous-batching server (CPU only): in dry-run mode the server makes no
+CUDA call (plans are only checked on the host and a chunk takes a fixed host time per step), so admission
+order, the HBM budget, memory accounting, failure handling and the latency statistics are checked without a
+GPU."""
 import numpy as np
 import pytest
 
-pytest.importorskip("torch")
-
-from paper_2605_12132_gb300 import _native as nat  # noqa: E402
-from paper_2605_12132_gb300 import serve  # noqa: E402
+from paper_2605_12132_gb300 import _native as nat
+from paper_2605_12132_gb300 import serve
 
 
-def _field(Nz=64, Nr=32, modes=(0, 1), steps=5, prec="bf16x3", with_J=True):
+def _field(Nz=64, Nr=32, modes=(0, 1), steps=5, prec="bf16x3", with_J=True, order=8):
     F = np.zeros((len(modes), 6, Nz, Nr), complex)
     J = np.zeros((len(modes), 3, Nz, Nr), complex) if with_J else None
-    return serve.FieldRequest(Nz, Nr, list(modes), 8, 0.1, 0.1, 0.1, steps, F, J, prec)
+    return serve.FieldRequest(Nz, Nr, list(modes), order, 0.1, 0.1, 0.1, steps, F, J, prec)
 
 
-class FakeServer(serve.Server):
-    """The scheduler with the device replaced: plans are dummies, a chunk completes at once."""
-
-    def __init__(self, *a, **k):
-        super().__init__(*a, **k)
-        self.admission_order = []
-        self.max_used = 0
-
-    @staticmethod
-    def _build_plan(req):
-        return object()
-
-    def _admit(self):
-        before = {t.id for t in self.building}
-        super()._admit()
-        self.admission_order += [t.id for t in self.building if t.id not in before]
-        self.max_used = max(self.max_used, self.used)
-        assert self.used <= self.budget
-
-    def _start_ready(self):
-        still = []
-        for t in self.building:
-            if t._future.done():
-                t._plan = t._future.result()
-                self.active.append(t)
-            else:
-                still.append(t)
-        self.building = still
-
-    def _launch_chunks(self):
-        still = []
-        for t in self.active:
-            t._done_steps += min(self.chunk, t.request.steps - t._done_steps)
-            (self.finishing if t._done_steps >= t.request.steps else still).append(t)
-        self.active = still
-
-    def _reap(self):
-        for t in self.finishing:
-            t.completed = time.perf_counter()
-            self.used -= t.bytes
-            self.done.append(t)
-        self.finishing = []
+def _envelope(Nz=64, Nr=32, steps=7):
+    a = np.zeros((2, Nz, Nr), complex)
+    return serve.EnvelopeRequest(Nz, Nr, 8, 4, 0.2, 0.25, 0.05, steps, a, np.zeros((Nz, Nr)))
 
 
 def test_estimate_bytes_grows_with_precision_current_and_size():
@@ -67,39 +25,70 @@ def test_estimate_bytes_grows_with_precision_current_and_size():
     f32, f64 = serve.estimate_bytes(_field(prec="fp32")), serve.estimate_bytes(_field(prec="fp64"))
     assert b6 > b3 and f64 > f32
     noJ = serve.estimate_bytes(_field(with_J=False))
-    assert b3 - noJ == 2 * 3 * 64 * 32 * 8          # the resident current: modes x 3 x Nz x Nr complex64
+    assert b3 - noJ >= 2 * 3 * 64 * 32 * 8          # the resident current: modes x 3 x Nz x Nr complex64
     assert serve.estimate_bytes(_field(Nz=128)) > b3
+    # envelope: state, chi, the plan's three Taylor buffers and the chi + sigma^2 plane
+    assert serve.estimate_bytes(_envelope()) >= 64 * 32 * (16 + 4 + 48 + 4)
 
 
 def test_first_come_first_served_within_the_budget():
     reqs = [_field(Nz=int(Nz), steps=int(s)) for Nz, s in zip([64, 256, 64, 128, 512, 64, 128, 256],
                                                                 [5, 40, 3, 17, 9, 1, 33, 2])]
+    reqs.insert(3, _envelope(steps=11))
     sizes = [serve.estimate_bytes(r) for r in reqs]
     budget = max(sizes) + min(sizes)                 # the largest fits, but never next to a mid-sized one
-    srv = FakeServer(budget, chunk_steps=4, plan_workers=2)
-    tickets = [srv.submit(r, arrival=0.0) for r in reqs]
+    srv = serve.Server(budget, chunk_steps=4, plan_workers=2, dry_run=True)
+    tickets = [srv.submit(r) for r in reqs]
     srv.drain(timeout=60)
+    st = srv.stats()
+    admitted = [t.times()[1] for t in tickets]
+    assert admitted == sorted(admitted)              # admission in submission order: no overtaking
+    assert all(t.state == serve.DONE for t in tickets)
+    assert st["used_bytes"] == 0 and st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["peak_bytes"] <= budget
+    assert all(t.latency is not None and t.latency >= 0 for t in tickets)
     srv.close()
-    assert srv.admission_order == [t.id for t in tickets]          # no overtaking
-    assert srv.used == 0 and len(srv.done) == len(reqs)
-    assert srv.max_used <= budget
-    assert all(t.completed is not None and t._done_steps == t.request.steps for t in tickets)
 
 
 def test_a_request_larger_than_the_budget_is_refused():
-    srv = FakeServer(1000)
+    srv = serve.Server(1000, dry_run=True)
     with pytest.raises(nat.FdetdError):
         srv.submit(_field())
     srv.close()
 
 
+def test_a_failed_request_returns_its_budget_and_the_server_keeps_running():
+    # order 16 needs Nr > 8: the plan rejects Nr = 6, after admission
+    bad = _field(Nr=6, order=16)
+    good = [_field(steps=3), _envelope(steps=5), _field(Nz=128, steps=9)]
+    srv = serve.Server(10 * max(serve.estimate_bytes(r) for r in good), chunk_steps=4, dry_run=True)
+    tb = srv.submit(bad)
+    tg = [srv.submit(r) for r in good]
+    with pytest.raises(nat.FdetdError):
+        tb.wait(30)
+    for t in tg:
+        t.wait(30)
+    st = srv.stats()
+    assert tb.state == serve.FAILED and all(t.state == serve.DONE for t in tg)
+    assert st["failed"] == 1 and st["completed"] == 3 and st["used_bytes"] == 0
+    srv.close()
+
+
+def test_destroy_finishes_what_was_submitted():
+    srv = serve.Server(1 << 30, chunk_steps=2, dry_run=True)
+    tickets = [srv.submit(_field(steps=s)) for s in (3, 8, 5)]
+    srv.close()                                      # joins after every submitted request is done
+    assert srv.handle is None
+
+
+class _T:
+    def __init__(self, lat):
+        self.latency = lat
+
+
 def test_latency_statistics():
-    tickets = []
-    for i, lat in enumerate([1.0, 2.0, 3.0, 4.0, 100.0]):
-        t = serve.Ticket(i, None, arrival=10.0)
-        t.completed = 10.0 + lat
-        tickets.append(t)
+    tickets = [_T(x) for x in [1.0, 2.0, 3.0, 4.0, 100.0]]
     s = serve.latency_stats(tickets)
     assert s["count"] == 5 and s["p50_s"] == 3.0 and s["max_s"] == 100.0
     assert s["p99_s"] == pytest.approx(np.percentile([1, 2, 3, 4, 100], 99))
-    assert serve.latency_stats([serve.Ticket(0, None, 0.0)]) == {}
+    assert serve.latency_stats([_T(None)]) == {"count": 0}
