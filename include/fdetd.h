@@ -151,6 +151,20 @@ int fdetd_step_host(fdetd_plan_t plan, void* host_fields, const void* host_J, in
  * of that step is undefined).  Clears the recorded timeout.
  */
 int fdetd_plan_status(fdetd_plan_t plan, void* stream);
+/* The same report under the name of the stream-status call: synchronise `stream`, return the plan's
+ * device-side failure (FDETD_ERR_TIMEOUT / FDETD_ERR_CUDA) or FDETD_OK. */
+int fdetd_stream_status(fdetd_plan_t plan, void* stream);
+
+/*
+ * fdetd_plan_set_wait_limit - polls before a bounded mbarrier wait of this plan's
+ * tensor-core kernels gives up (polls < 0 restores the default of 2^26; 0 makes every
+ * wait give up at once).  A limit of 0 drives the timeout path on a healthy pipeline:
+ * the next fdetd_step's kernels stop at their first wait, drain what they issued,
+ * release their tensor memory and return, and fdetd_plan_status reports
+ * FDETD_ERR_TIMEOUT; the device context stays usable.  FDETD_ERR_UNSUPPORTED for the
+ * CUDA-core precisions (they have no pipeline waits).  Takes effect at the next step.
+ */
+int fdetd_plan_set_wait_limit(fdetd_plan_t plan, long long polls);
 
 /* Bytes of device memory the plan holds (tables + scratch). */
 size_t fdetd_plan_device_bytes(fdetd_plan_t plan);

@@ -11,7 +11,11 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
 
 
 class FdetdError(RuntimeError):
-    pass
+    """A library call failed; `code` is its FDETD_ERR_* value."""
+
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 def lib_path():
@@ -45,6 +49,8 @@ def lib():
     L.fdetd_plan_destroy.argtypes = [c_vp]
     L.fdetd_plan_set_profiling.argtypes = [c_vp, c_int]
     L.fdetd_plan_status.argtypes = [c_vp, c_vp]
+    L.fdetd_stream_status.argtypes = [c_vp, c_vp]
+    L.fdetd_plan_set_wait_limit.argtypes = [c_vp, ctypes.c_longlong]
     L.fdetd_plan_kernel_times.argtypes = [c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]
     L.fdetd_host_tables.argtypes = [c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, dp, dp, dp, dp, dp, dp,
                                     u8p, u8p, dp, dp, dp]
@@ -89,7 +95,7 @@ def _check(rc):
     if rc != 0:
         buf = ctypes.create_string_buffer(512)
         lib().fdetd_last_error(buf, 512)
-        raise FdetdError(f"fdetd error {rc}: {buf.value.decode(errors='replace')}")
+        raise FdetdError(f"fdetd error {rc}: {buf.value.decode(errors='replace')}", rc)
 
 
 def _stream_handle(stream):
@@ -127,6 +133,10 @@ class FdetdPlan:
     def status(self, stream=None):
         """Synchronise and raise FdetdError if an earlier step failed on the device."""
         _check(lib().fdetd_plan_status(self.handle, _stream_handle(stream)))
+
+    def set_wait_limit(self, polls=-1):
+        """Polls before a tensor-core pipeline wait gives up (< 0: default; 0: at once, drives the timeout path)."""
+        _check(lib().fdetd_plan_set_wait_limit(self.handle, int(polls)))
 
     def set_profiling(self, on=True):
         _check(lib().fdetd_plan_set_profiling(self.handle, int(on)))
@@ -473,6 +483,10 @@ class FdetdBatch:
 
     def launch(self, stream=None):
         _check(lib().fdetd_batch_launch(self.handle, _stream_handle(stream)))
+
+    def set_wait_limit(self, polls=-1):
+        """Polls before a tensor-core pipeline wait gives up (< 0: default; 0: at once, drives the timeout path)."""
+        _check(lib().fdetd_plan_set_wait_limit(self.handle, int(polls)))
 
     def set_profiling(self, on=True):
         """Record stage-timing events into the graph at the next capture (drops the captured graph)."""

@@ -635,6 +635,15 @@ extern "C" int fdetd_plan_status(fdetd_plan_t p, void* stream) {
   return FDETD_OK;
 }
 
+extern "C" int fdetd_stream_status(fdetd_plan_t p, void* stream) { return fdetd_plan_status(p, stream); }
+
+extern "C" int fdetd_plan_set_wait_limit(fdetd_plan_t p, long long polls) {
+  if (!p) return fail(FDETD_ERR_ARG, "plan is null");
+  if (!p->tc) return fail(FDETD_ERR_UNSUPPORTED, "only the tensor-core pipelines have bounded waits");
+  tc_set_wait_limit(p->tc, polls);
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_plan_set_profiling(fdetd_plan_t p, int on) {
   if (!p) return fail(FDETD_ERR_ARG, "plan is null");
   prof_collect(p);

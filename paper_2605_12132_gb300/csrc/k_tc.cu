@@ -46,7 +46,7 @@ namespace fdetd {
 
 namespace {
 
-constexpr long kSpinLimit = 1L << 26;
+constexpr long long kSpinLimit = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -70,10 +70,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity.  Returns false on timeout (and raises the
-// abort flag) or as soon as another role has raised it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  for (long it = 0; it < kSpinLimit; ++it) {
+// Bounded wait for the phase with the given parity: at most `spin` polls (a kernel parameter, kSpinLimit
+// unless a plan sets another limit).  Returns false on timeout (and raises the abort flag) or as soon as
+// another role has raised it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, long long spin) {
+  for (long long it = 0; it < spin; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255) == 255 && *abort) return false;
   }
@@ -82,7 +83,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 }
 // Bounded wait that ignores the abort flag (draining in-flight copies before exit).
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
-  for (long it = 0; it < kSpinLimit; ++it)
+  for (long long it = 0; it < kSpinLimit; ++it)
     if (mbar_try(bar, parity)) return;
 }
 
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
         const int s = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
         // all 128 converter threads take the same decision, so none is left behind at a barrier
-        const bool ok = bar_and_128(mbar_wait(&sb->fullS[s], ph, abort));
+        const bool ok = bar_and_128(mbar_wait(&sb->fullS[s], ph, abort, gp.spin));
         if (!ok) {
           if (threadIdx.x == 0) record_error(I.err, 11);
           live = false;
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
       const GInst& I = gp.inst[tl.x];
       const int b = NBUF == 2 ? (it & 1) : 0;
       const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
-      if (!mbar_wait(&sb->tfull[b], use & 1u, abort)) {
+      if (!mbar_wait(&sb->tfull[b], use & 1u, abort, gp.spin)) {
         if (lane == 0) record_error(I.err, 14);
         break;
       }
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
         const int s = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
         bool ok = true;
-        if (lane == 0) ok = mbar_wait(&sb->empty[s], ph ^ 1u, abort);
+        if (lane == 0) ok = mbar_wait(&sb->empty[s], ph ^ 1u, abort, gp.spin);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) record_error(I.err, 12);
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
         const int T = proj_blocks(g, ob, bl) * nks;
         const int b = NBUF == 2 ? (it & 1) : 0;
         const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
-        if (!mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort)) {
+        if (!mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort, gp.spin)) {
           record_error(I.err, 15);
           break;
         }
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
           const uint32_t ph = (uint32_t)(q / S) & 1u;
-          if (!mbar_wait(&sb->fullA[s], ph, abort) || !mbar_wait(&sb->fullB[s], ph, abort)) {
+          if (!mbar_wait(&sb->fullA[s], ph, abort, gp.spin) || !mbar_wait(&sb->fullB[s], ph, abort, gp.spin)) {
             record_error(I.err, 13);
             live = false;
             break;
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
       const GInst& I = gp.inst[tl.x];
       const int b = NBUF == 2 ? (it & 1) : 0;
       const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
-      if (!mbar_wait(&sb->tfull[b], use & 1u, abort)) {
+      if (!mbar_wait(&sb->tfull[b], use & 1u, abort, gp.spin)) {
         if (lane == 0) record_error(I.err, 24);
         break;
       }
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
           const uint32_t ph = (uint32_t)(q / S) & 1u;
-          if (!mbar_wait(&sb->empty[s], ph ^ 1u, abort)) {
+          if (!mbar_wait(&sb->empty[s], ph ^ 1u, abort, gp.spin)) {
             record_error(I.err, 21);
             live = false;
             break;
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         const int T = back_blocks(g, fb, bl) * ks;
         const int b = NBUF == 2 ? (it & 1) : 0;
         const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
-        if (!mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort)) {
+        if (!mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort, gp.spin)) {
           record_error(I.err, 25);
           break;
         }
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
           const uint32_t ph = (uint32_t)(q / S) & 1u;
-          if (!mbar_wait(&sb->fullB[s], ph, abort)) {
+          if (!mbar_wait(&sb->fullB[s], ph, abort, gp.spin)) {
             record_error(I.err, 23);
             live = false;
             break;
@@ -758,6 +759,7 @@ struct TcPlan {
   int* d_err = nullptr;  // owned by the caller's plan
   size_t bytes = 0;
   TcConfig cfg;
+  long long spin = -1;   // pipeline wait limit of the single-instance launches (< 0: kSpinLimit)
   // one-instance groups used by tc_project / tc_backproject, without (0) and with (1) a current:
   // the tile tables depend only on the shapes, the pointers are kernel parameters
   TcGroup* self[2] = {nullptr, nullptr};
@@ -1131,6 +1133,7 @@ cudaError_t tc_group_create(TcGroup** out, TcPlan* const* plans, const void* con
     }
   }
   G->params.count = count;
+  G->params.spin = kSpinLimit;
   cudaError_t e = build_tiles(G);
   if (e != cudaSuccess) {
     tc_group_destroy(G);
@@ -1166,6 +1169,7 @@ static cudaError_t self_group(TcPlan* t, const void* fields, const void* J, void
     if (e != cudaSuccess) return e;
   }
   GroupParams& gp = t->self[h]->params;
+  gp.spin = t->spin < 0 ? kSpinLimit : t->spin;
   GInst& I = gp.inst[0];
   const bool moved = I.fields != (float2*)fields || I.J != (const float2*)J;
   I.fields = (float2*)fields;
@@ -1194,8 +1198,11 @@ cudaError_t tc_backproject(TcPlan* t, void* fields, cudaStream_t st) {
   TcGroup* G = t->self[t->last];
   if (!G) return cudaErrorInvalidValue;
   G->params.inst[0].fields = (float2*)fields;
+  G->params.spin = t->spin < 0 ? kSpinLimit : t->spin;
   return launch_backproject(G, st);
 }
+
+void tc_set_wait_limit(TcPlan* t, long long polls) { t->spin = polls < 0 ? -1 : polls; }
 
 int tc_launches_per_step(const TcPlan*) { return 2; }
 

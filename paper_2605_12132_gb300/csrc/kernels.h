@@ -120,6 +120,7 @@ struct GroupParams {
   CUtensorMap fmap[kMaxGroupInstances];  // FP32 views of the fields (rows of 2 n floats), 64 x 64 boxes
   CUtensorMap jmap[kMaxGroupInstances];  // the same for J (unused entries zero)
   int count;
+  long long spin;                         // polls before a pipeline wait gives up (kSpinLimit unless set)
 };
 // Tile shapes and schedules of the persistent kernels (chosen by the autotuner):
 // tn_p / tn_b = N tile of the projection / back-projection (128 or 256); sched = tile order
@@ -147,6 +148,9 @@ cudaError_t tc_prepare(TcPlan* p, const void* fields, const void* J, void* coef)
 cudaError_t tc_project(TcPlan* p, const void* fields, const void* J, void* coef, cudaStream_t st);
 cudaError_t tc_backproject(TcPlan* p, void* fields, cudaStream_t st);
 int tc_launches_per_step(const TcPlan* p);
+// polls before a pipeline wait of this plan's single-instance launches gives up (< 0: the default limit;
+// 0: every wait gives up at once, which drives the timeout path on a healthy pipeline)
+void tc_set_wait_limit(TcPlan* p, long long polls);
 // grouped launches over up to kMaxGroupInstances instances of one precision
 cudaError_t tc_group_create(TcGroup** out, TcPlan* const* plans, const void* const* fields, const void* const* J,
                             int count, const TcConfig& cfg);
