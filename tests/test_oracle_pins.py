@@ -284,3 +284,64 @@ def test_vacuum_pulse_group_velocity():
     # the moving part carries all but a (lambda / w0)^2-small static fraction of the energy, and keeps it
     assert 0.99 < d1[win].sum() / d0.sum() < 1.0
     assert abs(d2[win].sum() / d1[win].sum() - 1) < 1e-3
+
+
+def test_vacuum_beam_waist_and_gouy_phase():
+    # A Gaussian pulse launched at its focus (flat phase front, m = 1, x-polarised, w0 = 2.5, tau = 6
+    # wavelengths) follows the paraxial beam of Sec. 5.1's vacuum test: the transverse intensity width grows as
+    # w(t) = w0 sqrt(1 + (t / z_R)^2), z_R = k w0^2 / 2, averaged over the pulse's spectral power, and the
+    # on-axis phase of the carrier's kz column lags a plane wave of the same discrete symbol by the Gouy phase
+    # arctan(t / z_R).  Both within the paraxial error (lambda / (pi w0))^2 = 1.6%.  Checked at t = z_R / 2 and
+    # t = z_R on the kz columns of the carrier band (Parseval: the z-summed intensity is the sum over kz).
+    from paper_2605_12132_gb300.inputs import pulse_fields
+    Nz, Nr, order, dz, dr = 384, 48, 16, 1 / 8, 1 / 4
+    dt, w0, tau, m = dz, 2.5, 6.0, 1
+    rad = mx.Radial(Nr, order, dr, m)
+    F = mx.fill_axis(pulse_fields(Nz, Nr, dz, dr, w0, tau, zc=24.0), rad)
+    q0 = int(round(Nz * dz))                       # kz = 2 pi
+    dq = np.arange(-12, 13)
+    band = [q0 + d for d in dq] + [Nz - q0 - d for d in dq]
+    zR = np.pi * w0 ** 2
+    n1 = int(round(zR / 2 / dt))
+    cols = mx.step_spectral(F, None, Nz, Nr, m, order, dz, dr, dt, nsteps=[n1, 2 * n1], kz_subset=band, method="eig")
+    Fh = np.fft.fft(F, axis=1)
+
+    def width(col):
+        I = sum(np.abs(col(q)[1]) ** 2 for q in band)   # E_theta: primary grid, |E_theta| = |E_x| on the axis plane
+        return np.sqrt(2 * (rad.rho ** 3 * I).sum() / (rad.rho * I).sum())
+
+    k = 2 * np.pi * (q0 + dq) / (Nz * dz)
+    power = np.exp(-(k - 2 * np.pi) ** 2 * tau ** 2 / 2)   # spectral power of the Gaussian envelope
+    sp, _ = mx.z_symbols(Nz, order, dz)
+    kappa = abs(sp[q0])
+    assert abs(width(lambda q: Fh[:, q, :]) / w0 - 1) < 2e-3
+    for n, c in zip((n1, 2 * n1), cols):
+        t = n * dt
+        w_exp = w0 * np.sqrt((power * (1 + (2 * t / (k * w0 ** 2)) ** 2)).sum() / power.sum())
+        assert abs(width(lambda q: c[q]) / w_exp - 1) < 1e-2, (t, width(lambda q: c[q]), w_exp)
+        gouy = np.angle(c[q0][1][0] / Fh[1, q0, 0] * np.exp(1j * kappa * t))
+        expect = -np.arctan(t / (kappa * w0 ** 2 / 2))
+        assert abs(gouy - expect) < 0.02 * abs(expect), (t, gouy, expect)
+
+
+def test_energy_drift_converges_with_radial_resolution():
+    # With J = 0 the discrete energy W is not exactly conserved (the mirror folds of D^+ and D^- near the axis
+    # are not exact negative transposes), but for a field smooth under the mode's parity the relative drift
+    # over a fixed time falls at second order in dr (the energy-versus-resolution study of Sec. 5.1):
+    # measured 1.3e-4, 3.2e-5, 8.1e-6 for dr = 1/4, 1/8, 1/16 (m = 1 pulse, order 8, t = 4 wavelengths).
+    from paper_2605_12132_gb300.inputs import pulse_fields
+    order, m, Nz, dz, R, T = 8, 1, 64, 1 / 4, 8.0, 4.0
+    dt = dz / 2
+    drift = []
+    for dr in (1 / 4, 1 / 8, 1 / 16):
+        Nr = int(R / dr)
+        rad = mx.Radial(Nr, order, dr, m)
+        F = mx.fill_axis(pulse_fields(Nz, Nr, dz, dr, 2.0, 3.0, zc=8.0), rad)
+        for f in (0, 4, 5):
+            F[f, :, 0] = 0
+        G = mx.step_spectral(F, None, Nz, Nr, m, order, dz, dr, dt, nsteps=int(round(T / dt)), method="eig")
+        W0, W1 = dg.energy(F, rad, dz), dg.energy(G, rad, dz)
+        drift.append(abs(W1 - W0) / W0)
+    r1, r2 = drift[0] / drift[1], drift[1] / drift[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, drift
+    assert drift[2] < 2e-5, drift
