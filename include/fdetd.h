@@ -75,7 +75,9 @@ typedef struct fdetd_taylor_s* fdetd_taylor_t;
  * (even, 2..32) in z and rho (Eq. spatial_derivativeSt), the parity-dependent
  * axis extensions of Eqs. spatialAM_derivativeS/A, the B_z axis value of
  * Sec. 2.4, taps beyond the outer radius dropped (Sec. 2.2), periodic z.
- * Nz >= 2 (the z transform takes a power of two, 64..8192), Nr >= order/2 + 2, M >= 0.
+ * Nz = 64 k in 64..8192 with no prime factor above 7 (FDETD_ERR_UNSUPPORTED otherwise; FP64 takes
+ * powers of two up to 4096 and other lengths while the five columns of a family fit in shared
+ * memory, about 2500), Nr >= order/2 + 2, M >= 0.
  * The radial eigen-decompositions, the omega table and the phase factors are
  * computed in FP64 on the host; device tables are allocated here and owned by
  * the plan.  Blocking; not stream-ordered.
@@ -399,13 +401,20 @@ int fdetd_host_coeffs(int kind, int order, double* out);
 
 /*
  * fdetd_host_spectral_order - host-only: the order in which the spectral kernel stores its per-kz
- * tables (phase records and z symbols).  Its in-place z transform (radix 8 for FP32 and the split-bf16
- * precisions, radix 4 for FP64, the leftover factor as the first stage, decimation in frequency)
- * leaves kz digit-reversed; the record of output position b * RL + r (RL the last stage's radix) sits
- * at table index r * (Nz / RL) + b.  kz: Nz ints, kz[i] = the kz index of table entry i.
- * precision: FDETD_PREC_*.  FDETD_ERR_ARG unless Nz is a power of two >= 2 and kz is non-null.
+ * tables (phase records and z symbols).  Its in-place z transform (decimation in frequency with the
+ * stage radices of fdetd_host_spectral_radices) leaves kz in mixed-radix digit-reversed order; the
+ * record of output position b * RL + r (RL the last stage's radix) sits at table index
+ * r * (Nz / RL) + b.  kz: Nz ints, kz[i] = the kz index of table entry i.  precision: FDETD_PREC_*.
+ * FDETD_ERR_ARG unless Nz >= 2 has no prime factor above 7 and kz is non-null.
+ *
+ * fdetd_host_spectral_radices - host-only: the stage radices of the z transform, first to last, in
+ * rad[0..15]: for Nz = 2^a the leftover factor 2^(a mod 3) (FP64: 2^(a mod 2)) first when it is not 1,
+ * then radix 8 (FP64: 4); for other 7-smooth Nz the factors 7, 5, 3 first, then the power-of-two part
+ * the same way.  Returns the number of stages, 0 when Nz has a prime factor above 7, -FDETD_ERR_ARG for
+ * a null rad or Nz < 2.
  */
 int fdetd_host_spectral_order(int Nz, int precision, int* kz);
+int fdetd_host_spectral_radices(int Nz, int precision, int* rad);
 
 /*
  * envelope_plan - exponential laser-envelope propagator of Sec. 4.2, mode m = 0:

@@ -25,6 +25,7 @@ from ._native import (  # noqa: F401
     fdetd_destagger,
     fdetd_host_coeffs,
     fdetd_host_spectral_order,
+    fdetd_host_spectral_radices,
     fdetd_host_tables,
     fdetd_plan,
     fdetd_plan_modes,

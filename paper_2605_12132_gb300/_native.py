@@ -56,6 +56,7 @@ def lib():
                                     u8p, u8p, dp, dp, dp]
     L.fdetd_host_coeffs.argtypes = [c_int, c_int, dp]
     L.fdetd_host_spectral_order.argtypes = [c_int, c_int, c_vp]
+    L.fdetd_host_spectral_radices.argtypes = [c_int, c_int, ctypes.POINTER(c_int)]
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_step_absorbing.argtypes = [c_vp, c_vp, c_vp, c_vp, c_int, c_vp]
@@ -357,6 +358,15 @@ def fdetd_host_spectral_order(Nz, precision="bf16x6"):
     out = np.zeros(Nz, dtype=np.int32)
     _check(lib().fdetd_host_spectral_order(Nz, PRECISIONS[precision], out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+def fdetd_host_spectral_radices(Nz, precision="bf16x6"):
+    """Host-only: the stage radices of the z transform, first to last (empty when Nz is not 7-smooth)."""
+    rad = (ctypes.c_int * 16)()
+    n = lib().fdetd_host_spectral_radices(Nz, PRECISIONS[precision], rad)
+    if n < 0:
+        _check(-n)
+    return [rad[k] for k in range(n)]
 
 
 def fdetd_host_coeffs(kind, order):

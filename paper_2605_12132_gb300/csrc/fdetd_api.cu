@@ -110,10 +110,14 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   *out = nullptr;
   if (!modes || nmodes < 1 || nmodes > 64) return fail(FDETD_ERR_ARG, "need 1..64 modes");
   if (precision < FDETD_PREC_FP64 || precision > FDETD_PREC_BF16X6) return fail(FDETD_ERR_ARG, "unknown precision");
-  if (!is_pow2(Nz) || Nz < 64 || Nz > 8192)
-    return fail(FDETD_ERR_UNSUPPORTED, "the z transform needs Nz a power of two in 64..8192");
+  int radices[MixedRadices::kMax];
+  if (Nz < 64 || Nz > 8192 || Nz % 64 || !spectral_radices(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, radices))
+    return fail(FDETD_ERR_UNSUPPORTED, "the z transform needs Nz = 64 k in 64..8192 with no prime factor above 7");
   const bool hasJ_max = true;
-  if (spectral_smem_bytes(Nz, precision, hasJ_max) > 227 * 1024)
+  if (is_pow2(Nz) ? spectral_smem_bytes(Nz, precision, hasJ_max) > 227 * 1024
+                  : spectral_mixed_smem_bytes(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, hasJ_max,
+                                              spectral_twiddles(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, nullptr,
+                                                                nullptr)) > 227 * 1024)
     return fail(FDETD_ERR_UNSUPPORTED, "Nz too long for the single-pass z transform at this precision");
   HostPlan hp;
   std::string msg;
@@ -130,7 +134,7 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   p->dr = dr;
   p->dt = dt;
   p->modes.assign(modes, modes + nmodes);
-  while ((1 << p->logNz) < Nz) ++p->logNz;
+  while ((1 << p->logNz) < Nz) ++p->logNz;   // log2 Nz (power-of-two lengths only)
   const int n = Nr, N3 = 3 * Nr;
   const bool fp64 = precision == FDETD_PREC_FP64;
   const bool tc = precision == FDETD_PREC_BF16X3 || precision == FDETD_PREC_BF16X6;
@@ -258,7 +262,7 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
     if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
     p->bytes += cbytes;
-    if (spectral_needs_source(Nz, prec_k, p->tw_count)) {
+    if (is_pow2(Nz) && spectral_needs_source(Nz, prec_k, p->tw_count)) {
       const size_t sbytes = (size_t)nmodes * 2 * 3 * n * Nz * (fp64 ? 16 : 8);
       if ((e = cudaMalloc(&p->d_src, sbytes)) != cudaSuccess) goto cuda_fail;
       p->bytes += sbytes;
@@ -322,9 +326,18 @@ static int stage_spectral(fdetd_plan_s* p, bool hasJ, cudaStream_t st) {
   const int prec = p->precision == FDETD_PREC_FP64 ? 0 : 1;
   const SpectralArgs sa = spectral_args(p, hasJ);
   prof_mark(p, 1, true, st);
-  // FP32 data with Nz up to 4096: the kernel specialised on Nz; otherwise the general one
-  cudaError_t e = prec == 1 && sa.zsymk ? launch_spectral32(sa, p->nmodes, p->tc != nullptr, st)
-                                        : launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
+  // FP32 data, Nz a power of two up to 4096: the kernel specialised on Nz; other powers of two: the general
+  // power-of-two kernel; other 7-smooth lengths: the mixed-radix kernel
+  cudaError_t e;
+  if (!is_pow2(p->Nz)) {
+    MixedRadices mr;
+    mr.nst = spectral_radices(p->Nz, prec, mr.rad);
+    e = launch_spectral_mixed(sa, mr, p->nmodes, prec, p->tc != nullptr, st);
+  } else if (prec == 1 && sa.zsymk) {
+    e = launch_spectral32(sa, p->nmodes, p->tc != nullptr, st);
+  } else {
+    e = launch_spectral(sa, p->nmodes, prec, p->tc != nullptr, st);
+  }
   prof_mark(p, 1, false, st);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("spectral: ") + cudaGetErrorString(e));
   return FDETD_OK;
@@ -698,9 +711,16 @@ extern "C" int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, do
 }
 
 extern "C" int fdetd_host_spectral_order(int Nz, int precision, int* kz) {
-  if (!kz || !is_pow2(Nz) || Nz < 2) return fail(FDETD_ERR_ARG, "Nz must be a power of two >= 2");
+  int rad[MixedRadices::kMax];
+  if (!kz || Nz < 2 || !spectral_radices(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, rad))
+    return fail(FDETD_ERR_ARG, "Nz must be >= 2 with no prime factor above 7");
   spectral_positions(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, kz);
   return FDETD_OK;
+}
+
+extern "C" int fdetd_host_spectral_radices(int Nz, int precision, int* rad) {
+  if (!rad || Nz < 2) return -FDETD_ERR_ARG;
+  return spectral_radices(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, rad);
 }
 
 extern "C" int fdetd_host_coeffs(int kind, int order, double* out) {

@@ -598,17 +598,37 @@ size_t spectral_smem_bytes(int Nz, int precision, bool hasJ) {
 }
 
 
-// Stage radices of the transform of length Nz = 2^logN: the leftover factor 2^(logN mod log2 R) first
-// (when it is not 1), then R (8 for FP32, 4 for FP64); a transform shorter than R is a single stage.
+// Stage radices of the transform, first to last.  Nz = 2^logN: the leftover factor 2^(logN mod log2 R) first
+// (when it is not 1), then R (8 for FP32, 4 for FP64); a transform shorter than R is a single stage.  Other
+// 7-smooth Nz: the odd factors first (7s, 5s, 3s), then the power-of-two part the same way, so the last stage
+// keeps the largest power-of-two radix.  Empty when Nz has a prime factor above 7.
 static std::vector<int> stage_radices(int Nz, int precision) {
   const int LR = precision == 0 ? 2 : 3;
+  std::vector<int> r;
+  int rest = Nz;
+  for (int p : {7, 5, 3})
+    while (rest % p == 0) {
+      r.push_back(p);
+      rest /= p;
+    }
   int logN = 0;
-  while ((1 << logN) < Nz) ++logN;
+  while ((1 << logN) < rest) ++logN;
+  if ((1 << logN) != rest) return std::vector<int>();
   const int nfull = logN / LR, rem = logN % LR;
-  if (!nfull) return std::vector<int>(1, 1 << logN);
-  std::vector<int> r(nfull, 1 << LR);
-  if (rem) r.insert(r.begin(), 1 << rem);
+  if (!nfull) {
+    if (rest > 1 || r.empty()) r.push_back(1 << logN);
+    return r;
+  }
+  if (rem) r.push_back(1 << rem);
+  for (int k = 0; k < nfull; ++k) r.push_back(1 << LR);
   return r;
+}
+
+int spectral_radices(int Nz, int precision, int* rad) {
+  const std::vector<int> r = stage_radices(Nz, precision);
+  if ((int)r.size() > MixedRadices::kMax) return 0;
+  for (size_t k = 0; k < r.size(); ++k) rad[k] = r[k];
+  return (int)r.size();
 }
 
 // Twiddle tables of the in-place stages in stage order: stage s < S-1 (radix R_s, stride L_s,

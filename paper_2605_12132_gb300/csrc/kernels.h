@@ -37,6 +37,17 @@ int spectral_twiddles(int Nz, int precision, double* re, double* im);
 // kz index held at each position of the forward transform's output (the order of the phase and z tables)
 void spectral_positions(int Nz, int precision, int* kz);
 bool spectral_needs_source(int Nz, int precision, int tw_count);
+// Stage radices of the z transform (first to last); spectral_radices fills them for any Nz = 2^a 3^b 5^c 7^d
+struct MixedRadices {
+  static constexpr int kMax = 16;
+  int nst;
+  int rad[kMax];
+};
+int spectral_radices(int Nz, int precision, int* rad);   // returns the number of stages (0: not 7-smooth)
+// Nz not a power of two (7-smooth): one kernel with runtime stage radices (k_spectral_mixed.cu)
+size_t spectral_mixed_smem_bytes(int Nz, int precision, bool hasJ, int tw_count);
+cudaError_t launch_spectral_mixed(const SpectralArgs& a, const MixedRadices& mr, int nmodes, int precision,
+                                  bool split_out, cudaStream_t st);
 // FP32 data, Nz = 2^k in 64..4096: the kernel specialised on Nz (k_spectral32.cu); cudaErrorNotSupported
 // for other lengths
 bool spectral32_supported(int Nz);

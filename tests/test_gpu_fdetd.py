@@ -118,7 +118,7 @@ def test_zero_steps_and_null_current():
 
 def test_argument_errors():
     with pytest.raises(fd.FdetdError):
-        fd.fdetd_plan_modes(100, 32, [0], 8, 0.1, 0.1, 0.1)          # Nz not a power of two
+        fd.fdetd_plan_modes(100, 32, [0], 8, 0.1, 0.1, 0.1)          # Nz not a multiple of 64
     with pytest.raises(fd.FdetdError):
         fd.fdetd_plan_modes(64, 32, [0], 7, 0.1, 0.1, 0.1)           # odd order
     with pytest.raises(fd.FdetdError):
@@ -200,3 +200,27 @@ def test_full_size_invariants(prec):
         tol = TOL[prec] * nsteps * stencil * fmax
         assert np.abs(dg.div_E(got[i], rad, w.order, w.dz) - (dE0 - nsteps * w.dt * dJ)).max() < tol
         assert np.abs(dg.div_B(got[i], rad, w.order, w.dz) - dB0).max() < tol
+
+
+@pytest.mark.parametrize("prec", ALL)
+@pytest.mark.parametrize("Nz", [192, 320, 448, 576])
+def test_parity_non_power_of_two_nz(prec, Nz):
+    # z lengths 64 k with odd factors 3, 5, 7, 9: the mixed-radix transform (radix 3, 5, 7 stages before the
+    # power-of-two ones), full field against the oracle after 2 steps, current on, modes 0 and 2
+    rng = np.random.default_rng(Nz)
+    Nr, modes, order, dz, dr, dt = 40, [0, 2], 8, 1 / 16, 1 / 4, 1 / 16
+    F = zero_axis(rng.standard_normal((2, 6, Nz, Nr)) + 1j * rng.standard_normal((2, 6, Nz, Nr)))
+    J = 0.3 * (rng.standard_normal((2, 3, Nz, Nr)) + 1j * rng.standard_normal((2, 3, Nz, Nr)))
+    nsteps = 2
+    got = _run(prec, F, J, Nz, Nr, modes, order, dz, dr, dt, nsteps)
+    ref = _oracle(F, J, Nz, Nr, modes, order, dz, dr, dt, nsteps)
+    for i, m in enumerate(modes):
+        rows = field_report(got[i], ref[i], nd=order // 2)
+        print("\n" + format_report(rows, f"{prec} Nz={Nz} m={m}"))
+        check_report(rows, TOL[prec] * nsteps, TOL_WEAK[prec] * nsteps, label=f"{prec} Nz={Nz} m={m}")
+
+
+def test_unsupported_z_lengths_are_refused():
+    for Nz in (100, 64 * 11, 4093):
+        with pytest.raises(fd.FdetdError):
+            fd.fdetd_plan_modes(Nz, 32, [0], 8, 0.1, 0.1, 0.1, precision="fp32")

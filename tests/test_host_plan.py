@@ -172,13 +172,11 @@ def test_taylor_bands_reproduce_oracle_radial_operators(m, order):
     assert np.allclose(axis[1], rad.axis_scalar[:ND]) and np.all(rad.axis_scalar[ND:] == 0)
 
 
-def _dif_model(x, LR):
-    """In-place decimation-in-frequency FFT with the leftover radix as the first stage (numpy model of the
-    spectral kernel's stage structure): returns the array of output positions."""
+def _dif_model(x, rad):
+    """In-place decimation-in-frequency FFT with the given stage radices (numpy model of the spectral kernels'
+    stage structure): returns the array of output positions and the last stage's radix."""
     N = len(x)
-    logN = N.bit_length() - 1
-    nfull, rem = divmod(logN, LR)
-    rad = [1 << logN] if not nfull else ([1 << rem] if rem else []) + [1 << LR] * nfull
+    assert int(np.prod(rad)) == N
     y = x.astype(complex).copy()
     M = N
     for R in rad:
@@ -193,7 +191,7 @@ def _dif_model(x, LR):
     return y, rad[-1]
 
 
-@pytest.mark.parametrize("Nz", [2, 4, 8, 16, 64, 128, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("Nz", [2, 4, 8, 16, 64, 128, 512, 1024, 2048, 4096, 96, 576, 640, 960, 1344, 3136, 4032])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
 def test_spectral_table_order_is_the_transform_output_order(Nz, prec):
     # the per-kz tables must list, entry by entry, the kz the in-place forward transform leaves at the
@@ -201,10 +199,20 @@ def test_spectral_table_order_is_the_transform_output_order(Nz, prec):
     _lib_or_skip()
     kz = native.fdetd_host_spectral_order(Nz, prec)
     assert sorted(kz.tolist()) == list(range(Nz))
+    rad = native.fdetd_host_spectral_radices(Nz, prec)
+    assert int(np.prod(rad)) == Nz and all(r in (2, 3, 4, 5, 7, 8) for r in rad)
     x = np.random.default_rng(Nz).standard_normal(Nz) + 1j * np.random.default_rng(Nz + 1).standard_normal(Nz)
-    y, RL = _dif_model(x, 2 if prec == "fp64" else 3)
+    y, RL = _dif_model(x, rad)
     X = np.fft.fft(x)
     nb = Nz // RL
     for i in range(Nz):
         p = (i % nb) * RL + i // nb
         assert abs(y[p] - X[kz[i]]) < 1e-9 * np.abs(X).max(), (i, p, kz[i])
+
+
+def test_spectral_radices_reject_large_prime_factors():
+    _lib_or_skip()
+    assert native.fdetd_host_spectral_radices(4093, "bf16x6") == []
+    assert native.fdetd_host_spectral_radices(64 * 11, "fp32") == []
+    assert native.fdetd_host_spectral_radices(4096, "fp32") == [8, 8, 8, 8]
+    assert native.fdetd_host_spectral_radices(4096, "fp64") == [4] * 6
