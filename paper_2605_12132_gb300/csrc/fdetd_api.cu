@@ -883,8 +883,10 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
         return fail(FDETD_ERR_CUDA, "batch: timing event creation failed");
       }
   }
+  // recorded as event nodes of the graph (external), so that each replay stamps them
   auto mark = [&](int step, int k) -> cudaError_t {
-    return b->profiling ? cudaEventRecord(b->stage_ev[(size_t)4 * step + k], cap) : cudaSuccess;
+    return b->profiling ? cudaEventRecordWithFlags(b->stage_ev[(size_t)4 * step + k], cap, cudaEventRecordExternal)
+                        : cudaSuccess;
   };
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = FDETD_OK;

@@ -96,20 +96,29 @@ class Ticket:
         self.server, self.request, self._c_req, self._keep = server, request, c_req, keep
         self.id = None
         self.arrival = None
+        self._final = None      # (state, latency) once done or failed: kept after the server is closed
+
+    def _poll(self):
+        if self._final is not None:
+            return self._final
+        if not self.server.handle:
+            return (QUEUED, None)
+        lat = ctypes.c_double(-1.0)
+        st = ctypes.c_int(0)
+        _bind().fdetd_server_poll(self.server.handle, self.id, ctypes.byref(st), ctypes.byref(lat))
+        if st.value in (DONE, FAILED):
+            self._final = (st.value, lat.value if st.value == DONE else None)
+            return self._final
+        return (st.value, None)
 
     @property
     def state(self):
-        st = ctypes.c_int(0)
-        _bind().fdetd_server_poll(self.server.handle, self.id, ctypes.byref(st), None)
-        return st.value
+        return self._poll()[0]
 
     @property
     def latency(self):
         """Completion minus submission time in seconds, None until done."""
-        lat = ctypes.c_double(-1.0)
-        st = ctypes.c_int(0)
-        _bind().fdetd_server_poll(self.server.handle, self.id, ctypes.byref(st), ctypes.byref(lat))
-        return lat.value if st.value == DONE else None
+        return self._poll()[1]
 
     def times(self):
         t = (ctypes.c_double * 3)()
@@ -208,7 +217,11 @@ class Server:
                 raise TimeoutError("server did not drain in time")
 
     def close(self):
+        """Finish every submitted request, record each ticket's final state, then stop the server."""
         if self.handle:
+            self.drain(timeout=3600.0)
+            for t in self.tickets:
+                t._poll()
             _bind().fdetd_server_destroy(self.handle)
             self.handle = None
 
