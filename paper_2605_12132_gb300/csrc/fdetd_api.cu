@@ -262,7 +262,8 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
     if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
     p->bytes += cbytes;
-    if (is_pow2(Nz) && spectral_needs_source(Nz, prec_k, p->tw_count)) {
+    if (is_pow2(Nz) ? spectral_needs_source(Nz, prec_k, p->tw_count)
+                    : spectral_mixed_needs_source(Nz, prec_k, p->tw_count)) {
       const size_t sbytes = (size_t)nmodes * 2 * 3 * n * Nz * (fp64 ? 16 : 8);
       if ((e = cudaMalloc(&p->d_src, sbytes)) != cudaSuccess) goto cuda_fail;
       p->bytes += sbytes;

@@ -203,10 +203,16 @@ __device__ __forceinline__ void unpack(const ZSymF& z, df& spr, df& spi, df& smr
   spr = z.spr; spi = z.spi; smr.h = -z.spr.h; smr.l = -z.spr.l; smi = z.spi;
 }
 
+// Kernel modes: FUSED transforms the family's field and current columns together; SOURCE transforms only
+// the current columns and writes the midpoint source term -dt exp(dt M / 2) x_J / Nz per table index; MAIN
+// transforms the field columns and adds that precomputed source (when five columns do not fit in shared
+// memory).
+enum { MFUSED = 0, MMAIN = 1, MSOURCE = 2 };
+
 // the last forward stage (radix RL, stride 1), the update of those RL kz and the first inverse stage
-template <int RL, int NT, typename T, typename K, typename PH, typename ZS, typename C>
+template <int RL, int MODE, int NT, typename T, typename K, typename PH, typename ZS, typename C>
 __device__ __forceinline__ void mfused(C* s, int Pc, int N, bool hasJ, int fam, const PH* phase, const ZS* zs, K lam,
-                                       T dt, T inv) {
+                                       T dt, T inv, const C* src, size_t sstride) {
   const int nb = N / RL;
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int p0 = b * RL;
@@ -221,7 +227,7 @@ __device__ __forceinline__ void mfused(C* s, int Pc, int N, bool hasJ, int fam, 
     for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int r = 0; r < RL; ++r) jv[c][r] = cmake<C>(0, 0);
-    if (hasJ) {
+    if (MODE == MFUSED && hasJ) {
       const int nj = fam == 0 ? 2 : 1;
       for (int c = 0; c < nj; ++c) {
 #pragma unroll
@@ -231,12 +237,18 @@ __device__ __forceinline__ void mfused(C* s, int Pc, int N, bool hasJ, int fam, 
     }
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
+      const int q = r * nb + b;
       K spr, spi, smr, smi, A1, A2;
       T B1, B2;
-      unpack(zs[r * nb + b], spr, spi, smr, smi);
-      unpack(phase[r * nb + b], A1, A2, B1, B2);
-      update_point<T, K, C>(v[0][r], v[1][r], v[2][r], jv[0][r], jv[1][r], hasJ, fam, lam, spr, spi, smr, smi, A1, A2,
-                            B1, B2, dt, inv);
+      unpack(zs[q], spr, spi, smr, smi);
+      unpack(phase[q], A1, A2, B1, B2);
+      update_point<T, K, C>(v[0][r], v[1][r], v[2][r], jv[0][r], jv[1][r], MODE == MFUSED && hasJ, fam, lam, spr,
+                            spi, smr, smi, A1, A2, B1, B2, dt, inv);
+      if (MODE == MMAIN && src) {
+        v[0][r] = cadd(v[0][r], src[q]);
+        v[1][r] = cadd(v[1][r], src[sstride + q]);
+        v[2][r] = cadd(v[2][r], src[2 * sstride + q]);
+      }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -248,17 +260,56 @@ __device__ __forceinline__ void mfused(C* s, int Pc, int N, bool hasJ, int fam, 
   __syncthreads();
 }
 
-template <int NT, typename T, typename K, typename PH, typename ZS, typename C>
-__device__ __forceinline__ void mfused_any(int RL, C* s, int Pc, int N, bool hasJ, int fam, const PH* phase,
-                                           const ZS* zs, K lam, T dt, T inv) {
-  switch (RL) {
-    case 2: mfused<2, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv); break;
-    case 3: mfused<3, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv); break;
-    case 4: mfused<4, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv); break;
-    case 5: mfused<5, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv); break;
-    case 7: mfused<7, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv); break;
-    default: mfused<8, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv); break;
+// SOURCE: the current columns' last forward stage and the source term -dt (x_J + B1 M x_J + B2 M^2 x_J) / Nz
+// per table index, to global memory
+template <int RL, int NT, typename T, typename K, typename PH, typename ZS, typename C>
+__device__ __forceinline__ void msource(const C* s, int Pc, int N, int fam, const PH* phase, const ZS* zs, K lam,
+                                        T dt, T inv, C* src, size_t sstride) {
+  const int nb = N / RL;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int p0 = b * RL;
+    C j0[RL], j1[RL];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      j0[r] = s[pad16(p0 + r)];
+      j1[r] = fam == 0 ? s[Pc + pad16(p0 + r)] : cmake<C>(0, 0);
+    }
+    dft_any<RL, false>(j0);
+    if (fam == 0) dft_any<RL, false>(j1);
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int q = r * nb + b;
+      K spr, spi, smr, smi, A1, A2;
+      T B1, B2;
+      unpack(zs[q], spr, spi, smr, smi);
+      unpack(phase[q], A1, A2, B1, B2);
+      // the update of the zero state with the current: x' = -dt (x_J + B1 M x_J + B2 M^2 x_J), then / Nz
+      C x0 = cmake<C>(0, 0), x1 = cmake<C>(0, 0), x2 = cmake<C>(0, 0);
+      update_point<T, K, C>(x0, x1, x2, j0[r], j1[r], true, fam, lam, spr, spi, smr, smi, A1, A2, B1, B2, dt, inv);
+      src[q] = x0;
+      src[sstride + q] = x1;
+      src[2 * sstride + q] = x2;
+    }
   }
+}
+
+template <int MODE, int NT, typename T, typename K, typename PH, typename ZS, typename C>
+__device__ __forceinline__ void mlast_any(int RL, C* s, int Pc, int N, bool hasJ, int fam, const PH* phase,
+                                          const ZS* zs, K lam, T dt, T inv, C* src, size_t sstride) {
+#define FDETD_MLAST(R)                                                                    \
+  if (MODE == MSOURCE)                                                                    \
+    msource<R, NT, T>(s, Pc, N, fam, phase, zs, lam, dt, inv, src, sstride);              \
+  else                                                                                    \
+    mfused<R, MODE, NT, T>(s, Pc, N, hasJ, fam, phase, zs, lam, dt, inv, src, sstride);
+  switch (RL) {
+    case 2: FDETD_MLAST(2) break;
+    case 3: FDETD_MLAST(3) break;
+    case 4: FDETD_MLAST(4) break;
+    case 5: FDETD_MLAST(5) break;
+    case 7: FDETD_MLAST(7) break;
+    default: FDETD_MLAST(8) break;
+  }
+#undef FDETD_MLAST
 }
 
 // the adjoint of stage 0 for the three field columns, to global memory (or the bf16 split pieces)
@@ -286,50 +337,65 @@ __device__ __forceinline__ void mstage0_out(const C* s, int Pc, int N, const C* 
     }
 }
 
+__host__ __device__ __forceinline__ constexpr int mixed_slots(int mode, bool hasJ) {
+  return mode == MFUSED ? (hasJ ? 5 : 3) : (mode == MMAIN ? 3 : 2);
+}
+// shared-memory bytes of one launch: the mode's column slots, then the staged twiddles (whole 16-byte copies)
+size_t mixed_bytes(int Nz, int precision, int mode, bool hasJ, int tw_staged) {
+  const size_t elt = precision == 0 ? 16 : 8, epc = 16 / elt;
+  return ((size_t)mixed_slots(mode, hasJ) * pad16(Nz) + ((size_t)tw_staged + epc - 1) / epc * epc) * elt;
+}
+
 __device__ __forceinline__ int column_of(int fam, int a) {
   if (fam == 0) return a < 2 ? a : (a == 2 ? 3 : a + 3);
   return a == 0 ? 2 : (a < 3 ? a + 3 : 8);
 }
 
-template <typename T, typename K, typename PH, typename ZS, int NT, bool SPLIT>
+template <typename T, typename K, typename PH, typename ZS, int NT, bool SPLIT, int MODE, bool TW_SMEM>
 __global__ void __launch_bounds__(NT) spectral_mixed_kernel(SpectralArgs args, MixedRadices mr) {
   typedef typename cplx<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int N = args.Nz, n = args.n, Pc = pad16(N);
   const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
-  const bool hasJ = args.hasJ != 0;
-  const int ncol = hasJ ? (fam == 0 ? 5 : 4) : 3;
-  const int slots = hasJ ? 5 : 3;
-  C* tws = s + (size_t)slots * Pc;
+  const bool hasJ = MODE == MFUSED && args.hasJ != 0;
+  const int ncol = MODE == MSOURCE ? (fam == 0 ? 2 : 1) : (hasJ ? (fam == 0 ? 5 : 4) : 3);
+  const int slots = mixed_slots(MODE, hasJ);
   const C* coef = reinterpret_cast<const C*>(args.coef);
   const C* twg = reinterpret_cast<const C*>(args.twiddle);
+  C* tws = s + (size_t)slots * Pc;
+  const C* tw = TW_SMEM ? tws : twg;
   constexpr int EPC = 16 / (int)sizeof(C);
   for (int i = threadIdx.x; i < ncol * (N / EPC); i += NT) {
     const int a = i / (N / EPC), e = (i - a * (N / EPC)) * EPC;
-    const C* col = coef + ((size_t)(md * 9 + column_of(fam, a)) * n + j) * N;
-    cp16(s + a * Pc + pad16(e), col + e);
+    const int c = MODE == MSOURCE ? (fam == 0 ? 6 + a : 8) : column_of(fam, a);
+    cp16(s + a * Pc + pad16(e), coef + ((size_t)(md * 9 + c) * n + j) * N + e);
   }
-  for (int i = threadIdx.x; i < (args.tw_count + EPC - 1) / EPC; i += NT) cp16(tws + i * EPC, twg + i * EPC);
+  if (TW_SMEM)
+    for (int i = threadIdx.x; i < (args.tw_count + EPC - 1) / EPC; i += NT) cp16(tws + i * EPC, twg + i * EPC);
   cp_wait_all();
   __syncthreads();
   const PH* phase = reinterpret_cast<const PH*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * N;
   const ZS* zs = reinterpret_cast<const ZS*>(args.zsym);
   const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
+  C* src = reinterpret_cast<C*>(args.src) + ((size_t)(md * 2 + fam) * 3 * n + j) * N;   // [md][fam][3][n][N]
+  const size_t sstride = (size_t)n * N;
   // forward stages but the last
   int L = N, off = 0;
   for (int st = 0; st + 1 < mr.nst; ++st) {
     const int R = mr.rad[st];
     L /= R;
-    mstage_any<false, NT>(R, s, Pc, ncol, N, L, tws + off);
+    mstage_any<false, NT>(R, s, Pc, ncol, N, L, tw + off);
     off += (R - 1) * L;
   }
-  mfused_any<NT, T>(mr.rad[mr.nst - 1], s, Pc, N, hasJ, fam, phase, zs, lam, (T)args.dt, (T)1 / (T)N);
+  mlast_any<MODE, NT, T>(mr.rad[mr.nst - 1], s, Pc, N, hasJ, fam, phase, zs, lam, (T)args.dt, (T)1 / (T)N,
+                         MODE == MMAIN && !args.src ? nullptr : src, sstride);
+  if (MODE == MSOURCE) return;
   // inverse stages in reverse order, stage 0's to global memory
   for (int st = mr.nst - 2; st >= 1; --st) {
     const int R = mr.rad[st];
     off -= (R - 1) * L;
-    mstage_any<true, NT>(R, s, Pc, 3, N, L, tws + off);
+    mstage_any<true, NT>(R, s, Pc, 3, N, L, tw + off);
     L *= R;
   }
   C* out = reinterpret_cast<C*>(args.coef);
@@ -341,31 +407,56 @@ __global__ void __launch_bounds__(NT) spectral_mixed_kernel(SpectralArgs args, M
     if (SPLIT) sc[a] = split_column(args.split_out, args.npieces, md, column_of(fam, a), j, args.split_kstages, N);
   }
   switch (mr.rad[0]) {
-    case 2: mstage0_out<2, NT, SPLIT>(s, Pc, N, tws, dst, sc); break;
-    case 3: mstage0_out<3, NT, SPLIT>(s, Pc, N, tws, dst, sc); break;
-    case 4: mstage0_out<4, NT, SPLIT>(s, Pc, N, tws, dst, sc); break;
-    case 5: mstage0_out<5, NT, SPLIT>(s, Pc, N, tws, dst, sc); break;
-    case 7: mstage0_out<7, NT, SPLIT>(s, Pc, N, tws, dst, sc); break;
-    default: mstage0_out<8, NT, SPLIT>(s, Pc, N, tws, dst, sc); break;
+    case 2: mstage0_out<2, NT, SPLIT>(s, Pc, N, tw, dst, sc); break;
+    case 3: mstage0_out<3, NT, SPLIT>(s, Pc, N, tw, dst, sc); break;
+    case 4: mstage0_out<4, NT, SPLIT>(s, Pc, N, tw, dst, sc); break;
+    case 5: mstage0_out<5, NT, SPLIT>(s, Pc, N, tw, dst, sc); break;
+    case 7: mstage0_out<7, NT, SPLIT>(s, Pc, N, tw, dst, sc); break;
+    default: mstage0_out<8, NT, SPLIT>(s, Pc, N, tw, dst, sc); break;
   }
 }
 
-template <typename T, typename K, typename PH, typename ZS, bool SPLIT>
-cudaError_t launch_m(const SpectralArgs& a, const MixedRadices& mr, int nmodes, cudaStream_t st) {
-  const size_t smem = spectral_mixed_smem_bytes(a.Nz, sizeof(T) == 8 ? 0 : 1, a.hasJ != 0, a.tw_count);
-  auto k = spectral_mixed_kernel<T, K, PH, ZS, 256, SPLIT>;
+template <typename T, typename K, typename PH, typename ZS, bool SPLIT, int MODE, bool TW_SMEM>
+cudaError_t launch_mm(const SpectralArgs& a, const MixedRadices& mr, int nmodes, cudaStream_t st) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const size_t smem = mixed_bytes(a.Nz, prec, MODE, MODE == MFUSED && a.hasJ, TW_SMEM ? a.tw_count : 0);
+  auto k = spectral_mixed_kernel<T, K, PH, ZS, 256, SPLIT, MODE, TW_SMEM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<dim3(a.n, 2, nmodes), 256, smem, st>>>(a, mr);
   return cudaGetLastError();
 }
 
+// the fused kernel when the family's columns and the twiddles fit in shared memory; otherwise the current's
+// source term first (SOURCE), then the field columns alone (MAIN), twiddles read through L1
+template <typename T, typename K, typename PH, typename ZS, bool SPLIT>
+cudaError_t launch_m(const SpectralArgs& a, const MixedRadices& mr, int nmodes, cudaStream_t st) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  if (mixed_bytes(a.Nz, prec, MFUSED, a.hasJ, a.tw_count) <= 227 * 1024)
+    return launch_mm<T, K, PH, ZS, SPLIT, MFUSED, true>(a, mr, nmodes, st);
+  if (a.hasJ) {
+    if (!a.src) return cudaErrorInvalidValue;
+    cudaError_t e = launch_mm<T, K, PH, ZS, SPLIT, MSOURCE, false>(a, mr, nmodes, st);
+    if (e != cudaSuccess) return e;
+    return launch_mm<T, K, PH, ZS, SPLIT, MMAIN, false>(a, mr, nmodes, st);
+  }
+  SpectralArgs b = a;
+  b.src = nullptr;
+  return launch_mm<T, K, PH, ZS, SPLIT, MMAIN, false>(b, mr, nmodes, st);
+}
+
 }  // namespace
 
+// Smallest shared-memory footprint the mixed-radix transform needs at this length: the three field columns
+// of the two-kernel path (twiddles through L1); the fused kernel is used whenever it fits.
 size_t spectral_mixed_smem_bytes(int Nz, int precision, bool hasJ, int tw_count) {
-  const size_t elt = precision == 0 ? 16 : 8;
-  const size_t epc = 16 / elt;
-  return ((size_t)(hasJ ? 5 : 3) * pad16(Nz) + (tw_count + epc - 1) / epc * epc) * elt;
+  (void)hasJ;
+  (void)tw_count;
+  return mixed_bytes(Nz, precision, MMAIN, false, 0);
+}
+
+bool spectral_mixed_needs_source(int Nz, int precision, int tw_count) {
+  return mixed_bytes(Nz, precision, MFUSED, true, tw_count) > 227 * 1024;
 }
 
 cudaError_t launch_spectral_mixed(const SpectralArgs& a, const MixedRadices& mr, int nmodes, int precision,

@@ -46,6 +46,7 @@ struct MixedRadices {
 int spectral_radices(int Nz, int precision, int* rad);   // returns the number of stages (0: not 7-smooth)
 // Nz not a power of two (7-smooth): one kernel with runtime stage radices (k_spectral_mixed.cu)
 size_t spectral_mixed_smem_bytes(int Nz, int precision, bool hasJ, int tw_count);
+bool spectral_mixed_needs_source(int Nz, int precision, int tw_count);
 cudaError_t launch_spectral_mixed(const SpectralArgs& a, const MixedRadices& mr, int nmodes, int precision,
                                   bool split_out, cudaStream_t st);
 // FP32 data, Nz = 2^k in 64..4096: the kernel specialised on Nz (k_spectral32.cu); cudaErrorNotSupported

@@ -105,7 +105,7 @@ extern "C" size_t fdetd_request_device_bytes(const fdetd_request* r) {
   const size_t elt = fp64 ? 16 : 8, cells = nm * Nz * n;
   size_t b = cells * 6 * elt + (r->J ? cells * 3 * elt : 0);              // resident fields and current
   b += cells * 9 * elt;                                                    // coefficient scratch
-  if (Nz > 4096) b += nm * 2 * 3 * n * Nz * elt;                           // source term of the long-z path
+  if (Nz > 4096 || (fp64 && Nz > 2048)) b += nm * 2 * 3 * n * Nz * elt;   // source term of the two-kernel path
   b += nm * 2 * n * Nz * (fp64 ? 32 : 16) + nm * 2 * n * 16;              // phase and eigenvalue tables
   b += Nz * 16 + Nz * 32 + 2 * (Nz + 64) * elt + 64;                        // z symbols, twiddles, flag
   if (r->precision == FDETD_PREC_BF16X3 || r->precision == FDETD_PREC_BF16X6) {

@@ -1,5 +1,7 @@
-"""Long z columns (two-kernel spectral path: the current's source term is transformed first, then the
-field columns alone) against the oracle on sampled kz columns, with and without a current."""
+"""Long z columns against the oracle on sampled kz columns, with and without a current: the two-kernel spectral
+paths (the current's source term transformed first, then the field columns alone) of the power-of-two transform
+(Nz = 8192; FP64 at 4096) and of the mixed-radix transform (FP64 at 3136 = 7^2 64 and 4032 = 7 3^2 64), and the
+fused mixed-radix kernel at long non-power-of-two lengths (3840, 2880)."""
 import numpy as np
 import pytest
 
@@ -21,7 +23,8 @@ TOL = {"fp64": 1e-12, "fp32": 1e-6, "bf16x6": 4e-6, "bf16x3": 2.5e-5}
 TOL_WEAK = {"fp64": 1e-11, "fp32": 3e-5, "bf16x6": 3e-5, "bf16x3": 1e-3}
 
 
-@pytest.mark.parametrize("prec,Nz", [("fp32", 8192), ("bf16x3", 8192), ("bf16x6", 8192), ("fp64", 4096)])
+@pytest.mark.parametrize("prec,Nz", [("fp32", 8192), ("bf16x3", 8192), ("bf16x6", 8192), ("fp64", 4096),
+                                     ("fp64", 4032), ("fp64", 3136), ("bf16x6", 3840), ("fp32", 2880)])
 @pytest.mark.parametrize("with_J", [True, False])
 def test_long_z_sampled_kz(prec, Nz, with_J):
     rng = np.random.default_rng(Nz + with_J)
