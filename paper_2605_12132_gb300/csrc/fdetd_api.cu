@@ -1124,6 +1124,7 @@ extern "C" int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, in
     b.cz1[t] = (float)(d1[t - 1] / dz);
   }
   b.k2 = (float)(2.0 * k0);
+  for (int n = 1; n <= 16; ++n) b.dt_over[n] = (float)(dt / n);
   *out = p;
   return FDETD_OK;
 }
@@ -1160,6 +1161,38 @@ static int envelope_taylor(envelope_plan_t p, float2* psi_a, float2* psi_t, cons
   return FDETD_OK;
 }
 
+// Whether the all-terms-in-one-launch kernel serves this plan (order 8, N_T = 4, Nz a multiple of its tile).
+static bool envelope_use_fused(envelope_plan_t p) {
+  return envelope_fused_supported(p->order, p->NT) && p->Nz % 32 == 0;
+}
+
+// n steps of the fused kernel between the caller's state and a plan buffer (the kernel reads halos of its
+// input, so input and output alternate), optionally damped around each step (absorbing layer); the result
+// ends in the caller's state.
+static int envelope_steps_fused(envelope_plan_t p, float2* psi, const float* chi, int nsteps, const float* sigma,
+                                float damp, cudaStream_t st) {
+  const size_t plane = (size_t)p->Nz * p->Nr;
+  float2* buf = p->d_buf;  // two planes: a, a~
+  float2* cur = psi;
+  float2* nxt = buf;
+  EnvArgs g = p->base;
+  g.chi = chi;
+  g.scale = 0.f;
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e = cudaSuccess;
+    if (sigma) e = launch_envelope_damp(cur, sigma, damp, plane, st);
+    if (e == cudaSuccess) e = launch_envelope_fused(g, cur, cur + plane, nxt, nxt + plane, p->NT, st);
+    if (e == cudaSuccess && sigma) e = launch_envelope_damp(nxt, sigma, damp, plane, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
+    std::swap(cur, nxt);
+  }
+  if (cur != psi) {
+    cudaError_t e = cudaMemcpyAsync(psi, cur, 2 * plane * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return FDETD_OK;
+}
+
 extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int nsteps, void* stream) {
   if (!p || !a || !chi) return fail(FDETD_ERR_ARG, "null argument");
   if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
@@ -1167,8 +1200,22 @@ extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int n
   cudaStream_t st = (cudaStream_t)stream;
   const size_t plane = (size_t)p->Nz * p->Nr;
   float2* psi_a = (float2*)a;
+  if (envelope_use_fused(p)) return envelope_steps_fused(p, psi_a, chi, nsteps, nullptr, 0.f, st);
   for (int s = 0; s < nsteps; ++s) {
     int rc = envelope_taylor(p, psi_a, psi_a + plane, chi, st);
+    if (rc) return rc;
+  }
+  return FDETD_OK;
+}
+
+extern "C" int envelope_step_terms(envelope_plan_t p, void* a, const float* chi, int nsteps, void* stream) {
+  if (!p || !a || !chi) return fail(FDETD_ERR_ARG, "null argument");
+  if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
+  if (((uintptr_t)a & 15) || ((uintptr_t)chi & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
+  const size_t plane = (size_t)p->Nz * p->Nr;
+  float2* psi_a = (float2*)a;
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = envelope_taylor(p, psi_a, psi_a + plane, chi, (cudaStream_t)stream);
     if (rc) return rc;
   }
   return FDETD_OK;
@@ -1186,6 +1233,7 @@ extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* 
   cudaError_t e = launch_envelope_chit(chi, sigma, p->d_chit, plane, st);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
   const float damp = (float)(-0.25 * p->dt);
+  if (envelope_use_fused(p)) return envelope_steps_fused(p, psi_a, p->d_chit, nsteps, sigma, damp, st);
   for (int s = 0; s < nsteps; ++s) {
     e = launch_envelope_damp(psi_a, sigma, damp, plane, st);
     if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
@@ -1197,7 +1245,9 @@ extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* 
   return FDETD_OK;
 }
 
-extern "C" int envelope_plan_launches_per_step(envelope_plan_t p) { return p ? p->NT : 0; }
+extern "C" int envelope_plan_launches_per_step(envelope_plan_t p) {
+  return p ? (envelope_use_fused(p) ? 1 : p->NT) : 0;
+}
 
 extern "C" size_t envelope_plan_device_bytes(envelope_plan_t p) { return p ? p->bytes : 0; }
 

@@ -211,8 +211,14 @@ struct EnvArgs {
   float cz2[17];        // centred second derivative in z divided by dz^2: e0, e1..eN
   float cz1[17];        // centred first derivative in z divided by dz: d1..dN at [1..N]
   float k2;             // 2 k0
+  float dt_over[17];    // (float)(dt / n), n = 1..16 (the fused launch)
 };
 cudaError_t launch_envelope_term(const EnvArgs& a, cudaStream_t st);
+// all N_T Taylor terms of one step in one launch (temporal blocking); order 8 and N_T = 4, Nz a multiple of 32
+size_t envelope_fused_smem(int order, int taylor_order);
+bool envelope_fused_supported(int order, int taylor_order);
+cudaError_t launch_envelope_fused(const EnvArgs& a, const float2* in_a, const float2* in_t, float2* out_a,
+                                  float2* out_t, int taylor_order, cudaStream_t st);
 cudaError_t launch_envelope_chit(const float* chi, const float* sigma, float* chit, size_t n, cudaStream_t st);
 cudaError_t launch_envelope_damp(float2* psi, const float* sigma, float c, size_t n, cudaStream_t st);
 

@@ -87,3 +87,23 @@ def test_envelope_absorbing_layer_matches_oracle():
     ra, rt = ev.envelope_step_absorbing(a, at, chi, sigma.astype(np.float32).astype(np.float64), order, NT, dz, dr,
                                         dt, nsteps=3)
     assert _rel(out[0], ra) < 2e-6 and _rel(out[1], rt) < 2e-6
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 5])
+def test_fused_envelope_equals_term_by_term_launches(nsteps):
+    # the all-terms-in-one-launch step (order 8, N_T = 4) does the term-by-term arithmetic cell for cell, so
+    # the two agree bit for bit; odd and even step counts (the state alternates with a plan buffer), a ragged
+    # radial tile (Nr = 200) and the periodic z halo
+    rng = np.random.default_rng(40 + nsteps)
+    Nz, Nr = 256, 200
+    a = rng.standard_normal((2, Nz, Nr)) + 1j * rng.standard_normal((2, Nz, Nr))
+    chi = 0.3 * rng.random((Nz, Nr))
+    plan = fd.envelope_plan(Nz, Nr, 8, 4, 0.2, 0.25, 0.05)
+    assert plan.launches_per_step == 1
+    c = torch.from_numpy(chi).float().cuda()
+    x = torch.from_numpy(a).to(torch.complex64).cuda()
+    y = x.clone()
+    fd.envelope_step(plan, x, c, nsteps)
+    fd.envelope_step_terms(plan, y, c, nsteps)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
