@@ -85,9 +85,9 @@ __device__ __forceinline__ void stage(float2* sm, const float2* tw, int ncol) {
     float2 w[R];
 #pragma unroll
     for (int r = 1; r < R; ++r) w[r] = tw[SH::TWO(s) + (r - 1) * L + n1];
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-      if (a >= ncol) break;
+    // columns rolled: the butterfly's code once, not five times (instruction-cache footprint)
+#pragma unroll 1
+    for (int a = 0; a < ncol; ++a) {
       float2* col = sm + a * SH::PC + base;
       float2 v[R];
 #pragma unroll
@@ -166,6 +166,10 @@ __device__ __forceinline__ void fused_last(float2* sm, int fam, const PhaseF* __
   const int t = threadIdx.x;
   const int base = pad16(8 * t);
   float2 x[3][8];
+  // the first kz's records are requested before the column transforms so that their latency overlaps them;
+  // the records of kz r + 1 are loaded while kz r is updated
+  PhaseF ph_next = phase[t];
+  ZSymK z_next = zs[t];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     load8(sm + a * SH::PC + base, x[a]);
@@ -182,9 +186,12 @@ __device__ __forceinline__ void fused_last(float2* sm, int fam, const PhaseF* __
   }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    const int q = r * NT + t;
-    const PhaseF ph = phase[q];
-    const ZSymK z = zs[q];
+    const PhaseF ph = ph_next;
+    const ZSymK z = z_next;
+    if (r < 7) {
+      ph_next = phase[(r + 1) * NT + t];
+      z_next = zs[(r + 1) * NT + t];
+    }
     const df A1 = ph.A1, A2 = ph.A2;
     float B1 = 0.f, B2 = 0.f, ch = 1.f;
     if (HASJ) half_step(ph, B1, B2, ch);
