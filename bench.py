@@ -110,7 +110,7 @@ def replica_rate(units_per_rank, seconds, world):
     return units_per_rank * world / seconds
 
 
-STAGE_SOURCE = {"projection": "k_tc.cu", "spectral": "k_spectral.cu", "backprojection": "k_tc.cu"}
+STAGE_SOURCE = {"projection": "k_tc.cu", "spectral": "k_spectral32.cu", "backprojection": "k_tc.cu"}
 
 
 def recorded_traffic(stage, workload, prec):
