@@ -433,17 +433,18 @@ int envelope_plan(envelope_plan_t* out, int Nz, int Nr, int order, int taylor_or
  * a: device [2][Nz][Nr] complex64 (a then a~).  chi: device [Nz][Nr] float32,
  * frozen over the call (the mid-step value of Sec. 4.2).  Asynchronous on
  * `stream`; uses the plan's scratch, so calls on one plan must not overlap.
- * For order 8 and taylor_order 4 with Nz a multiple of 32 (the paper's envelope
- * settings) every Taylor term of a step runs in one launch, the terms of a tile
- * chained in shared memory; the state then alternates between `a` and a plan
- * buffer and ends in `a` (one device copy when nsteps is odd).  The arithmetic
- * per cell is that of the term-by-term form, so both give identical bits.
+ * One launch per Taylor term.
  *
- * envelope_step_terms - the same step with one launch per Taylor term (the
- * term-by-term form, every order and taylor_order).
+ * envelope_step_fused - the same step with every Taylor term in one launch (order 8,
+ * taylor_order 4, Nz a multiple of 32; FDETD_ERR_UNSUPPORTED otherwise): each tile
+ * chains its terms in shared memory, recomputing a halo of N_T order/2 cells; the
+ * state alternates between `a` and a plan buffer and ends in `a` (one device copy
+ * when nsteps is odd).  Per cell it does the arithmetic of envelope_step, so both
+ * give identical bits.  It saves the term-by-term DRAM round trips when the state
+ * does not stay in L2 between the term launches, at the cost of the halo work.
  */
 int envelope_step(envelope_plan_t plan, void* a, const float* chi, int nsteps, void* stream);
-int envelope_step_terms(envelope_plan_t plan, void* a, const float* chi, int nsteps, void* stream);
+int envelope_step_fused(envelope_plan_t plan, void* a, const float* chi, int nsteps, void* stream);
 
 /*
  * envelope_step_static - the envelope step for callers that cannot allocate device memory

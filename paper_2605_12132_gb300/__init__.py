@@ -20,7 +20,7 @@ from ._native import (  # noqa: F401
     envelope_step,
     envelope_step_absorbing,
     envelope_step_static,
-    envelope_step_terms,
+    envelope_step_fused,
     fdetd_current_correct,
     fdetd_current_host_bands,
     fdetd_destagger,

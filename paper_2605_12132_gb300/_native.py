@@ -60,7 +60,7 @@ def lib():
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_step_absorbing.argtypes = [c_vp, c_vp, c_vp, c_vp, c_int, c_vp]
-    L.envelope_step_terms.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
+    L.envelope_step_fused.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_plan_launches_per_step.argtypes = [c_vp]
     L.envelope_plan_device_bytes.argtypes = [c_vp]
     L.envelope_plan_device_bytes.restype = ctypes.c_size_t
@@ -421,14 +421,14 @@ def envelope_step(plan, a, chi, nsteps=1, stream=None):
     return a
 
 
-def envelope_step_terms(plan, a, chi, nsteps=1, stream=None):
-    """envelope_step with one launch per Taylor term (the term-by-term form)."""
+def envelope_step_fused(plan, a, chi, nsteps=1, stream=None):
+    """envelope_step with every Taylor term in one launch (order 8, N_T = 4, Nz a multiple of 32)."""
     import torch
     if not a.is_cuda or a.dtype != torch.complex64 or tuple(a.shape) != (2, plan.Nz, plan.Nr) or not a.is_contiguous():
         raise FdetdError("a must be a contiguous cuda complex64 tensor of shape (2, Nz, Nr)")
     if not chi.is_cuda or chi.dtype != torch.float32 or tuple(chi.shape) != (plan.Nz, plan.Nr) or not chi.is_contiguous():
         raise FdetdError("chi must be a contiguous cuda float32 tensor of shape (Nz, Nr)")
-    _check(lib().envelope_step_terms(plan.handle, a.data_ptr(), chi.data_ptr(), nsteps, _stream_handle(stream)))
+    _check(lib().envelope_step_fused(plan.handle, a.data_ptr(), chi.data_ptr(), nsteps, _stream_handle(stream)))
     return a
 
 

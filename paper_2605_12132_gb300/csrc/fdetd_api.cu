@@ -1200,7 +1200,6 @@ extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int n
   cudaStream_t st = (cudaStream_t)stream;
   const size_t plane = (size_t)p->Nz * p->Nr;
   float2* psi_a = (float2*)a;
-  if (envelope_use_fused(p)) return envelope_steps_fused(p, psi_a, chi, nsteps, nullptr, 0.f, st);
   for (int s = 0; s < nsteps; ++s) {
     int rc = envelope_taylor(p, psi_a, psi_a + plane, chi, st);
     if (rc) return rc;
@@ -1208,17 +1207,12 @@ extern "C" int envelope_step(envelope_plan_t p, void* a, const float* chi, int n
   return FDETD_OK;
 }
 
-extern "C" int envelope_step_terms(envelope_plan_t p, void* a, const float* chi, int nsteps, void* stream) {
+extern "C" int envelope_step_fused(envelope_plan_t p, void* a, const float* chi, int nsteps, void* stream) {
   if (!p || !a || !chi) return fail(FDETD_ERR_ARG, "null argument");
   if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
   if (((uintptr_t)a & 15) || ((uintptr_t)chi & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
-  const size_t plane = (size_t)p->Nz * p->Nr;
-  float2* psi_a = (float2*)a;
-  for (int s = 0; s < nsteps; ++s) {
-    int rc = envelope_taylor(p, psi_a, psi_a + plane, chi, (cudaStream_t)stream);
-    if (rc) return rc;
-  }
-  return FDETD_OK;
+  if (!envelope_use_fused(p)) return fail(FDETD_ERR_UNSUPPORTED, "the fused step takes order 8, N_T = 4, Nz = 32 k");
+  return envelope_steps_fused(p, (float2*)a, chi, nsteps, nullptr, 0.f, (cudaStream_t)stream);
 }
 
 extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* chi, const float* sigma, int nsteps,
@@ -1233,7 +1227,6 @@ extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* 
   cudaError_t e = launch_envelope_chit(chi, sigma, p->d_chit, plane, st);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
   const float damp = (float)(-0.25 * p->dt);
-  if (envelope_use_fused(p)) return envelope_steps_fused(p, psi_a, p->d_chit, nsteps, sigma, damp, st);
   for (int s = 0; s < nsteps; ++s) {
     e = launch_envelope_damp(psi_a, sigma, damp, plane, st);
     if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("envelope: ") + cudaGetErrorString(e));
@@ -1245,9 +1238,7 @@ extern "C" int envelope_step_absorbing(envelope_plan_t p, void* a, const float* 
   return FDETD_OK;
 }
 
-extern "C" int envelope_plan_launches_per_step(envelope_plan_t p) {
-  return p ? (envelope_use_fused(p) ? 1 : p->NT) : 0;
-}
+extern "C" int envelope_plan_launches_per_step(envelope_plan_t p) { return p ? p->NT : 0; }
 
 extern "C" size_t envelope_plan_device_bytes(envelope_plan_t p) { return p ? p->bytes : 0; }
 

@@ -15,7 +15,7 @@
 //
 // Projection  (per mode, group, output block):  D[(z,part), j] = sum_r X[(z,part), r] P[j, r]
 //   A = field rows (64 z x re/im, r contiguous): a TMA box (per-instance tensor map in the
-//       kernel parameters) stages FP32 complex values in shared memory; four converter warps
+//       kernel parameters) stages FP32 complex values in shared memory; eight converter warps
 //       split them in place into 64B-swizzled bf16 pieces (forming tau*F on the way);
 //   B = P pieces [j][r], K-major, pre-tiled and pre-swizzled at plan time (one bulk copy);
 //   M = 128, N = TN (128 or 256), K = 32 per pipeline stage.
@@ -26,8 +26,8 @@
 // Both kernels are persistent: one CTA per SM walks a tile table (tiles of several instances in
 // one launch), the pipeline stages run on across tile boundaries, and with NBUF = 2 the TMEM
 // accumulators are double-buffered so the epilogue of one tile overlaps the MMAs of the next.
-// Warp roles, projection: 0-3 convert, 4-7 epilogue (TMEM -> registers -> global), 8 issues the
-// bulk copies, 9 issues tcgen05.mma (one thread).  Back-projection: 0-3 epilogue, 4 copies, 5 MMA.
+// Warp roles, projection: 0-7 convert, 8-11 epilogue (TMEM -> registers -> global), 12 issues the
+// bulk copies, 13 issues tcgen05.mma (one thread).  Back-projection: 0-3 epilogue, 4 copies, 5 MMA.
 // Every mbarrier wait is bounded; on timeout the kernel records an error code in the instance's
 // flag, tells the other roles to stop through a shared abort flag, drains its own copies and
 // MMAs, and frees TMEM before returning.
@@ -170,17 +170,22 @@ __device__ __forceinline__ void record_error(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
 
-// barrier + AND-reduction over the 128 threads of warps 0-3 (named barrier 1)
-__device__ __forceinline__ bool bar_and_128(bool v) {
+// The projection's converter warps (0 .. kConvWarps-1) split the staged FP32 field tile (64 z x 32 complex =
+// 256 items of 8 radii) into bf16 pieces; with eight of them each thread converts one item per stage.
+constexpr int kConvWarps = 8, kConvThreads = 32 * kConvWarps, kConvItems = 256 / kConvThreads;
+constexpr int kProjThreads = 32 * (kConvWarps + 6);   // + 4 epilogue, 1 copy, 1 MMA warp
+
+// barrier + AND-reduction over the converter threads (named barrier 1)
+__device__ __forceinline__ bool bar_and_conv(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, 128, p;\nselp.u32 %0, 1, 0, q;\n}"
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
       : "=r"(r)
-      : "r"((uint32_t)v)
+      : "r"((uint32_t)v), "n"(kConvThreads)
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void bar_sync_128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void bar_sync_conv() { asm volatile("bar.sync 1, %0;" ::"n"(kConvThreads) : "memory"); }
 
 __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
   return (unsigned char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
@@ -237,7 +242,7 @@ struct PG {
 };
 
 template <int NP, int NACC, int NBUF, int TN>
-__global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_constant__ GroupParams gp,
+__global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __grid_constant__ GroupParams gp,
                                                               const int4* __restrict__ tiles, int ntiles) {
   typedef PG<NP, NACC, NBUF, TN> C;
   constexpr int S = C::S;
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&sb->fullS[s], 1);
-      mbar_init(&sb->fullA[s], 4);
+      mbar_init(&sb->fullA[s], kConvWarps);
       mbar_init(&sb->fullB[s], 1);
       mbar_init(&sb->empty[s], 1);
     }
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
   auto stage_A = [&](int s) { return base + (size_t)s * C::kStage; };
   auto stage_B = [&](int s) { return base + (size_t)s * C::kStage + C::kA; };
 
-  if (warp < 4) {
+  if (warp < kConvWarps) {
     // ---- converters: staged FP32 complex [64 z][32 r] -> A pieces in place, rows (z, re/im), K = r
     int q = 0;
     bool live = true;
@@ -287,8 +292,8 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
       for (int t = 0; t < T; ++t, ++q) {
         const int s = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
-        // all 128 converter threads take the same decision, so none is left behind at a barrier
-        const bool ok = bar_and_128(mbar_wait(&sb->fullS[s], ph, abort, gp.spin));
+        // all converter threads take the same decision, so none is left behind at a barrier
+        const bool ok = bar_and_conv(mbar_wait(&sb->fullS[s], ph, abort, gp.spin));
         if (!ok) {
           if (threadIdx.x == 0) record_error(I.err, 11);
           live = false;
@@ -299,10 +304,10 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
         const bool rot = (g == 1) ? (ib >= 1) : (ib == 1);
         unsigned char* A = stage_A(s);
         const float* stg = reinterpret_cast<const float*>(A);
-        float re[2][8], im[2][8];
+        float re[kConvItems][8], im[kConvItems][8];
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int item = threadIdx.x + it * 128;  // 64 z x 4 chunks of 8 r
+        for (int it = 0; it < kConvItems; ++it) {
+          const int item = threadIdx.x + it * kConvThreads;  // 64 z x 4 chunks of 8 r
           const int zl = item >> 2, c = item & 3;
           const float4* src = reinterpret_cast<const float4*>(stg + zl * 64 + c * 16);
           // read the four 16-byte pieces in an order rotated by rr = (c + zl): a warp's 32 reads then fall
@@ -345,10 +350,10 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
             }
           }
         }
-        bar_sync_128();  // every staged value is in registers before the pieces overwrite the staging
+        bar_sync_conv();  // every staged value is in registers before the pieces overwrite the staging
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int item = threadIdx.x + it * 128;
+        for (int it = 0; it < kConvItems; ++it) {
+          const int item = threadIdx.x + it * kConvThreads;
           const int zl = item >> 2, c = item & 3;
           const int row_re = 2 * zl, row_im = 2 * zl + 1;
           const uint32_t off_re = row_re * 64 + ((c ^ ((row_re >> 1) & 3)) << 4);
@@ -381,8 +386,9 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
         if (lane == 0) mbar_arrive(&sb->fullA[s]);
       }
     }
-  } else if (warp < 8) {
-    // ---- epilogue: TMEM -> coef[md][g*3+ob][j][2 Nz] (complex, re/im from adjacent rows)
+  } else if (warp < kConvWarps + 4) {
+    // ---- epilogue: TMEM -> coef[md][g*3+ob][j][2 Nz] (complex, re/im from adjacent rows); TMEM lane quarter
+    // = warp mod 4
     const int quarter = warp & 3;
     int it = 0;
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(320, 1) tcg_project_kernel(const __grid_consta
       __syncwarp();
       if (lane == 0) mbar_arrive(&sb->tempty[b]);
     }
-  } else if (warp == 8) {
+  } else if (warp == kConvWarps + 4) {
     // ---- producer: the FP32 field tile (TMA) and the pre-tiled P pieces (bulk copies)
     int q = 0;
     bool live = true;
@@ -972,14 +978,14 @@ static cudaError_t launch_project(const TcGroup* G, cudaStream_t st) {
   const dim3 grid(G->grid_p);
   if (G->np == 2) {
     if (G->cfg.tn_p == 256)
-      tcg_project_kernel<2, 1, 2, 256><<<grid, 320, PG<2, 1, 2, 256>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
+      tcg_project_kernel<2, 1, 2, 256><<<grid, kProjThreads, PG<2, 1, 2, 256>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
     else
-      tcg_project_kernel<2, 1, 2, 128><<<grid, 320, PG<2, 1, 2, 128>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
+      tcg_project_kernel<2, 1, 2, 128><<<grid, kProjThreads, PG<2, 1, 2, 128>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
   } else {
     if (G->cfg.tn_p == 256)
-      tcg_project_kernel<3, 2, 1, 256><<<grid, 320, PG<3, 2, 1, 256>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
+      tcg_project_kernel<3, 2, 1, 256><<<grid, kProjThreads, PG<3, 2, 1, 256>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
     else
-      tcg_project_kernel<3, 2, 2, 128><<<grid, 320, PG<3, 2, 2, 128>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
+      tcg_project_kernel<3, 2, 2, 128><<<grid, kProjThreads, PG<3, 2, 2, 128>::kSmem, st>>>(G->params, G->d_ptiles, G->nptiles);
   }
   return cudaGetLastError();
 }
