@@ -334,6 +334,8 @@ int fdetd_batch_destroy(fdetd_batch_t batch);
  * times (seconds on a monotonic clock; 0 where not reached yet).
  * fdetd_server_stats(server, &stats): budget, bytes in use and their peak, request counts,
  * graph re-captures, scheduling rounds, served cell*mode*steps.
+ * fdetd_server_cancel_queued(server, &n): requests still waiting for admission end as failed
+ * ("cancelled before admission"); admitted ones run to completion; n = how many (may be NULL).
  * fdetd_server_destroy(server): stops accepting requests, finishes every request already
  * submitted, then joins the threads and frees everything.
  */
@@ -380,6 +382,7 @@ int fdetd_server_poll(fdetd_server_t server, uint64_t ticket, int* state, double
 int fdetd_server_wait(fdetd_server_t server, uint64_t ticket, double timeout_s, double* latency_s);
 int fdetd_server_ticket_times(fdetd_server_t server, uint64_t ticket, double* times);
 int fdetd_server_stats(fdetd_server_t server, fdetd_server_stats_t* stats);
+int fdetd_server_cancel_queued(fdetd_server_t server, uint64_t* cancelled);
 int fdetd_server_destroy(fdetd_server_t server);
 
 /*

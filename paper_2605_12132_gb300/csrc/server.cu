@@ -516,6 +516,27 @@ extern "C" int fdetd_server_stats(fdetd_server_t s, fdetd_server_stats_t* st) {
   return FDETD_OK;
 }
 
+extern "C" int fdetd_server_cancel_queued(fdetd_server_t s, uint64_t* cancelled) {
+  if (!s) return fdetd::set_error(FDETD_ERR_ARG, "server is null");
+  uint64_t n = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const double t = now_s();
+    for (Ticket* q : s->queue) {
+      q->state = FDETD_TICKET_FAILED;
+      q->err = FDETD_ERR_ARG;
+      q->msg = "cancelled before admission";
+      q->t_done = t;
+      ++s->failed;
+      ++n;
+    }
+    s->queue.clear();
+  }
+  s->cv_done.notify_all();
+  if (cancelled) *cancelled = n;
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_server_destroy(fdetd_server_t s) {
   if (!s) return FDETD_OK;
   {

@@ -52,6 +52,7 @@ def _bind():
     L.fdetd_server_wait.argtypes = [vp, u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     L.fdetd_server_ticket_times.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_double)]
     L.fdetd_server_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    L.fdetd_server_cancel_queued.argtypes = [vp, ctypes.POINTER(u64)]
     L.fdetd_server_destroy.argtypes = [vp]
     L._server_bound = True
     return L
@@ -135,8 +136,9 @@ class Ticket:
         return lat.value
 
 
-def _c_request(req):
-    """The C request and the host arrays it points into (kept alive by the ticket)."""
+def _c_request(req, keep_result=True):
+    """The C request and the host arrays it points into (kept alive by the ticket); without keep_result the
+    library copies no result back."""
     keep = {}
     r = _Request()
     r.Nz, r.Nr, r.order, r.steps = req.Nz, req.Nr, req.order, req.steps
@@ -158,9 +160,9 @@ def _c_request(req):
         if req.J is not None:
             keep["J"] = np.ascontiguousarray(req.J, dtype=cdt)
             r.J = keep["J"].ctypes.data
-    keep["out"] = np.empty_like(keep["fields"])
+    keep["out"] = np.empty_like(keep["fields"]) if keep_result else None
     r.fields = keep["fields"].ctypes.data
-    r.out = keep["out"].ctypes.data
+    r.out = keep["out"].ctypes.data if keep_result else None
     return r, keep
 
 
@@ -180,8 +182,8 @@ class Server:
         self.budget = int(hbm_budget)
         self.tickets = []
 
-    def submit(self, req, arrival=None):
-        r, keep = _c_request(req)
+    def submit(self, req, arrival=None, keep_result=True):
+        r, keep = _c_request(req, keep_result)
         t = Ticket(self, req, r, keep)
         tid = ctypes.c_uint64(0)
         nat._check(_bind().fdetd_server_submit(self.handle, ctypes.byref(r), ctypes.byref(tid)))
@@ -216,6 +218,12 @@ class Server:
             if rc == 6:
                 raise TimeoutError("server did not drain in time")
 
+    def cancel_queued(self):
+        """End every request still waiting for admission (failed, 'cancelled before admission')."""
+        n = ctypes.c_uint64(0)
+        nat._check(_bind().fdetd_server_cancel_queued(self.handle, ctypes.byref(n)))
+        return n.value
+
     def close(self):
         """Finish every submitted request, record each ticket's final state, then stop the server."""
         if self.handle:
@@ -232,8 +240,9 @@ class Server:
             pass
 
 
-def run_poisson(server, make_request, rate_hz, duration_s, seed=0, max_requests=None):
-    """Submit requests with Poisson arrivals (rate_hz over duration_s); returns the tickets (not waited for)."""
+def run_poisson(server, make_request, rate_hz, duration_s, seed=0, max_requests=None, keep_result=True):
+    """Submit requests with Poisson arrivals (rate_hz over duration_s), each built when it arrives; returns the
+    tickets (not waited for)."""
     rng = np.random.default_rng(seed)
     times = []
     t = 0.0
@@ -242,14 +251,14 @@ def run_poisson(server, make_request, rate_hz, duration_s, seed=0, max_requests=
         if t > duration_s or (max_requests and len(times) >= max_requests):
             break
         times.append(t)
-    reqs = [make_request(i, rng) for i in range(len(times))]
     t0 = time.perf_counter()
     tickets = []
     for k, at in enumerate(times):
+        req = make_request(k, rng)
         delay = t0 + at - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets.append(server.submit(reqs[k], arrival=t0 + at))
+        tickets.append(server.submit(req, arrival=t0 + at, keep_result=keep_result))
     return tickets
 
 

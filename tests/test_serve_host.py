@@ -92,3 +92,20 @@ def test_latency_statistics():
     assert s["count"] == 5 and s["p50_s"] == 3.0 and s["max_s"] == 100.0
     assert s["p99_s"] == pytest.approx(np.percentile([1, 2, 3, 4, 100], 99))
     assert serve.latency_stats([_T(None)]) == {"count": 0}
+
+
+def test_cancel_queued_ends_only_the_waiting_requests():
+    reqs = [_field(Nz=256, steps=400) for _ in range(6)]
+    one = serve.estimate_bytes(reqs[0])
+    srv = serve.Server(one * 2, chunk_steps=2, dry_run=True)   # two fit at a time
+    tickets = [srv.submit(r) for r in reqs]
+    import time
+    time.sleep(0.05)
+    n = srv.cancel_queued()
+    srv.drain(timeout=60)
+    states = [t.state for t in tickets]
+    assert n >= 1 and states.count(serve.FAILED) == n
+    assert states.count(serve.DONE) == len(reqs) - n
+    st = srv.stats()
+    assert st["used_bytes"] == 0 and st["failed"] == n
+    srv.close()
