@@ -398,6 +398,19 @@ int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, double dr, do
                       double* PB, double* QE, double* QB, double* lam, double* mu, uint8_t* tm_live,
                       uint8_t* te_live, double* kappa2, double* sp, double* sm);
 
+/*
+ * fdetd_plan_cache_set_limit / fdetd_plan_cache_stats - the process-wide cache of per-mode radial
+ * tables.  A mode's radial eigenbases and projection matrices (Sec. 2.5 operator, Sec. 2.4 axis rule)
+ * depend on (Nr, order, dr, m) only, so every plan construction (fdetd_plan, fdetd_plan_modes, the
+ * server's builders, fdetd_host_tables) looks them up there first and skips the eigen-decompositions on
+ * a hit; the tables are bitwise the same either way.  The cache lives in host memory, is thread-safe
+ * and evicts least recently used entries above `bytes` (default 4 GiB; 0 empties and disables it; an
+ * entry is 4 (3 Nr)^2 doubles, about 75 MB at Nr = 512).  Stats: bytes held, the limit, entries, and
+ * the hit and miss counts since the process started; any pointer may be NULL.  Both return FDETD_OK.
+ */
+int fdetd_plan_cache_set_limit(size_t bytes);
+int fdetd_plan_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits, uint64_t* misses);
+
 /* Host-only: staggered (kind 0), centred first (1), centred second (2, e0 first) derivative
  * coefficients of `order`, or axis coefficients (3, N = order/2); returns the count written. */
 int fdetd_host_coeffs(int kind, int order, double* out);

@@ -57,6 +57,10 @@ def lib():
     L.fdetd_host_coeffs.argtypes = [c_int, c_int, dp]
     L.fdetd_host_spectral_order.argtypes = [c_int, c_int, c_vp]
     L.fdetd_host_spectral_radices.argtypes = [c_int, c_int, ctypes.POINTER(c_int)]
+    L.fdetd_plan_cache_set_limit.argtypes = [ctypes.c_size_t]
+    L.fdetd_plan_cache_stats.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                         ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_uint64)]
     L.envelope_plan.argtypes = [ctypes.POINTER(c_vp), c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl]
     L.envelope_step.argtypes = [c_vp, c_vp, c_vp, c_int, c_vp]
     L.envelope_step_absorbing.argtypes = [c_vp, c_vp, c_vp, c_vp, c_int, c_vp]
@@ -368,6 +372,21 @@ def fdetd_host_spectral_radices(Nz, precision="bf16x6"):
     if n < 0:
         _check(-n)
     return [rad[k] for k in range(n)]
+
+
+def fdetd_plan_cache_set_limit(nbytes):
+    """Byte limit of the process-wide cache of per-mode radial tables (0 empties and disables it)."""
+    _check(lib().fdetd_plan_cache_set_limit(int(nbytes)))
+
+
+def fdetd_plan_cache_stats():
+    """The radial-table cache: bytes held, limit, entries, hits and misses since the process started."""
+    b, lim = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    n = ctypes.c_int(0)
+    h, m = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().fdetd_plan_cache_stats(ctypes.byref(b), ctypes.byref(lim), ctypes.byref(n), ctypes.byref(h),
+                                        ctypes.byref(m)))
+    return {"bytes": b.value, "limit": lim.value, "entries": n.value, "hits": h.value, "misses": m.value}
 
 
 def fdetd_host_coeffs(kind, order):

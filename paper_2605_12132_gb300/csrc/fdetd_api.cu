@@ -724,6 +724,17 @@ extern "C" int fdetd_host_spectral_radices(int Nz, int precision, int* rad) {
   return spectral_radices(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, rad);
 }
 
+extern "C" int fdetd_plan_cache_set_limit(size_t bytes) {
+  mode_cache_set_limit(bytes);
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits,
+                                      uint64_t* misses) {
+  mode_cache_stats(bytes, limit, entries, hits, misses);
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_host_coeffs(int kind, int order, double* out) {
   if (order < 2 || order > 32 || (order & 1) || !out) return fail(FDETD_ERR_ARG, "bad order or null out");
   std::vector<double> v;

@@ -4,6 +4,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <list>
+#include <memory>
+#include <mutex>
 
 #include "eig.h"
 
@@ -600,6 +604,97 @@ int current_bands(int n, int order, double dr, int m, std::vector<double>& divp,
   return 0;
 }
 
+// ------------------------------------------------------------------ cache of per-mode radial tables
+// A mode's radial tables depend on (Nr, order, dr, m) only, not on Nz, dt or the precision, so plans that share a
+// radial grid (repeated requests to a server, the instances of a batch) share one eigen-decomposition.  The cache
+// holds immutable tables, keyed on those four values (dr by its bit pattern), bounded in bytes, least recently used
+// evicted first; two threads that miss on the same key both build it and the first insert wins.
+namespace {
+
+struct ModeKey {
+  int n, order, m;
+  uint64_t dr_bits;
+  bool operator==(const ModeKey& o) const {
+    return n == o.n && order == o.order && m == o.m && dr_bits == o.dr_bits;
+  }
+};
+
+struct ModeCache {
+  std::mutex mu;
+  std::list<std::pair<ModeKey, std::shared_ptr<const ModePlan>>> lru;  // front = most recently used
+  size_t bytes = 0, limit = size_t(4) << 30;
+  uint64_t hits = 0, misses = 0;
+};
+
+ModeCache& mode_cache() {
+  static ModeCache c;
+  return c;
+}
+
+size_t mode_plan_bytes(const ModePlan& P) {
+  return sizeof(double) * (P.lam.size() + P.mu.size() + P.PE.size() + P.PB.size() + P.QE.size() + P.QB.size()) +
+         P.tm_live.size() + P.te_live.size();
+}
+
+void evict_over_limit(ModeCache& c) {
+  while (c.bytes > c.limit && !c.lru.empty()) {
+    c.bytes -= mode_plan_bytes(*c.lru.back().second);
+    c.lru.pop_back();
+  }
+}
+
+int cached_mode(ModePlan& P, int n, int order, double dr, int m, std::string& msg) {
+  ModeKey key{n, order, m, 0};
+  std::memcpy(&key.dr_bits, &dr, sizeof(dr));
+  ModeCache& c = mode_cache();
+  std::shared_ptr<const ModePlan> hit;
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    for (auto it = c.lru.begin(); it != c.lru.end(); ++it)
+      if (it->first == key) {
+        c.lru.splice(c.lru.begin(), c.lru, it);
+        hit = it->second;
+        ++c.hits;
+        break;
+      }
+    if (!hit) ++c.misses;
+  }
+  if (hit) {
+    P = *hit;
+    return 0;
+  }
+  const int rc = build_mode(P, n, order, dr, m, msg);
+  if (rc) return rc;
+  const size_t b = mode_plan_bytes(P);
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (b > c.limit) return 0;
+  for (const auto& e : c.lru)
+    if (e.first == key) return 0;
+  c.lru.emplace_front(key, std::make_shared<const ModePlan>(P));
+  c.bytes += b;
+  evict_over_limit(c);
+  return 0;
+}
+
+}  // namespace
+
+void mode_cache_set_limit(size_t bytes) {
+  ModeCache& c = mode_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  c.limit = bytes;
+  evict_over_limit(c);
+}
+
+void mode_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits, uint64_t* misses) {
+  ModeCache& c = mode_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (bytes) *bytes = c.bytes;
+  if (limit) *limit = c.limit;
+  if (entries) *entries = (int)c.lru.size();
+  if (hits) *hits = c.hits;
+  if (misses) *misses = c.misses;
+}
+
 int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
                     double dr, double dt, std::string& msg) {
   if (order < 2 || order > 32 || (order & 1)) {
@@ -623,7 +718,7 @@ int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, 
       msg = "mode numbers must be 0..64";
       return 1;
     }
-    int rc = build_mode(hp.mp[i], Nr, order, dr, modes[i], msg);
+    int rc = cached_mode(hp.mp[i], Nr, order, dr, modes[i], msg);
     if (rc) return rc;
   }
   // z symbols of the periodic staggered stencil: s+ = i kappa e^{+i th/2}, s- = i kappa e^{-i th/2},

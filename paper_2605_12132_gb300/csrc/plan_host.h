@@ -13,6 +13,7 @@
 // back-projection (Q) matrices; the axis rule of Sec. 2.4 is folded into Q's
 // axis rows.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -54,6 +55,11 @@ struct HostPlan {
 // (1 = bad argument, 4 = eigen-solve failure).
 int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, int order, double dz,
                     double dr, double dt, std::string& msg);
+
+// Process-wide cache of per-mode radial tables (keyed on Nr, order, dr, m): byte limit (0 empties and disables
+// it; default 4 GiB) and counters.
+void mode_cache_set_limit(size_t bytes);
+void mode_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits, uint64_t* misses);
 
 // Banded radial operators of H for the Taylor scheme (layout documented at the definition).
 // Returns 0, or 1 for a bad order / too few radial points.

@@ -216,3 +216,40 @@ def test_spectral_radices_reject_large_prime_factors():
     assert native.fdetd_host_spectral_radices(64 * 11, "fp32") == []
     assert native.fdetd_host_spectral_radices(4096, "fp32") == [8, 8, 8, 8]
     assert native.fdetd_host_spectral_radices(4096, "fp64") == [4] * 6
+
+
+def test_radial_table_cache_returns_the_same_tables_and_honours_its_limit():
+    # the radial tables depend on (Nr, order, dr, m) only: a second plan with another Nz and dt is a hit and its
+    # tables are bitwise those of a fresh build; limit 0 empties and disables the cache
+    _lib_or_skip()
+    native.fdetd_plan_cache_set_limit(0)
+    native.fdetd_plan_cache_set_limit(1 << 30)
+    s0 = native.fdetd_plan_cache_stats()
+    assert s0["bytes"] == 0 and s0["entries"] == 0 and s0["limit"] == 1 << 30
+    a = native.fdetd_host_tables(16, 40, 1, 8, 1 / 16, 1 / 4, 1 / 16)
+    s1 = native.fdetd_plan_cache_stats()
+    assert s1["misses"] == s0["misses"] + 1 and s1["entries"] == 1
+    assert s1["bytes"] >= 4 * (3 * 40) ** 2 * 8
+    b = native.fdetd_host_tables(32, 40, 1, 8, 1 / 8, 1 / 4, 1 / 32)
+    s2 = native.fdetd_plan_cache_stats()
+    assert s2["hits"] == s1["hits"] + 1 and s2["misses"] == s1["misses"]
+    for k in ("PE", "PB", "QE", "QB", "lam", "mu", "tm_live", "te_live"):
+        assert np.array_equal(a[k], b[k]), k
+    # a different dr, m or order is a different key
+    native.fdetd_host_tables(16, 40, 1, 8, 1 / 16, 1 / 5, 1 / 16)
+    native.fdetd_host_tables(16, 40, 2, 8, 1 / 16, 1 / 4, 1 / 16)
+    native.fdetd_host_tables(16, 40, 1, 4, 1 / 16, 1 / 4, 1 / 16)
+    s3 = native.fdetd_plan_cache_stats()
+    assert s3["misses"] == s2["misses"] + 3 and s3["entries"] == 4
+    # a limit that holds about two entries evicts the least recently used ones
+    one = s1["bytes"]
+    native.fdetd_plan_cache_set_limit(2 * one + one // 2)
+    s4 = native.fdetd_plan_cache_stats()
+    assert s4["entries"] == 2 and s4["bytes"] <= 2 * one + one // 2
+    native.fdetd_plan_cache_set_limit(0)
+    c = native.fdetd_host_tables(16, 40, 1, 8, 1 / 16, 1 / 4, 1 / 16)
+    s5 = native.fdetd_plan_cache_stats()
+    assert s5["entries"] == 0 and s5["misses"] == s4["misses"] + 1
+    for k in ("PE", "PB", "QE", "QB", "lam", "mu"):
+        assert np.array_equal(a[k], c[k]), k
+    native.fdetd_plan_cache_set_limit(4 << 30)
