@@ -127,6 +127,11 @@ def recorded_traffic(stage, workload, prec):
         return None
 
 
+def _rounded(pipeline):
+    """Pipeline shares of the tensor-core kernels, rounded for the JSON line."""
+    return {k: {a: (round(b, 4) if isinstance(b, float) else b) for a, b in v.items()} for k, v in pipeline.items()}
+
+
 def gemm_flops(w, hasJ):
     """Algorithmic FLOPs of one step's radial transforms: each nonzero n x n block of the
     (3n)^2 projection / back-projection matrices times a complex column, per z row and mode."""
@@ -283,7 +288,6 @@ def run_batch(args, rank, world, dist):
     # timed region: K graph replays, each bracketed by events on the launching stream
     clocks = ClockSampler()
     clocks.start()
-    batch.set_profiling(True) if False else None
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     t_wall = time.perf_counter()
@@ -302,6 +306,7 @@ def run_batch(args, rank, world, dist):
     ms = max_over_ranks(float(lat.sum()), dist, "cuda")
     value = replica_rate(cells * args.steps, ms / 1e3, world)
     st = batch.stage_times()
+    pipeline = _rounded(batch.pipeline_waits())
 
     # plain FP64 path on the same mix: its one-step result is the accuracy reference, its rate the baseline
     fp64_value = err = None
@@ -369,12 +374,13 @@ def run_batch(args, rank, world, dist):
                 "note": f"achieved = the survey's algorithmic flops x {products} bf16 products per FP32-accurate "
                         "product; executed = the folded dense blocks the kernel multiplies"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = recorded_traffic(dom, f"uneven_mix_{len(cfgs)}", prec)
     roof["algorithmic"] = algo
     roof["kernel"] = {"projection": "tcg_project_kernel (grouped, persistent)", "spectral": "spectral32_kernel",
                       "backprojection": "tcg_backproject_kernel (grouped, persistent)"}[dom]
     roof["peak_source"] = src
     roof["stage_ms_per_step"] = stage_ms
+    roof["pipeline"] = pipeline
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -702,6 +708,7 @@ def run_step(args, w, prec, leg=False, dist=None, rank=0, world=1):
     t_wall = time.perf_counter() - t_wall
     clk = None if leg else clocks.stop()
     ktimes = plan.kernel_times()
+    pipeline = _rounded(plan.pipeline_waits()) if prec in ("bf16x3", "bf16x6") else None
     plan.set_profiling(False)
     plan.status()
     lat = np.array([a.elapsed_time(b) for a, b in evs])
@@ -732,7 +739,7 @@ def run_step(args, w, prec, leg=False, dist=None, rank=0, world=1):
 
     summary = {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order, "precision": prec,
                "steps": steps, "ms_per_step": ms / steps, "value": value, "stage_ms_per_step": stage_ms,
-               "fp64_value": fp64_value, "rel_err_vs_fp64_1step": err, "tiles": tiles,
+               "fp64_value": fp64_value, "rel_err_vs_fp64_1step": err, "tiles": tiles, "pipeline": pipeline,
                "l2": "flushed between timed steps (256 MiB write)"}
     launches = plan.launches_per_step * steps
     plan.close()

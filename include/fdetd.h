@@ -185,6 +185,20 @@ int fdetd_plan_launches_per_step(fdetd_plan_t plan);
 int fdetd_plan_set_profiling(fdetd_plan_t plan, int on);
 int fdetd_plan_kernel_times(fdetd_plan_t plan, double* ms, long* calls);
 
+/*
+ * fdetd_plan_pipeline_waits - pipeline accounting of the tensor-core kernels (BF16X3 / BF16X6 plans),
+ * counted while profiling is on (fdetd_plan_set_profiling(plan, 1) zeroes the counters).  out: 16
+ * unsigned 64-bit SM clock-cycle sums over all CTAs and launches, out[0..7] for the projection and
+ * out[8..15] for the back-projection: [0] CTA residency seen by the MMA-issuing thread, [1] MMA issuer
+ * waiting for a stage's A operand (projection: the converted field pieces), [2] waiting for its B
+ * operand (back-projection: both operands), [3] waiting for a free TMEM accumulator, [4] producer
+ * waiting for a free stage, [5] converters waiting for the staged FP32 tile, [6] converters busy, [7]
+ * epilogue busy (TMEM to global).  Slots a kernel lacks stay 0.  Synchronous (device-to-host copy);
+ * FDETD_ERR_UNSUPPORTED for the CUDA-core precisions.  fdetd_batch_pipeline_waits reports the same
+ * for a batch captured with profiling on (sum over its groups and graph replays).
+ */
+int fdetd_plan_pipeline_waits(fdetd_plan_t plan, unsigned long long* out);
+
 int fdetd_plan_destroy(fdetd_plan_t plan);
 
 /*
@@ -295,6 +309,7 @@ int fdetd_batch_group_info(fdetd_batch_t batch, int group, int* info, double* ms
 int fdetd_batch_launch(fdetd_batch_t batch, void* stream);
 int fdetd_batch_set_profiling(fdetd_batch_t batch, int on);
 int fdetd_batch_collect_stage_times(fdetd_batch_t batch);
+int fdetd_batch_pipeline_waits(fdetd_batch_t batch, unsigned long long* out);
 int fdetd_batch_stage_times(fdetd_batch_t batch, double* ms, long* steps);
 int fdetd_batch_step_host(fdetd_batch_t batch, void* const* host_fields, const void* const* host_J, int nlaunch,
                           void* stream);

@@ -87,6 +87,8 @@ def lib():
     L.fdetd_batch_set_profiling.argtypes = [c_vp, c_int]
     L.fdetd_batch_collect_stage_times.argtypes = [c_vp]
     L.fdetd_batch_stage_times.argtypes = [c_vp, dp, ctypes.POINTER(ctypes.c_long)]
+    L.fdetd_batch_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.fdetd_plan_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fdetd_batch_step_host.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
     L.envelope_step_static.argtypes = [c_vp, c_vp, c_int, c_int, c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_int,
@@ -115,6 +117,22 @@ def _stream_handle(stream):
 
 def _dptr(arr):
     return arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if arr is not None else None
+
+
+PIPELINE_SLOTS = ("cta", "mma_wait_a", "mma_wait_b", "mma_wait_tmem", "producer_wait_stage",
+                  "converter_wait_staged", "converter_busy", "epilogue_busy")
+
+
+def pipeline_report(counters):
+    """The 16 raw counters as {kernel: {slot: share of the CTA residency}} plus the raw cycle sums."""
+    rep = {}
+    for k, name in enumerate(("projection", "backprojection")):
+        c = counters[8 * k: 8 * k + 8]
+        tot = c[0]
+        rep[name] = {"cycles": tot}
+        if tot:
+            rep[name].update({slot: c[i] / tot for i, slot in enumerate(PIPELINE_SLOTS) if i})
+    return rep
 
 
 class FdetdPlan:
@@ -153,6 +171,12 @@ class FdetdPlan:
         calls = (ctypes.c_long * 3)()
         _check(lib().fdetd_plan_kernel_times(self.handle, ms, calls))
         return {name: (ms[i], calls[i]) for i, name in enumerate(("projection", "spectral", "backprojection"))}
+
+    def pipeline_waits(self):
+        """Pipeline cycle counters of the tensor-core kernels while profiling is on (see pipeline_report)."""
+        out = (ctypes.c_uint64 * 16)()
+        _check(lib().fdetd_plan_pipeline_waits(self.handle, out))
+        return pipeline_report(list(out))
 
     @property
     def tile_config(self):
@@ -543,6 +567,12 @@ class FdetdBatch:
         n = ctypes.c_long(0)
         _check(lib().fdetd_batch_stage_times(self.handle, ms, ctypes.byref(n)))
         return {k: (ms[i], n.value) for i, k in enumerate(("projection", "spectral", "backprojection"))}
+
+    def pipeline_waits(self):
+        """Pipeline cycle counters of the grouped tensor-core kernels of a batch captured with profiling on."""
+        out = (ctypes.c_uint64 * 16)()
+        _check(lib().fdetd_batch_pipeline_waits(self.handle, out))
+        return pipeline_report(list(out))
 
     def step_host(self, host_fields, host_J=None, nlaunch=1, stream=None):
         """Host-buffer form: copy every instance's fields (and J) in, replay the graph nlaunch times, copy the

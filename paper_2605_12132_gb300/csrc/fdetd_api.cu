@@ -52,6 +52,7 @@ struct fdetd_plan_s {
   void* d_cur = nullptr;     // current correction: band tables per mode (built on first use)
   // optional per-kernel timing: events recorded around each launch on the launch stream
   bool profiling = false;
+  unsigned long long* d_waits = nullptr;  // pipeline cycle counters of the tensor-core kernels (profiling)
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   double kern_ms[3] = {0, 0, 0};
   long kern_calls[3] = {0, 0, 0};
@@ -87,7 +88,7 @@ static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
   void* ptrs[] = {p->d_P,    p->d_Q,   p->d_phase,  p->d_zsym, p->d_zsymk, p->d_lam,
-                  p->d_tw,   p->d_coef, p->d_src,   p->d_hostio, p->d_err,  p->d_cur};
+                  p->d_tw,   p->d_coef, p->d_src,   p->d_hostio, p->d_err,  p->d_cur, p->d_waits};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -666,7 +667,31 @@ extern "C" int fdetd_plan_set_profiling(fdetd_plan_t p, int on) {
     p->kern_ms[k] = 0;
     p->kern_calls[k] = 0;
   }
+  if (p->tc) {
+    if (on) {
+      cudaError_t e = p->d_waits ? cudaSuccess : cudaMalloc(&p->d_waits, 16 * sizeof(unsigned long long));
+      if (e == cudaSuccess) e = cudaMemset(p->d_waits, 0, 16 * sizeof(unsigned long long));
+      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e));
+    }
+    tc_set_waits(p->tc, on ? p->d_waits : nullptr);
+  }
   return FDETD_OK;
+}
+
+static int read_waits(const unsigned long long* d, unsigned long long* out) {
+  if (!d) {
+    std::fill(out, out + 16, 0ull);
+    return FDETD_OK;
+  }
+  cudaError_t e = cudaMemcpy(out, d, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_plan_pipeline_waits(fdetd_plan_t p, unsigned long long* out) {
+  if (!p || !out) return fail(FDETD_ERR_ARG, "null argument");
+  if (!p->tc) return fail(FDETD_ERR_UNSUPPORTED, "only the tensor-core pipelines have pipeline counters");
+  return read_waits(p->d_waits, out);
 }
 
 extern "C" int fdetd_plan_kernel_times(fdetd_plan_t p, double* ms, long* calls) {
@@ -778,6 +803,7 @@ struct fdetd_batch_s {
   // stage timing: per captured step, events before the grouped projections, after them, after the
   // spectral branches have joined, after the grouped back-projections (recorded as graph nodes)
   int profiling = 0;
+  unsigned long long* d_waits = nullptr;  // pipeline cycle counters of the grouped kernels (profiling)
   std::vector<cudaEvent_t> stage_ev;
   double stage_ms[3] = {0, 0, 0};
   long stage_calls = 0;
@@ -874,6 +900,16 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
         return fail(FDETD_ERR_CUDA, std::string("batch group: ") + cudaGetErrorString(e));
       }
       for (size_t k = 0; k < G.members.size(); ++k) tc_group_set_coef(G.g, (int)k, pl[k]->d_coef);
+      if (b->profiling) {
+        cudaError_t e2 = b->d_waits ? cudaSuccess : cudaMalloc(&b->d_waits, 16 * sizeof(unsigned long long));
+        if (e2 == cudaSuccess) e2 = cudaMemset(b->d_waits, 0, 16 * sizeof(unsigned long long));
+        if (e2 != cudaSuccess) {
+          tc_group_destroy(G.g);
+          batch_release_graph(b);
+          return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e2));
+        }
+        tc_group_set_waits(G.g, b->d_waits);
+      }
       b->groups.push_back(G);
     }
   }
@@ -1014,6 +1050,11 @@ extern "C" int fdetd_batch_collect_stage_times(fdetd_batch_t b) {
   return FDETD_OK;
 }
 
+extern "C" int fdetd_batch_pipeline_waits(fdetd_batch_t b, unsigned long long* out) {
+  if (!b || !out) return fail(FDETD_ERR_ARG, "null argument");
+  return read_waits(b->d_waits, out);
+}
+
 extern "C" int fdetd_batch_stage_times(fdetd_batch_t b, double* ms, long* steps) {
   if (!b || !ms) return fail(FDETD_ERR_ARG, "null argument");
   for (int k = 0; k < 3; ++k) ms[k] = b->stage_ms[k];
@@ -1057,6 +1098,7 @@ extern "C" int fdetd_batch_destroy(fdetd_batch_t b) {
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->d_waits) cudaFree(b->d_waits);
   delete b;
   return FDETD_OK;
 }

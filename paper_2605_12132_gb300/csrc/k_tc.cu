@@ -170,6 +170,22 @@ __device__ __forceinline__ void record_error(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
 
+// Pipeline accounting (GroupParams.waits, 8 counters per kernel, summed over CTAs): clock cycles a role spent
+// waiting on one kind of barrier, or busy, so that the idle time of the tensor pipe can be attributed.
+enum {
+  kWaitCta = 0,     // MMA issuer: whole residency of the CTA (the denominator)
+  kWaitA = 1,       // MMA issuer: waiting for the A operand of a stage (projection: the converted pieces)
+  kWaitB = 2,       // MMA issuer: waiting for the B operand of a stage (back-projection: both operands)
+  kWaitTmem = 3,    // MMA issuer: waiting for the epilogue to free an accumulator
+  kWaitStage = 4,   // producer: waiting for a free stage of the ring
+  kWaitStaged = 5,  // converters: waiting for the staged FP32 tile
+  kBusyConv = 6,    // converters: from the staged tile to the pieces' arrival
+  kBusyEpi = 7      // epilogue: from a full accumulator to its release
+};
+__device__ __forceinline__ void add_waits(unsigned long long* w, int slot, long long cycles) {
+  if (w) atomicAdd(w + slot, (unsigned long long)cycles);
+}
+
 // The projection's converter warps (0 .. kConvWarps-1) split the staged FP32 field tile (64 z x 32 complex =
 // 256 items of 8 radii) into bf16 pieces; with eight of them each thread converts one item per stage.
 constexpr int kConvWarps = 8, kConvThreads = 32 * kConvWarps, kConvItems = 256 / kConvThreads;
@@ -282,6 +298,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
     // ---- converters: staged FP32 complex [64 z][32 r] -> A pieces in place, rows (z, re/im), K = r
     int q = 0;
     bool live = true;
+    long long w_staged = 0, busy = 0;
     for (int ti = blockIdx.x; live && ti < ntiles; ti += gridDim.x) {
       const int4 tl = tiles[ti];
       int md, g, ob, bl[2];
@@ -292,8 +309,11 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       for (int t = 0; t < T; ++t, ++q) {
         const int s = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
+        const long long c0 = clock64();
         // all converter threads take the same decision, so none is left behind at a barrier
         const bool ok = bar_and_conv(mbar_wait(&sb->fullS[s], ph, abort, gp.spin));
+        const long long c1 = clock64();
+        w_staged += c1 - c0;
         if (!ok) {
           if (threadIdx.x == 0) record_error(I.err, 11);
           live = false;
@@ -384,13 +404,19 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&sb->fullA[s]);
+        busy += clock64() - c1;
       }
+    }
+    if (threadIdx.x == 0) {
+      add_waits(gp.waits, kWaitStaged, w_staged);
+      add_waits(gp.waits, kBusyConv, busy);
     }
   } else if (warp < kConvWarps + 4) {
     // ---- epilogue: TMEM -> coef[md][g*3+ob][j][2 Nz] (complex, re/im from adjacent rows); TMEM lane quarter
     // = warp mod 4
     const int quarter = warp & 3;
     int it = 0;
+    long long busy = 0;
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
       const int4 tl = tiles[ti];
       int md, g, ob;
@@ -402,6 +428,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         if (lane == 0) record_error(I.err, 14);
         break;
       }
+      const long long c1 = clock64();
       tc_fence_after();
       const int n = I.n, Nz = I.Nz, z0 = tl.z, j0 = tl.w;
       const int row = quarter * 32 + lane;
@@ -427,11 +454,14 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sb->tempty[b]);
+      busy += clock64() - c1;
     }
+    if (warp == kConvWarps && lane == 0) add_waits(gp.waits, kBusyEpi, busy);
   } else if (warp == kConvWarps + 4) {
     // ---- producer: the FP32 field tile (TMA) and the pre-tiled P pieces (bulk copies)
     int q = 0;
     bool live = true;
+    long long w_stage = 0;
     for (int ti = blockIdx.x; live && ti < ntiles; ti += gridDim.x) {
       const int4 tl = tiles[ti];
       int md, g, ob, bl[2];
@@ -443,7 +473,9 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         const int s = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
         bool ok = true;
+        const long long c0 = clock64();
         if (lane == 0) ok = mbar_wait(&sb->empty[s], ph ^ 1u, abort, gp.spin);
+        w_stage += clock64() - c0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) record_error(I.err, 12);
@@ -472,6 +504,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         }
       }
     }
+    if (lane == 0) add_waits(gp.waits, kWaitStage, w_stage);
     // after an abort: wait (bounded) for the copies already issued that no consumer will wait for
     if (!live && lane == 0) {
       for (int k = 1; k <= S; ++k) {
@@ -487,6 +520,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       const uint32_t idesc = idesc_bf16(TN, false);
       int q = 0, it = 0;
       bool live = true;
+      const long long t_start = clock64();
+      long long w_a = 0, w_b = 0, w_tmem = 0;
       for (int ti = blockIdx.x; live && ti < ntiles; ti += gridDim.x, ++it) {
         const int4 tl = tiles[ti];
         int md, g, ob, bl[2];
@@ -496,7 +531,10 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         const int T = proj_blocks(g, ob, bl) * nks;
         const int b = NBUF == 2 ? (it & 1) : 0;
         const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
-        if (!mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort, gp.spin)) {
+        const long long c0 = clock64();
+        const bool freed = mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort, gp.spin);
+        w_tmem += clock64() - c0;
+        if (!freed) {
           record_error(I.err, 15);
           break;
         }
@@ -505,7 +543,13 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
           const uint32_t ph = (uint32_t)(q / S) & 1u;
-          if (!mbar_wait(&sb->fullA[s], ph, abort, gp.spin) || !mbar_wait(&sb->fullB[s], ph, abort, gp.spin)) {
+          const long long c1 = clock64();
+          const bool okA = mbar_wait(&sb->fullA[s], ph, abort, gp.spin);
+          const long long c2 = clock64();
+          const bool okB = okA && mbar_wait(&sb->fullB[s], ph, abort, gp.spin);
+          w_a += c2 - c1;
+          w_b += clock64() - c2;
+          if (!okB) {
             record_error(I.err, 13);
             live = false;
             break;
@@ -531,6 +575,10 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       }
       mma_commit(&sb->done);
       mbar_drain(&sb->done, 0);
+      add_waits(gp.waits, kWaitCta, clock64() - t_start);
+      add_waits(gp.waits, kWaitA, w_a);
+      add_waits(gp.waits, kWaitB, w_b);
+      add_waits(gp.waits, kWaitTmem, w_tmem);
     }
   }
   tc_fence_before();
@@ -590,11 +638,13 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
   const uint32_t tmem = sb->tmem_base;
   auto stage_A = [&](int s) { return base + (size_t)s * C::kStage; };
   auto stage_B = [&](int s) { return base + (size_t)s * C::kStage + NP * C::kA; };
+  unsigned long long* const waits = gp.waits ? gp.waits + 8 : nullptr;
 
   if (warp < 4) {
     // ---- epilogue: TMEM rows r, columns (z, part) -> fields[md][field][z][r]
     const int quarter = warp;
     int it = 0;
+    long long busy = 0;
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
       const int4 tl = tiles[ti];
       int md, g, fb;
@@ -606,6 +656,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         if (lane == 0) record_error(I.err, 24);
         break;
       }
+      const long long c1 = clock64();
       tc_fence_after();
       const int n = I.n, Nz = I.Nz, z0 = tl.z;
       const int r = tl.w + quarter * 32 + lane;
@@ -635,12 +686,15 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sb->tempty[b]);
+      busy += clock64() - c1;
     }
+    if (warp == 0 && lane == 0) add_waits(waits, kBusyEpi, busy);
   } else if (warp == 4) {
     // ---- producer: pre-tiled Q pieces and coefficient pieces, one bulk copy each per piece
     if (lane == 0) {
       int q = 0;
       bool live = true;
+      long long w_stage = 0;
       for (int ti = blockIdx.x; live && ti < ntiles; ti += gridDim.x) {
         const int4 tl = tiles[ti];
         int md, g, fb, bl[2];
@@ -651,7 +705,10 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
           const uint32_t ph = (uint32_t)(q / S) & 1u;
-          if (!mbar_wait(&sb->empty[s], ph ^ 1u, abort, gp.spin)) {
+          const long long c0 = clock64();
+          const bool freed = mbar_wait(&sb->empty[s], ph ^ 1u, abort, gp.spin);
+          w_stage += clock64() - c0;
+          if (!freed) {
             record_error(I.err, 21);
             live = false;
             break;
@@ -668,6 +725,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
           }
         }
       }
+      add_waits(waits, kWaitStage, w_stage);
       if (!live) {
         for (int k = 1; k <= S; ++k) {
           const int qq = q - k;
@@ -682,6 +740,8 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
       const uint32_t idesc = idesc_bf16(TN, true);
       int q = 0, it = 0;
       bool live = true;
+      const long long t_start = clock64();
+      long long w_b = 0, w_tmem = 0;
       for (int ti = blockIdx.x; live && ti < ntiles; ti += gridDim.x, ++it) {
         const int4 tl = tiles[ti];
         int md, g, fb, bl[2];
@@ -691,7 +751,10 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         const int T = back_blocks(g, fb, bl) * ks;
         const int b = NBUF == 2 ? (it & 1) : 0;
         const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
-        if (!mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort, gp.spin)) {
+        const long long c0 = clock64();
+        const bool freed = mbar_wait(&sb->tempty[b], (use & 1u) ^ 1u, abort, gp.spin);
+        w_tmem += clock64() - c0;
+        if (!freed) {
           record_error(I.err, 25);
           break;
         }
@@ -700,7 +763,10 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
           const uint32_t ph = (uint32_t)(q / S) & 1u;
-          if (!mbar_wait(&sb->fullB[s], ph, abort, gp.spin)) {
+          const long long c1 = clock64();
+          const bool okB = mbar_wait(&sb->fullB[s], ph, abort, gp.spin);
+          w_b += clock64() - c1;
+          if (!okB) {
             record_error(I.err, 23);
             live = false;
             break;
@@ -728,6 +794,9 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
       }
       mma_commit(&sb->done);
       mbar_drain(&sb->done, 0);
+      add_waits(waits, kWaitCta, clock64() - t_start);
+      add_waits(waits, kWaitB, w_b);
+      add_waits(waits, kWaitTmem, w_tmem);
     }
   }
   tc_fence_before();
@@ -766,6 +835,7 @@ struct TcPlan {
   size_t bytes = 0;
   TcConfig cfg;
   long long spin = -1;   // pipeline wait limit of the single-instance launches (< 0: kSpinLimit)
+  unsigned long long* waits = nullptr;  // pipeline cycle counters of the single-instance launches (or null)
   // one-instance groups used by tc_project / tc_backproject, without (0) and with (1) a current:
   // the tile tables depend only on the shapes, the pointers are kernel parameters
   TcGroup* self[2] = {nullptr, nullptr};
@@ -1176,6 +1246,7 @@ static cudaError_t self_group(TcPlan* t, const void* fields, const void* J, void
   }
   GroupParams& gp = t->self[h]->params;
   gp.spin = t->spin < 0 ? kSpinLimit : t->spin;
+  gp.waits = t->waits;
   GInst& I = gp.inst[0];
   const bool moved = I.fields != (float2*)fields || I.J != (const float2*)J;
   I.fields = (float2*)fields;
@@ -1205,10 +1276,13 @@ cudaError_t tc_backproject(TcPlan* t, void* fields, cudaStream_t st) {
   if (!G) return cudaErrorInvalidValue;
   G->params.inst[0].fields = (float2*)fields;
   G->params.spin = t->spin < 0 ? kSpinLimit : t->spin;
+  G->params.waits = t->waits;
   return launch_backproject(G, st);
 }
 
 void tc_set_wait_limit(TcPlan* t, long long polls) { t->spin = polls < 0 ? -1 : polls; }
+void tc_set_waits(TcPlan* t, unsigned long long* counters) { t->waits = counters; }
+void tc_group_set_waits(TcGroup* G, unsigned long long* counters) { G->params.waits = counters; }
 
 int tc_launches_per_step(const TcPlan*) { return 2; }
 

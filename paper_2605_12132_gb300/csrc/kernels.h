@@ -133,6 +133,7 @@ struct GroupParams {
   CUtensorMap jmap[kMaxGroupInstances];  // the same for J (unused entries zero)
   int count;
   long long spin;                         // polls before a pipeline wait gives up (kSpinLimit unless set)
+  unsigned long long* waits;              // pipeline cycle counters, 8 per kernel (null: not counted)
 };
 // Tile shapes and schedules of the persistent kernels (chosen by the autotuner):
 // tn_p / tn_b = N tile of the projection / back-projection (128 or 256); sched = tile order
@@ -163,6 +164,9 @@ int tc_launches_per_step(const TcPlan* p);
 // polls before a pipeline wait of this plan's single-instance launches gives up (< 0: the default limit;
 // 0: every wait gives up at once, which drives the timeout path on a healthy pipeline)
 void tc_set_wait_limit(TcPlan* p, long long polls);
+// pipeline cycle counters (16 device words: 8 of the projection, 8 of the back-projection; null stops counting)
+void tc_set_waits(TcPlan* p, unsigned long long* counters);
+void tc_group_set_waits(TcGroup* g, unsigned long long* counters);
 // grouped launches over up to kMaxGroupInstances instances of one precision
 cudaError_t tc_group_create(TcGroup** out, TcPlan* const* plans, const void* const* fields, const void* const* J,
                             int count, const TcConfig& cfg);
