@@ -153,6 +153,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 columns of two accumulators, issued without waiting: the registers are written asynchronously and must
+// not be read before tmem_wait2 on the same arrays, which the compiler sees as redefining them
+__device__ __forceinline__ void tmem_ld2x32(uint32_t ta, uint32_t tb, uint32_t* a, uint32_t* b) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%"
+      "48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+        "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
+        "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]),
+        "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]),
+        "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+        "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]),
+        "=r"(b[16]), "=r"(b[17]), "=r"(b[18]), "=r"(b[19]), "=r"(b[20]), "=r"(b[21]), "=r"(b[22]), "=r"(b[23]),
+        "=r"(b[24]), "=r"(b[25]), "=r"(b[26]), "=r"(b[27]), "=r"(b[28]), "=r"(b[29]), "=r"(b[30]), "=r"(b[31])
+      : "r"(ta), "r"(tb));
+}
+__device__ __forceinline__ void tmem_wait2(uint32_t* a, uint32_t* b) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                 "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]),
+                 "+r"(a[15]), "+r"(a[16]), "+r"(a[17]), "+r"(a[18]), "+r"(a[19]), "+r"(a[20]), "+r"(a[21]),
+                 "+r"(a[22]), "+r"(a[23]), "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]), "+r"(a[28]),
+                 "+r"(a[29]), "+r"(a[30]), "+r"(a[31]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                 "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]),
+                 "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]), "+r"(b[16]), "+r"(b[17]),
+                 "+r"(b[18]), "+r"(b[19]), "+r"(b[20]), "+r"(b[21]), "+r"(b[22]), "+r"(b[23]), "+r"(b[24]),
+                 "+r"(b[25]), "+r"(b[26]), "+r"(b[27]), "+r"(b[28]), "+r"(b[29]), "+r"(b[30]), "+r"(b[31])
+               :
+               : "memory");
+}
+
+// the N extent of a projection tile starting at output j0 of an instance with n outputs: the rest of the
+// instance rounded up to the MMA granularity of 16, at most the tile width TN
+__host__ __device__ __forceinline__ int tile_n(int TN, int n, int j0) {
+  const int r = ((n - j0) + 15) & ~15;
+  return r < TN ? r : TN;
+}
+
 // products (ia, ib) with ia + ib < NP, leading product first
 template <int NP>
 __device__ __forceinline__ void product(int p, int& ia, int& ib) {
@@ -435,20 +475,20 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       const int z = z0 + (row >> 1), part = row & 1;
       float* out = I.coef + (size_t)(md * 9 + g * 3 + ob) * n * 2 * Nz + 2 * z + part;
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * NACC * TN);
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        if (j0 + c0 >= n) break;
-        float v[32];
-        tmem_ld32(tbase + c0, v);
-        if (NACC == 2) {
-          float w[32];
-          tmem_ld32(tbase + TN + c0, w);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += w[i];
-        }
+      // 32-column chunks that hold outputs j < n; NACC = 1 reads its single accumulator twice (the
+      // second copy unused) so that both forms share one load instruction pair
+      const int nch = (tile_n(TN, n, j0) + 31) >> 5;
+      const uint32_t corr = NACC == 2 ? (uint32_t)TN : 0u;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int c0 = 32 * ch;
+        uint32_t lead[32], cr[32];
+        tmem_ld2x32(tbase + c0, tbase + corr + c0, lead, cr);  // both accumulators, one wait
+        tmem_wait2(lead, cr);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
+          const float v = NACC == 2 ? __uint_as_float(lead[i]) + __uint_as_float(cr[i]) : __uint_as_float(lead[i]);
           const int j = j0 + c0 + i;
-          if (j < n) out[(size_t)j * 2 * Nz] = v[i];
+          if (j < n) out[(size_t)j * 2 * Nz] = v;
         }
       }
       tc_fence_before();
@@ -469,6 +509,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       const GInst& I = gp.inst[tl.x];
       const int n = I.n, Nz = I.Nz, nks = (n + 31) >> 5, z0 = tl.z, j0 = tl.w;
       const int T = proj_blocks(g, ob, bl) * nks;
+      const uint32_t bbytes = (uint32_t)tile_n(TN, n, j0) * 64u;  // one B piece: ne rows of 32 K bf16
       for (int t = 0; t < T; ++t, ++q) {
         const int s = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
@@ -492,15 +533,16 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
             const int field = (g == 1) ? (ib == 0 ? 4 : (ib == 1 ? 3 : 5)) : ib;
             tma_load_2d(stage_A(s), &gp.fmap[tl.x], &sb->fullS[s], 2 * r0, (md * 6 + field) * Nz + z0);
           }
-          mbar_expect_tx(&sb->fullB[s], (uint32_t)NP * C::kBp);
+          mbar_expect_tx(&sb->fullB[s], (uint32_t)NP * bbytes);
         }
         __syncwarp();
         if (lane < NP) {
-          // P block (md, g, piece, ob, ib, rs, jb): 128 rows x 32 K, 8 KB; TN/128 consecutive jb blocks
+          // P block (md, g, piece, ob, ib, rs, jb): 128 rows x 32 K, 8 KB; the tile's rows j0 .. j0 + ne - 1
+          // are contiguous over consecutive jb blocks (whole 8-row swizzle atoms, ne a multiple of 16)
           const size_t blk = (((((size_t)(md * 2 + (g == 1 ? 1 : 0)) * NP + lane) * 3 + ob) * 3 + ib) * nks + rs) *
                                  I.njb +
                              (j0 >> 7);
-          bulk_g2s(stage_B(s) + lane * C::kBp, I.P + blk * 8192, C::kBp, &sb->fullB[s]);
+          bulk_g2s(stage_B(s) + lane * C::kBp, I.P + blk * 8192, bbytes, &sb->fullB[s]);
         }
       }
     }
@@ -517,7 +559,6 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
   } else {
     // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(TN, false);
       int q = 0, it = 0;
       bool live = true;
       const long long t_start = clock64();
@@ -529,6 +570,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         const GInst& I = gp.inst[tl.x];
         const int nks = (I.n + 31) >> 5;
         const int T = proj_blocks(g, ob, bl) * nks;
+        const uint32_t idesc = idesc_bf16(tile_n(TN, I.n, tl.w), false);
         const int b = NBUF == 2 ? (it & 1) : 0;
         const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
         const long long c0 = clock64();
@@ -985,10 +1027,11 @@ static cudaError_t build_tiles(TcGroup* G) {
       for (int g = 0; g < ngroups; ++g)
         for (int ob = 0; ob < 3; ++ob) {
           const bool single = (g != 1 && ob == 0) || (g == 1 && ob == 2);
-          const int cost = (single ? 1 : 2) * t->nks;
-          for (int j0 = 0; j0 < t->n; j0 += c.tn_p)
+          for (int j0 = 0; j0 < t->n; j0 += c.tn_p) {
+            const int cost = (single ? 1 : 2) * t->nks * tile_n(c.tn_p, t->n, j0);  // stages x MMA width
             for (int z0 = 0; z0 < t->Nz; z0 += 64)
               pt.push_back({cost, make_int4((int)k, md | g << 8 | ob << 12, z0, j0)});
+          }
         }
     for (int md = 0; md < t->nmodes; ++md)
       for (int g = 0; g < 2; ++g)
