@@ -424,6 +424,10 @@ int fdetd_host_tables(int Nz, int Nr, int m, int order, double dz, double dr, do
  * the hit and miss counts since the process started; any pointer may be NULL.  Both return FDETD_OK.
  */
 int fdetd_plan_cache_set_limit(size_t bytes);
+/* Computes the tables of `modes` for a radial grid (Nr, order, dr) into the cache unless they are there
+ * (a server precomputing the grids it expects); host only, thread-safe.  FDETD_ERR_ARG for invalid
+ * arguments, FDETD_ERR_EIG if an eigen-decomposition fails. */
+int fdetd_plan_cache_warm(int Nr, int order, double dr, const int* modes, int nmodes);
 int fdetd_plan_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits, uint64_t* misses);
 
 /* Host-only: staggered (kind 0), centred first (1), centred second (2, e0 first) derivative

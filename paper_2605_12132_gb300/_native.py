@@ -58,6 +58,7 @@ def lib():
     L.fdetd_host_spectral_order.argtypes = [c_int, c_int, c_vp]
     L.fdetd_host_spectral_radices.argtypes = [c_int, c_int, ctypes.POINTER(c_int)]
     L.fdetd_plan_cache_set_limit.argtypes = [ctypes.c_size_t]
+    L.fdetd_plan_cache_warm.argtypes = [c_int, c_int, c_dbl, ctypes.POINTER(c_int), c_int]
     L.fdetd_plan_cache_stats.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                          ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64)]
@@ -401,6 +402,12 @@ def fdetd_host_spectral_radices(Nz, precision="bf16x6"):
 def fdetd_plan_cache_set_limit(nbytes):
     """Byte limit of the process-wide cache of per-mode radial tables (0 empties and disables it)."""
     _check(lib().fdetd_plan_cache_set_limit(int(nbytes)))
+
+
+def fdetd_plan_cache_warm(Nr, order, dr, modes):
+    """Compute the radial tables of `modes` on the grid (Nr, order, dr) into the cache (host only)."""
+    m = (ctypes.c_int * len(modes))(*modes)
+    _check(lib().fdetd_plan_cache_warm(int(Nr), int(order), float(dr), m, len(modes)))
 
 
 def fdetd_plan_cache_stats():

@@ -754,6 +754,18 @@ extern "C" int fdetd_plan_cache_set_limit(size_t bytes) {
   return FDETD_OK;
 }
 
+extern "C" int fdetd_plan_cache_warm(int Nr, int order, double dr, const int* modes, int nmodes) {
+  if (order < 2 || order > 32 || (order & 1) || Nr < order / 2 + 2 || !(dr > 0) || nmodes < 1 || !modes)
+    return fail(FDETD_ERR_ARG, "invalid order, Nr, dr or modes");
+  for (int i = 0; i < nmodes; ++i) {
+    if (modes[i] < 0 || modes[i] > 64) return fail(FDETD_ERR_ARG, "mode numbers must be 0..64");
+    std::string msg;
+    const int rc = mode_cache_warm(Nr, order, dr, modes[i], msg);
+    if (rc) return fail(rc == 4 ? FDETD_ERR_EIG : FDETD_ERR_ARG, msg);
+  }
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_plan_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits,
                                       uint64_t* misses) {
   mode_cache_stats(bytes, limit, entries, hits, misses);

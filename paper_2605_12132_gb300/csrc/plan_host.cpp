@@ -678,6 +678,19 @@ int cached_mode(ModePlan& P, int n, int order, double dr, int m, std::string& ms
 
 }  // namespace
 
+int mode_cache_warm(int n, int order, double dr, int m, std::string& msg) {
+  ModeKey key{n, order, m, 0};
+  std::memcpy(&key.dr_bits, &dr, sizeof(dr));
+  {
+    ModeCache& c = mode_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    for (const auto& e : c.lru)
+      if (e.first == key) return 0;
+  }
+  ModePlan P;
+  return cached_mode(P, n, order, dr, m, msg);
+}
+
 void mode_cache_set_limit(size_t bytes) {
   ModeCache& c = mode_cache();
   std::lock_guard<std::mutex> lk(c.mu);

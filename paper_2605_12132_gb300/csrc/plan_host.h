@@ -59,6 +59,8 @@ int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, 
 // Process-wide cache of per-mode radial tables (keyed on Nr, order, dr, m): byte limit (0 empties and disables
 // it; default 4 GiB) and counters.
 void mode_cache_set_limit(size_t bytes);
+// Builds mode m's tables into the cache unless present (0, or 4 with msg for a failed eigen-solve).
+int mode_cache_warm(int n, int order, double dr, int m, std::string& msg);
 void mode_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits, uint64_t* misses);
 
 // Banded radial operators of H for the Taylor scheme (layout documented at the definition).

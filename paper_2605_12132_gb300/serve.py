@@ -192,6 +192,17 @@ class Server:
         self.tickets.append(t)
         return t
 
+    def prewarm(self, requests, workers=8):
+        """Compute the radial tables of the field requests' grids into the library's plan cache before they
+        arrive (distinct (Nr, order, dr, mode) only, on `workers` threads; the calls release the GIL).
+        Returns the number of distinct mode tables."""
+        import concurrent.futures as cf
+        keys = sorted({(r.Nr, r.order, float(r.dr), m) for r in requests if r.kind == "field" for m in r.modes},
+                      key=lambda k: -k[0])
+        with cf.ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
+            list(ex.map(lambda k: nat.fdetd_plan_cache_warm(k[0], k[1], k[2], [k[3]]), keys))
+        return len(keys)
+
     def stats(self):
         s = _Stats()
         nat._check(_bind().fdetd_server_stats(self.handle, ctypes.byref(s)))

@@ -109,3 +109,19 @@ def test_cancel_queued_ends_only_the_waiting_requests():
     st = srv.stats()
     assert st["used_bytes"] == 0 and st["failed"] == n
     srv.close()
+
+
+def test_prewarm_fills_the_radial_table_cache_once_per_grid():
+    nat.fdetd_plan_cache_set_limit(0)
+    nat.fdetd_plan_cache_set_limit(1 << 30)
+    reqs = [_field(Nr=48, modes=(0, 1)), _field(Nr=48, modes=(1, 2), Nz=128), _envelope(), _field(Nr=40, modes=(0,))]
+    srv = serve.Server(1 << 30, dry_run=True)
+    assert srv.prewarm(reqs, workers=3) == 4          # (48, m) for m = 0, 1, 2 and (40, 0)
+    st = nat.fdetd_plan_cache_stats()
+    assert st["entries"] == 4 and st["misses"] >= 4
+    hits = st["hits"]
+    assert srv.prewarm(reqs) == 4
+    assert nat.fdetd_plan_cache_stats()["misses"] == st["misses"]   # already there: no new builds
+    assert nat.fdetd_plan_cache_stats()["hits"] == hits
+    srv.close()
+    nat.fdetd_plan_cache_set_limit(4 << 30)
