@@ -59,7 +59,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void l2_prefetch(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((uint64_t)src), "r"(bytes) : "memory");
 }
@@ -108,17 +110,30 @@ __device__ __forceinline__ void stage(float2* sm, const float2* tw, int ncol) {
   __syncthreads();
 }
 
+// forward stages 1 .. s (stage 0 runs column by column as the columns arrive, first_stage)
 template <int LOGN, int s>
 struct Forward {
-  static __device__ __forceinline__ void run(float2* sm, const float2* tw, int ncol) {
-    Forward<LOGN, s - 1>::run(sm, tw, ncol);
+  static __device__ __forceinline__ void run_after_first(float2* sm, const float2* tw, int ncol) {
+    Forward<LOGN, s - 1>::run_after_first(sm, tw, ncol);
     stage<LOGN, s, false>(sm, tw, ncol);
   }
 };
 template <int LOGN>
 struct Forward<LOGN, 0> {
-  static __device__ __forceinline__ void run(float2* sm, const float2* tw, int ncol) { stage<LOGN, 0, false>(sm, tw, ncol); }
+  static __device__ __forceinline__ void run_after_first(float2*, const float2*, int) {}
 };
+
+// Forward stage 0 of column a once its copy group (and, for a = 0, the twiddles) has landed; the copies of
+// the columns after it stay in flight.  Columns a >= ncol have empty groups and no work.
+template <int LOGN, int a>
+__device__ __forceinline__ void first_stage(float2* sm, const float2* tw, int ncol) {
+  if constexpr (a < 5) {
+    cp_wait<4 - a>();
+    __syncthreads();
+    if (a < ncol) stage<LOGN, 0, false>(sm + a * Shape<LOGN>::PC, tw, 1);
+    first_stage<LOGN, a + 1>(sm, tw, ncol);
+  }
+}
 // adjoint stages s .. 1 (stage 0's adjoint writes to global memory)
 template <int LOGN, int s>
 struct Inverse {
@@ -300,22 +315,25 @@ __global__ void __launch_bounds__(Shape<LOGN>::NT, Shape<LOGN>::MINB) spectral32
   const float2* coef = reinterpret_cast<const float2*>(args.coef);
   const PhaseF* phase = reinterpret_cast<const PhaseF*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * N;
   if (threadIdx.x == 0) l2_prefetch(phase, (uint32_t)(N * sizeof(PhaseF)));
-  // the family's columns into the padded layout and the twiddles behind them, 16 bytes per copy
+  // the twiddles and the family's columns into the padded layout, 16 bytes per copy, one commit group per
+  // column (group 0 also holds the twiddles; groups past ncol are empty): the first stage of column a runs
+  // while the columns after it are still arriving
   constexpr int PER = N / 2;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    if (a >= ncol) break;
-    const float2* col = coef + ((size_t)(md * 9 + column_of(fam, a)) * n + j) * N;
-#pragma unroll
-    for (int i = threadIdx.x; i < PER; i += NT) cp16(sm + a * SH::PC + pad16(2 * i), col + 2 * i);
-  }
   const float2* twg = reinterpret_cast<const float2*>(args.twiddle);
   for (int i = threadIdx.x; i < (SH::TW + 1) / 2; i += NT) cp16(tws + 2 * i, twg + 2 * i);
-  cp_wait_all();
-  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    if (a < ncol) {
+      const float2* col = coef + ((size_t)(md * 9 + column_of(fam, a)) * n + j) * N;
+#pragma unroll
+      for (int i = threadIdx.x; i < PER; i += NT) cp16(sm + a * SH::PC + pad16(2 * i), col + 2 * i);
+    }
+    cp_commit();
+  }
 
   static_assert(SH::S >= 2, "at least two stages");
-  Forward<LOGN, SH::S - 2>::run(sm, tws, ncol);
+  first_stage<LOGN, 0>(sm, tws, ncol);
+  Forward<LOGN, SH::S - 2>::run_after_first(sm, tws, ncol);
   const df lam = reinterpret_cast<const df*>(args.lam)[(md * 2 + fam) * n + j];
   fused_last<LOGN, HASJ>(sm, fam, phase, reinterpret_cast<const ZSymK*>(args.zsymk), lam, (float)args.dt,
                          1.0f / (float)N);
