@@ -186,6 +186,27 @@ __device__ __forceinline__ void tmem_wait2(uint32_t* a, uint32_t* b) {
                : "memory");
 }
 
+// 4 x 4 transpose over the four lanes 4g .. 4g+3 of a group (q = lane & 3): on entry x[c] is element (q, c) of
+// the group's block, on exit element (c, q).  Two butterfly exchanges: across lanes q ^ 1 the elements whose
+// column's low bit differs from q's, then across q ^ 2 those whose column's high bit differs.
+__device__ __forceinline__ void transpose4(float* x, int q) {
+  const bool lo = q & 1, hi = q & 2;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = lo ? x[2 * k] : x[2 * k + 1];
+    const float r = __shfl_xor_sync(0xffffffffu, send, 1);
+    if (lo) x[2 * k] = r;
+    else x[2 * k + 1] = r;
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = hi ? x[k] : x[k + 2];
+    const float r = __shfl_xor_sync(0xffffffffu, send, 2);
+    if (hi) x[k] = r;
+    else x[k + 2] = r;
+  }
+}
+
 // the N extent of a projection tile starting at output j0 of an instance with n outputs: the rest of the
 // instance rounded up to the MMA granularity of 16, at most the tile width TN
 __host__ __device__ __forceinline__ int tile_n(int TN, int n, int j0) {
@@ -471,24 +492,32 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       const long long c1 = clock64();
       tc_fence_after();
       const int n = I.n, Nz = I.Nz, z0 = tl.z, j0 = tl.w;
-      const int row = quarter * 32 + lane;
-      const int z = z0 + (row >> 1), part = row & 1;
-      float* out = I.coef + (size_t)(md * 9 + g * 3 + ob) * n * 2 * Nz + 2 * z + part;
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * NACC * TN);
       // 32-column chunks that hold outputs j < n; NACC = 1 reads its single accumulator twice (the
       // second copy unused) so that both forms share one load instruction pair
       const int nch = (tile_n(TN, n, j0) + 31) >> 5;
       const uint32_t corr = NACC == 2 ? (uint32_t)TN : 0u;
+      // lanes 4g .. 4g+3 hold four consecutive rows (contiguous in memory along z, re/im); a 4 x 4 transpose
+      // over each such group leaves lane 4g + q with column q of the block, so that it stores the four rows
+      // as one 16-byte vector: 8 vector stores per 32 columns instead of 32 scalar ones
+      const int q = lane & 3;
+      float* const out4 = I.coef + (size_t)(md * 9 + g * 3 + ob) * n * 2 * Nz + 2 * z0 + quarter * 32 + (lane & ~3);
       for (int ch = 0; ch < nch; ++ch) {
         const int c0 = 32 * ch;
         uint32_t lead[32], cr[32];
         tmem_ld2x32(tbase + c0, tbase + corr + c0, lead, cr);  // both accumulators, one wait
         tmem_wait2(lead, cr);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float v = NACC == 2 ? __uint_as_float(lead[i]) + __uint_as_float(cr[i]) : __uint_as_float(lead[i]);
-          const int j = j0 + c0 + i;
-          if (j < n) out[(size_t)j * 2 * Nz] = v;
+        for (int b4 = 0; b4 < 8; ++b4) {
+          float x[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int i = 4 * b4 + m;
+            x[m] = NACC == 2 ? __uint_as_float(lead[i]) + __uint_as_float(cr[i]) : __uint_as_float(lead[i]);
+          }
+          transpose4(x, q);
+          const int j = j0 + c0 + 4 * b4 + q;
+          if (j < n) *reinterpret_cast<float4*>(out4 + (size_t)j * 2 * Nz) = make_float4(x[0], x[1], x[2], x[3]);
         }
       }
       tc_fence_before();
