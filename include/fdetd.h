@@ -298,8 +298,15 @@ int fdetd_taylor_host_bands(int Nr, int order, double dr, int m, double* bands, 
  * buffers.  host_fields[k] / host_J[k] are instance k's fields and current in host memory, in
  * the layouts of fdetd_step (pinned memory gives asynchronous copies); host_J may be NULL when
  * no instance was added with a current.  Copies every instance's inputs to the registered device
- * buffers, replays the graph nlaunch times, copies the fields back into host_fields, and
- * synchronizes `stream` before returning.  FDETD_ERR_ARG for a missing graph or buffer.
+ * buffers, advances every instance by nlaunch times the captured steps, copies the fields back into
+ * host_fields, and synchronizes `stream` before returning.  FDETD_ERR_ARG for a missing graph or
+ * buffer.  Copies and compute overlap: the instances are split into up to
+ * fdetd_batch_set_host_pipeline(batch, parts) contiguous parts of about equal bytes (default 4; 1
+ * gives the serial form: all copies in, the main graph, all copies out), each with a one-step graph
+ * of its own (built at the first call with the main capture's tile shapes; results bitwise equal to
+ * the main graph's); part p's inputs are copied in on an internal stream, its graph runs on `stream`
+ * once they have landed, and its fields are copied out on a second internal stream while the next
+ * part computes.  The batch's graphs share the plans' scratch: do not run them concurrently.
  */
 int fdetd_batch_create(fdetd_batch_t* out);
 int fdetd_batch_add(fdetd_batch_t batch, fdetd_plan_t plan, void* fields, const void* J, int* index);
@@ -311,6 +318,7 @@ int fdetd_batch_set_profiling(fdetd_batch_t batch, int on);
 int fdetd_batch_collect_stage_times(fdetd_batch_t batch);
 int fdetd_batch_pipeline_waits(fdetd_batch_t batch, unsigned long long* out);
 int fdetd_batch_stage_times(fdetd_batch_t batch, double* ms, long* steps);
+int fdetd_batch_set_host_pipeline(fdetd_batch_t batch, int parts);
 int fdetd_batch_step_host(fdetd_batch_t batch, void* const* host_fields, const void* const* host_J, int nlaunch,
                           void* stream);
 int fdetd_batch_destroy(fdetd_batch_t batch);

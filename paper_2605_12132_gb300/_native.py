@@ -89,6 +89,7 @@ def lib():
     L.fdetd_batch_collect_stage_times.argtypes = [c_vp]
     L.fdetd_batch_stage_times.argtypes = [c_vp, dp, ctypes.POINTER(ctypes.c_long)]
     L.fdetd_batch_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.fdetd_batch_set_host_pipeline.argtypes = [c_vp, c_int]
     L.fdetd_plan_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fdetd_batch_step_host.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
@@ -580,6 +581,10 @@ class FdetdBatch:
         out = (ctypes.c_uint64 * 16)()
         _check(lib().fdetd_batch_pipeline_waits(self.handle, out))
         return pipeline_report(list(out))
+
+    def set_host_pipeline(self, parts):
+        """Parts of the host-buffer step whose copies overlap each other's compute (1: serial form)."""
+        _check(lib().fdetd_batch_set_host_pipeline(self.handle, int(parts)))
 
     def step_host(self, host_fields, host_J=None, nlaunch=1, stream=None):
         """Host-buffer form: copy every instance's fields (and J) in, replay the graph nlaunch times, copy the

@@ -816,6 +816,19 @@ struct fdetd_batch_s {
   // spectral branches have joined, after the grouped back-projections (recorded as graph nodes)
   int profiling = 0;
   unsigned long long* d_waits = nullptr;  // pipeline cycle counters of the grouped kernels (profiling)
+  // host-buffer step: the instances split into parts with a one-step graph each, so that the copies of one part
+  // overlap the compute of another (built at the first fdetd_batch_step_host, dropped with the main graph)
+  struct Part {
+    std::vector<int> members;
+    std::vector<Group> groups;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t in = nullptr, done = nullptr;
+  };
+  std::vector<Part> parts;
+  int host_parts = 4;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   std::vector<cudaEvent_t> stage_ev;
   double stage_ms[3] = {0, 0, 0};
   long stage_calls = 0;
@@ -826,7 +839,20 @@ static void batch_release_events(fdetd_batch_s* b) {
   b->stage_ev.clear();
 }
 
+static void batch_release_parts(fdetd_batch_s* b) {
+  for (auto& P : b->parts) {
+    if (P.exec) cudaGraphExecDestroy(P.exec);
+    if (P.graph) cudaGraphDestroy(P.graph);
+    for (auto& g : P.groups)
+      if (g.g) tc_group_destroy(g.g);
+    if (P.in) cudaEventDestroy(P.in);
+    if (P.done) cudaEventDestroy(P.done);
+  }
+  b->parts.clear();
+}
+
 static void batch_release_graph(fdetd_batch_s* b) {
+  batch_release_parts(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
@@ -872,18 +898,14 @@ extern "C" int fdetd_batch_add(fdetd_batch_t b, fdetd_plan_t plan, void* fields,
 // captures `nsteps` steps: per step, one grouped projection launch per group, every instance's
 // spectral kernel on its own branch, one grouped back-projection launch per group.  Instances on
 // the CUDA-core paths run their own step sequence on concurrent branches.
-extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
-  if (!b || nsteps < 1) return fail(FDETD_ERR_ARG, "bad batch or nsteps");
-  if (b->inst.empty()) return fail(FDETD_ERR_ARG, "empty batch");
-  for (auto& i : b->inst)
-    if (i.plan->profiling) return fail(FDETD_ERR_ARG, "turn profiling off before capturing");
-  batch_release_graph(b);
-  cudaStream_t s0 = (cudaStream_t)stream;
-  // ---- groups (built and tuned before the capture: tile tables are uploaded synchronously)
+// Tensor-core groups over the instances `ids`: by precision, at most kMaxGroupInstances per group; tile shapes
+// autotuned on the instances' data, or taken from `like` (a group list of the same batch) when given.
+static int build_groups(fdetd_batch_s* b, const std::vector<int>& ids_all, cudaStream_t s0,
+                        const std::vector<fdetd_batch_s::Group>* like, std::vector<fdetd_batch_s::Group>& out) {
   for (int np : {2, 3}) {
     std::vector<int> ids;
-    for (size_t k = 0; k < b->inst.size(); ++k)
-      if (b->inst[k].plan->tc && tc_pieces(b->inst[k].plan->tc) == np) ids.push_back((int)k);
+    for (int k : ids_all)
+      if (b->inst[k].plan->tc && tc_pieces(b->inst[k].plan->tc) == np) ids.push_back(k);
     for (size_t c0 = 0; c0 < ids.size(); c0 += kMaxGroupInstances) {
       fdetd_batch_s::Group G;
       G.members.assign(ids.begin() + c0, ids.begin() + std::min(ids.size(), c0 + (size_t)kMaxGroupInstances));
@@ -899,75 +921,66 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
         j.push_back(b->inst[k].J);
       }
       G.cfg = tc_default_config(np);
-      if (b->autotune) {
+      bool found = false;
+      if (like)
+        for (const auto& L : *like)
+          if (!found && L.g && tc_pieces(b->inst[L.members[0]].plan->tc) == np) {
+            G.cfg = L.cfg;
+            found = true;
+          }
+      if (!found && b->autotune) {
         int rc = tune_group(pl, f, j, s0, &G.cfg, G.tuned_ms);
-        if (rc) {
-          batch_release_graph(b);
-          return rc;
-        }
+        if (rc) return rc;
       }
       cudaError_t e = tc_group_create(&G.g, tp.data(), fc.data(), j.data(), (int)G.members.size(), G.cfg);
-      if (e != cudaSuccess) {
-        batch_release_graph(b);
-        return fail(FDETD_ERR_CUDA, std::string("batch group: ") + cudaGetErrorString(e));
-      }
+      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("batch group: ") + cudaGetErrorString(e));
       for (size_t k = 0; k < G.members.size(); ++k) tc_group_set_coef(G.g, (int)k, pl[k]->d_coef);
-      if (b->profiling) {
-        cudaError_t e2 = b->d_waits ? cudaSuccess : cudaMalloc(&b->d_waits, 16 * sizeof(unsigned long long));
-        if (e2 == cudaSuccess) e2 = cudaMemset(b->d_waits, 0, 16 * sizeof(unsigned long long));
-        if (e2 != cudaSuccess) {
-          tc_group_destroy(G.g);
-          batch_release_graph(b);
-          return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e2));
-        }
-        tc_group_set_waits(G.g, b->d_waits);
-      }
-      b->groups.push_back(G);
+      out.push_back(G);
     }
   }
-  if (cudaStreamSynchronize(s0) != cudaSuccess) return fail(FDETD_ERR_CUDA, "batch: stream error before capture");
-  // ---- capture
+  return FDETD_OK;
+}
+
+// Captures `nsteps` steps of the instances `ids` (their groups already built) into a graph: per step, one grouped
+// projection launch per group, every instance's spectral kernel on its own branch, one grouped back-projection
+// launch per group; CUDA-core instances run their own step sequence on a branch.  With `marks`, event nodes
+// stamp each step's stage boundaries (marks[4 step + 0..3]).
+static int capture_steps(fdetd_batch_s* b, const std::vector<int>& ids, std::vector<fdetd_batch_s::Group>& groups,
+                         int nsteps, cudaStream_t s0, const std::vector<cudaEvent_t>* marks, cudaGraph_t* graph_out,
+                         cudaGraphExec_t* exec_out) {
+  *graph_out = nullptr;
+  *exec_out = nullptr;
   cudaStream_t cap = s0;
   cudaStream_t own = nullptr;
   if (!cap) {  // the legacy default stream cannot be captured
     if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return fail(FDETD_ERR_CUDA, "stream");
     cap = own;
   }
-  batch_release_events(b);
-  if (b->profiling) {
-    b->stage_ev.resize((size_t)4 * nsteps, nullptr);
-    for (auto& ev : b->stage_ev)
-      if (cudaEventCreate(&ev) != cudaSuccess) {
-        if (own) cudaStreamDestroy(own);
-        batch_release_events(b);
-        return fail(FDETD_ERR_CUDA, "batch: timing event creation failed");
-      }
-  }
   // recorded as event nodes of the graph (external), so that each replay stamps them
   auto mark = [&](int step, int k) -> cudaError_t {
-    return b->profiling ? cudaEventRecordWithFlags(b->stage_ev[(size_t)4 * step + k], cap, cudaEventRecordExternal)
-                        : cudaSuccess;
+    return marks ? cudaEventRecordWithFlags((*marks)[(size_t)4 * step + k], cap, cudaEventRecordExternal)
+                 : cudaSuccess;
   };
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int rc = FDETD_OK;
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
-  // CUDA-core instances: their own step sequence on a side branch
   std::vector<int> simt;
-  for (size_t k = 0; e == cudaSuccess && rc == FDETD_OK && k < b->inst.size(); ++k) {
+  for (int k : ids) {
+    if (e != cudaSuccess || rc != FDETD_OK) break;
     if (b->inst[k].plan->tc) continue;
-    simt.push_back((int)k);
+    simt.push_back(k);
     e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
     if (e == cudaSuccess) rc = fdetd_step(b->inst[k].plan, b->inst[k].fields, b->inst[k].J, nsteps, b->side[k]);
   }
   for (int s = 0; s < nsteps && e == cudaSuccess && rc == FDETD_OK; ++s) {
     e = mark(s, 0);
-    for (auto& G : b->groups) {
+    for (auto& G : groups) {
       if (e != cudaSuccess) break;
       e = tc_group_project(G.g, cap);
     }
     if (e == cudaSuccess) e = mark(s, 1);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, cap);
-    for (auto& G : b->groups)
+    for (auto& G : groups)
       for (int k : G.members) {
         if (e != cudaSuccess || rc != FDETD_OK) break;
         e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
@@ -976,7 +989,7 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
         if (e == cudaSuccess && rc == FDETD_OK) e = cudaStreamWaitEvent(cap, b->join[k], 0);
       }
     if (e == cudaSuccess && rc == FDETD_OK) e = mark(s, 2);
-    for (auto& G : b->groups) {
+    for (auto& G : groups) {
       if (e != cudaSuccess || rc != FDETD_OK) break;
       e = tc_group_backproject(G.g, cap);
     }
@@ -995,13 +1008,50 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
     return rc;
   }
   if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    b->exec = nullptr;
     return fail(FDETD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
-  b->graph = g;
+  *graph_out = g;
+  *exec_out = ex;
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
+  if (!b || nsteps < 1) return fail(FDETD_ERR_ARG, "bad batch or nsteps");
+  if (b->inst.empty()) return fail(FDETD_ERR_ARG, "empty batch");
+  for (auto& i : b->inst)
+    if (i.plan->profiling) return fail(FDETD_ERR_ARG, "turn profiling off before capturing");
+  batch_release_graph(b);
+  cudaStream_t s0 = (cudaStream_t)stream;
+  std::vector<int> all(b->inst.size());
+  for (size_t k = 0; k < all.size(); ++k) all[k] = (int)k;
+  // groups are built and tuned before the capture: tile tables are uploaded synchronously
+  int rc = build_groups(b, all, s0, nullptr, b->groups);
+  if (rc == FDETD_OK && b->profiling) {
+    cudaError_t e2 = b->d_waits ? cudaSuccess : cudaMalloc(&b->d_waits, 16 * sizeof(unsigned long long));
+    if (e2 == cudaSuccess) e2 = cudaMemset(b->d_waits, 0, 16 * sizeof(unsigned long long));
+    if (e2 != cudaSuccess) rc = fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e2));
+    for (auto& G : b->groups) tc_group_set_waits(G.g, b->d_waits);
+  }
+  if (rc != FDETD_OK) {
+    batch_release_graph(b);
+    return rc;
+  }
+  if (cudaStreamSynchronize(s0) != cudaSuccess) return fail(FDETD_ERR_CUDA, "batch: stream error before capture");
+  batch_release_events(b);
+  if (b->profiling) {
+    b->stage_ev.resize((size_t)4 * nsteps, nullptr);
+    for (auto& ev : b->stage_ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        batch_release_events(b);
+        return fail(FDETD_ERR_CUDA, "batch: timing event creation failed");
+      }
+  }
+  rc = capture_steps(b, all, b->groups, nsteps, s0, b->profiling ? &b->stage_ev : nullptr, &b->graph, &b->exec);
+  if (rc != FDETD_OK) return rc;
   b->steps = nsteps;
   return FDETD_OK;
 }
@@ -1074,29 +1124,114 @@ extern "C" int fdetd_batch_stage_times(fdetd_batch_t b, double* ms, long* steps)
   return FDETD_OK;
 }
 
+static size_t inst_field_bytes(const fdetd_plan_s* p) {
+  return 6 * (size_t)p->nmodes * p->Nz * p->Nr * (p->precision == FDETD_PREC_FP64 ? 16 : 8);
+}
+
+// Splits the instances into at most host_parts contiguous parts of about equal bytes and captures a one-step
+// graph for each (groups with the tile shapes the main capture chose).
+static int build_parts(fdetd_batch_s* b, cudaStream_t st) {
+  batch_release_parts(b);
+  const int n = (int)b->inst.size();
+  const int P = std::max(1, std::min(b->host_parts, n));
+  size_t total = 0;
+  for (auto& i : b->inst) total += inst_field_bytes(i.plan);
+  std::vector<int> cur;
+  size_t acc = 0;
+  for (int k = 0; k < n; ++k) {
+    cur.push_back(k);
+    acc += inst_field_bytes(b->inst[k].plan);
+    const bool last = k == n - 1;
+    if (last || (acc * P >= total * (b->parts.size() + 1) && (int)b->parts.size() < P - 1)) {
+      b->parts.emplace_back();
+      b->parts.back().members = cur;
+      cur.clear();
+    }
+  }
+  if (!b->s_in && cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(FDETD_ERR_CUDA, "stream");
+  if (!b->s_out && cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(FDETD_ERR_CUDA, "stream");
+  if (!b->ev_start && cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming) != cudaSuccess)
+    return fail(FDETD_ERR_CUDA, "event");
+  if (!b->ev_end && cudaEventCreateWithFlags(&b->ev_end, cudaEventDisableTiming) != cudaSuccess)
+    return fail(FDETD_ERR_CUDA, "event");
+  for (auto& part : b->parts) {
+    int rc = build_groups(b, part.members, st, &b->groups, part.groups);
+    if (rc == FDETD_OK && (cudaEventCreateWithFlags(&part.in, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&part.done, cudaEventDisableTiming) != cudaSuccess))
+      rc = fail(FDETD_ERR_CUDA, "event");
+    if (rc == FDETD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(FDETD_ERR_CUDA, "stream error");
+    if (rc == FDETD_OK) rc = capture_steps(b, part.members, part.groups, 1, st, nullptr, &part.graph, &part.exec);
+    if (rc != FDETD_OK) {
+      batch_release_parts(b);
+      return rc;
+    }
+  }
+  return FDETD_OK;
+}
+
+extern "C" int fdetd_batch_set_host_pipeline(fdetd_batch_t b, int parts) {
+  if (!b || parts < 1) return fail(FDETD_ERR_ARG, "bad batch or parts < 1");
+  if (parts != b->host_parts) batch_release_parts(b);
+  b->host_parts = parts;
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_batch_step_host(fdetd_batch_t b, void* const* host_fields, const void* const* host_J,
                                      int nlaunch, void* stream) {
   if (!b || !b->exec || !host_fields) return fail(FDETD_ERR_ARG, "batch has no captured graph or null fields");
   if (nlaunch < 0) return fail(FDETD_ERR_ARG, "nlaunch < 0");
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaSuccess;
-  for (size_t k = 0; k < b->inst.size() && e == cudaSuccess; ++k) {
-    const fdetd_plan_s* p = b->inst[k].plan;
-    const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
-    const size_t plane = (size_t)p->nmodes * p->Nz * p->Nr * elt;
+  for (size_t k = 0; k < b->inst.size(); ++k) {
     if (!host_fields[k]) return fail(FDETD_ERR_ARG, "null host fields");
-    e = cudaMemcpyAsync(b->inst[k].fields, host_fields[k], 6 * plane, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && b->inst[k].J) {
-      if (!host_J || !host_J[k]) return fail(FDETD_ERR_ARG, "instance was added with a current: host J needed");
-      e = cudaMemcpyAsync((void*)b->inst[k].J, host_J[k], 3 * plane, cudaMemcpyHostToDevice, st);
-    }
+    if (b->inst[k].J && (!host_J || !host_J[k]))
+      return fail(FDETD_ERR_ARG, "instance was added with a current: host J needed");
   }
-  for (int s = 0; s < nlaunch && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->exec, st);
-  for (size_t k = 0; k < b->inst.size() && e == cudaSuccess; ++k) {
+  cudaStream_t st = (cudaStream_t)stream;
+  auto h2d = [&](int k, cudaStream_t s) {
     const fdetd_plan_s* p = b->inst[k].plan;
-    const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
-    e = cudaMemcpyAsync(host_fields[k], b->inst[k].fields, 6 * (size_t)p->nmodes * p->Nz * p->Nr * elt,
-                        cudaMemcpyDeviceToHost, st);
+    const size_t fb = inst_field_bytes(p);
+    cudaError_t e = cudaMemcpyAsync(b->inst[k].fields, host_fields[k], fb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && b->inst[k].J)
+      e = cudaMemcpyAsync((void*)b->inst[k].J, host_J[k], fb / 2, cudaMemcpyHostToDevice, s);
+    return e;
+  };
+  auto d2h = [&](int k, cudaStream_t s) {
+    return cudaMemcpyAsync(host_fields[k], b->inst[k].fields, inst_field_bytes(b->inst[k].plan),
+                           cudaMemcpyDeviceToHost, s);
+  };
+  cudaError_t e = cudaSuccess;
+  if (b->host_parts <= 1 || b->inst.size() < 2 || nlaunch == 0) {
+    // serial form: every copy in, the main graph, every copy out, on the caller's stream
+    for (size_t k = 0; k < b->inst.size() && e == cudaSuccess; ++k) e = h2d((int)k, st);
+    for (int s = 0; s < nlaunch && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->exec, st);
+    for (size_t k = 0; k < b->inst.size() && e == cudaSuccess; ++k) e = d2h((int)k, st);
+  } else {
+    if (b->parts.empty()) {
+      const int rc = build_parts(b, st);
+      if (rc) return rc;
+    }
+    // copies in on s_in, the parts' graphs on the caller's stream, copies out on s_out: part p's copies
+    // overlap the compute of the parts around it; the copy engines of the two directions run concurrently
+    e = cudaEventRecord(b->ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_in, b->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_out, b->ev_start, 0);
+    for (auto& part : b->parts) {
+      for (int k : part.members)
+        if (e == cudaSuccess) e = h2d(k, b->s_in);
+      if (e == cudaSuccess) e = cudaEventRecord(part.in, b->s_in);
+    }
+    for (auto& part : b->parts) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, part.in, 0);
+      // a part's graph holds one step; the main graph holds b->steps
+      for (int s = 0; s < nlaunch * b->steps && e == cudaSuccess; ++s) e = cudaGraphLaunch(part.exec, st);
+      if (e == cudaSuccess) e = cudaEventRecord(part.done, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_out, part.done, 0);
+      for (int k : part.members)
+        if (e == cudaSuccess) e = d2h(k, b->s_out);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_end, b->s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_end, 0);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("batch host step: ") + cudaGetErrorString(e));
@@ -1111,6 +1246,10 @@ extern "C" int fdetd_batch_destroy(fdetd_batch_t b) {
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_waits) cudaFree(b->d_waits);
+  if (b->s_in) cudaStreamDestroy(b->s_in);
+  if (b->s_out) cudaStreamDestroy(b->s_out);
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
+  if (b->ev_end) cudaEventDestroy(b->ev_end);
   delete b;
   return FDETD_OK;
 }
