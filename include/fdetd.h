@@ -186,16 +186,19 @@ int fdetd_plan_set_profiling(fdetd_plan_t plan, int on);
 int fdetd_plan_kernel_times(fdetd_plan_t plan, double* ms, long* calls);
 
 /*
- * fdetd_plan_pipeline_waits - pipeline accounting of the tensor-core kernels (BF16X3 / BF16X6 plans),
- * counted while profiling is on (fdetd_plan_set_profiling(plan, 1) zeroes the counters).  out: 16
- * unsigned 64-bit SM clock-cycle sums over all CTAs and launches, out[0..7] for the projection and
- * out[8..15] for the back-projection: [0] CTA residency seen by the MMA-issuing thread, [1] MMA issuer
- * waiting for a stage's A operand (projection: the converted field pieces), [2] waiting for its B
- * operand (back-projection: both operands), [3] waiting for a free TMEM accumulator, [4] producer
- * waiting for a free stage, [5] converters waiting for the staged FP32 tile, [6] converters busy, [7]
- * epilogue busy (TMEM to global).  Slots a kernel lacks stay 0.  Synchronous (device-to-host copy);
- * FDETD_ERR_UNSUPPORTED for the CUDA-core precisions.  fdetd_batch_pipeline_waits reports the same
- * for a batch captured with profiling on (sum over its groups and graph replays).
+ * fdetd_plan_pipeline_waits - pipeline accounting, counted while profiling is on
+ * (fdetd_plan_set_profiling(plan, 1) zeroes the counters).  out: 24 unsigned 64-bit SM clock-cycle
+ * sums over all CTAs and launches.  out[0..7] the projection and out[8..15] the back-projection
+ * (tensor-core plans): [0] CTA residency seen by the MMA-issuing thread, [1] MMA issuer waiting for a
+ * stage's A operand (projection: the converted field pieces), [2] waiting for its B operand
+ * (back-projection: both operands), [3] waiting for a free TMEM accumulator, [4] producer waiting for
+ * a free stage, [5] converters waiting for the staged FP32 tile, [6] converters busy, [7] epilogue
+ * busy (TMEM to global).  out[16..23] the spectral kernel specialised on Nz (FP32 data, Nz = 2^k <=
+ * 4096): [16] block residency, [17] column loads and first forward stage, [18] other forward stages,
+ * [19] last forward stage + update + first inverse stage, [20] other inverse stages, [21] output
+ * stage, [22] blocks counted.  Slots a plan's kernels lack stay 0.  Synchronous (device-to-host
+ * copy).  fdetd_batch_pipeline_waits reports the tensor-core slots for a batch captured with
+ * profiling on (sum over its groups and graph replays; its spectral slots stay 0).
  */
 int fdetd_plan_pipeline_waits(fdetd_plan_t plan, unsigned long long* out);
 

@@ -125,8 +125,13 @@ PIPELINE_SLOTS = ("cta", "mma_wait_a", "mma_wait_b", "mma_wait_tmem", "producer_
                   "converter_wait_staged", "converter_busy", "epilogue_busy")
 
 
+SPECTRAL_PHASES = ("cycles", "load_and_first_stage", "forward_stages", "middle_fused", "inverse_stages",
+                   "output_stage", "blocks")
+
+
 def pipeline_report(counters):
-    """The 16 raw counters as {kernel: {slot: share of the CTA residency}} plus the raw cycle sums."""
+    """The 24 raw counters as {kernel: {slot: share of the residency}} with the raw cycle sums: the two
+    tensor-core kernels' role waits, and the phases of the spectral kernel specialised on Nz (per block)."""
     rep = {}
     for k, name in enumerate(("projection", "backprojection")):
         c = counters[8 * k: 8 * k + 8]
@@ -134,6 +139,11 @@ def pipeline_report(counters):
         rep[name] = {"cycles": tot}
         if tot:
             rep[name].update({slot: c[i] / tot for i, slot in enumerate(PIPELINE_SLOTS) if i})
+    c = counters[16:24]
+    rep["spectral"] = {"cycles": c[0], "blocks": c[6]}
+    if c[0]:
+        rep["spectral"].update({ph: c[i] / c[0] for i, ph in enumerate(SPECTRAL_PHASES) if 1 <= i <= 5})
+        rep["spectral"]["cycles_per_block"] = c[0] / max(c[6], 1)
     return rep
 
 
@@ -176,7 +186,7 @@ class FdetdPlan:
 
     def pipeline_waits(self):
         """Pipeline cycle counters of the tensor-core kernels while profiling is on (see pipeline_report)."""
-        out = (ctypes.c_uint64 * 16)()
+        out = (ctypes.c_uint64 * 24)()
         _check(lib().fdetd_plan_pipeline_waits(self.handle, out))
         return pipeline_report(list(out))
 
@@ -578,7 +588,7 @@ class FdetdBatch:
 
     def pipeline_waits(self):
         """Pipeline cycle counters of the grouped tensor-core kernels of a batch captured with profiling on."""
-        out = (ctypes.c_uint64 * 16)()
+        out = (ctypes.c_uint64 * 24)()
         _check(lib().fdetd_batch_pipeline_waits(self.handle, out))
         return pipeline_report(list(out))
 

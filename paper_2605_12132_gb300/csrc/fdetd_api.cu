@@ -305,6 +305,7 @@ static SpectralArgs spectral_args(fdetd_plan_s* p, bool hasJ) {
   sa.n = p->Nr;
   sa.dt = p->dt;
   sa.hasJ = hasJ;
+  sa.phases = p->profiling && p->d_waits ? p->d_waits + 16 : nullptr;
   return sa;
 }
 
@@ -659,6 +660,9 @@ extern "C" int fdetd_plan_set_wait_limit(fdetd_plan_t p, long long polls) {
   return FDETD_OK;
 }
 
+// pipeline counters: 8 words of the projection, 8 of the back-projection, 8 of the spectral kernel
+constexpr int kWaitWords = 24;
+
 extern "C" int fdetd_plan_set_profiling(fdetd_plan_t p, int on) {
   if (!p) return fail(FDETD_ERR_ARG, "plan is null");
   prof_collect(p);
@@ -667,30 +671,27 @@ extern "C" int fdetd_plan_set_profiling(fdetd_plan_t p, int on) {
     p->kern_ms[k] = 0;
     p->kern_calls[k] = 0;
   }
-  if (p->tc) {
-    if (on) {
-      cudaError_t e = p->d_waits ? cudaSuccess : cudaMalloc(&p->d_waits, 16 * sizeof(unsigned long long));
-      if (e == cudaSuccess) e = cudaMemset(p->d_waits, 0, 16 * sizeof(unsigned long long));
-      if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e));
-    }
-    tc_set_waits(p->tc, on ? p->d_waits : nullptr);
+  if (on) {
+    cudaError_t e = p->d_waits ? cudaSuccess : cudaMalloc(&p->d_waits, kWaitWords * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(p->d_waits, 0, kWaitWords * sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e));
   }
+  if (p->tc) tc_set_waits(p->tc, on ? p->d_waits : nullptr);
   return FDETD_OK;
 }
 
 static int read_waits(const unsigned long long* d, unsigned long long* out) {
   if (!d) {
-    std::fill(out, out + 16, 0ull);
+    std::fill(out, out + kWaitWords, 0ull);
     return FDETD_OK;
   }
-  cudaError_t e = cudaMemcpy(out, d, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(out, d, kWaitWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e));
   return FDETD_OK;
 }
 
 extern "C" int fdetd_plan_pipeline_waits(fdetd_plan_t p, unsigned long long* out) {
   if (!p || !out) return fail(FDETD_ERR_ARG, "null argument");
-  if (!p->tc) return fail(FDETD_ERR_UNSUPPORTED, "only the tensor-core pipelines have pipeline counters");
   return read_waits(p->d_waits, out);
 }
 
@@ -1031,8 +1032,8 @@ extern "C" int fdetd_batch_capture(fdetd_batch_t b, int nsteps, void* stream) {
   // groups are built and tuned before the capture: tile tables are uploaded synchronously
   int rc = build_groups(b, all, s0, nullptr, b->groups);
   if (rc == FDETD_OK && b->profiling) {
-    cudaError_t e2 = b->d_waits ? cudaSuccess : cudaMalloc(&b->d_waits, 16 * sizeof(unsigned long long));
-    if (e2 == cudaSuccess) e2 = cudaMemset(b->d_waits, 0, 16 * sizeof(unsigned long long));
+    cudaError_t e2 = b->d_waits ? cudaSuccess : cudaMalloc(&b->d_waits, kWaitWords * sizeof(unsigned long long));
+    if (e2 == cudaSuccess) e2 = cudaMemset(b->d_waits, 0, kWaitWords * sizeof(unsigned long long));
     if (e2 != cudaSuccess) rc = fail(FDETD_ERR_CUDA, std::string("pipeline counters: ") + cudaGetErrorString(e2));
     for (auto& G : b->groups) tc_group_set_waits(G.g, b->d_waits);
   }

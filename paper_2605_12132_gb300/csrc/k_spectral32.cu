@@ -312,6 +312,9 @@ __global__ void __launch_bounds__(Shape<LOGN>::NT, Shape<LOGN>::MINB) spectral32
   const int n = args.n;
   const int j = blockIdx.x, fam = blockIdx.y, md = blockIdx.z;
   const int ncol = HASJ ? (fam == 0 ? 5 : 4) : 3;
+  // phase accounting (args.phases): thread 0's clock at the end of each phase; every phase ends at a barrier
+  long long ck[6];
+  ck[0] = clock64();
   const float2* coef = reinterpret_cast<const float2*>(args.coef);
   const PhaseF* phase = reinterpret_cast<const PhaseF*>(args.phase) + ((size_t)(md * 2 + fam) * n + j) * N;
   if (threadIdx.x == 0) l2_prefetch(phase, (uint32_t)(N * sizeof(PhaseF)));
@@ -333,11 +336,15 @@ __global__ void __launch_bounds__(Shape<LOGN>::NT, Shape<LOGN>::MINB) spectral32
 
   static_assert(SH::S >= 2, "at least two stages");
   first_stage<LOGN, 0>(sm, tws, ncol);
+  ck[1] = clock64();
   Forward<LOGN, SH::S - 2>::run_after_first(sm, tws, ncol);
+  ck[2] = clock64();
   const df lam = reinterpret_cast<const df*>(args.lam)[(md * 2 + fam) * n + j];
   fused_last<LOGN, HASJ>(sm, fam, phase, reinterpret_cast<const ZSymK*>(args.zsymk), lam, (float)args.dt,
                          1.0f / (float)N);
+  ck[3] = clock64();
   Inverse<LOGN, SH::S - 2>::run(sm, tws);
+  ck[4] = clock64();
 
   float2* out = reinterpret_cast<float2*>(args.coef);
   float2* dst[3];
@@ -348,6 +355,14 @@ __global__ void __launch_bounds__(Shape<LOGN>::NT, Shape<LOGN>::MINB) spectral32
     if (SPLIT) sc[a] = split_column(args.split_out, args.npieces, md, column_of(fam, a), j, args.split_kstages, N);
   }
   stage0_out<LOGN, SPLIT>(sm, tws, dst, sc);
+  if (args.phases && threadIdx.x == 0) {
+    ck[5] = clock64();
+    // [0] residency, [1] loads and first stage, [2] other forward stages, [3] last forward stage + update +
+    // first inverse stage, [4] other inverse stages, [5] output stage, [6] blocks
+    atomicAdd(args.phases + 0, (unsigned long long)(ck[5] - ck[0]));
+    for (int k = 1; k <= 5; ++k) atomicAdd(args.phases + k, (unsigned long long)(ck[k] - ck[k - 1]));
+    atomicAdd(args.phases + 6, 1ull);
+  }
 }
 
 template <int LOGN, bool HASJ, bool SPLIT>

@@ -29,6 +29,7 @@ struct SpectralArgs {
   int* err;              // the plan's device failure flag (the spectral kernel has no waits that could set it)
   void* src;             // [nmodes][2][3][n][Nz] complex<T>: kz-space source term (two-kernel path)
   const void* zsymk;     // [Nz] ZSymK, position order (FP32 data: the kernel specialised on Nz)
+  unsigned long long* phases;  // cycle counters of the Nz-specialised kernel's phases (8 words) or null
 };
 
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);

@@ -32,6 +32,8 @@ def _check_shares(rep):
             if slot in r:
                 assert 0.0 <= r[slot] <= 1.0 + 1e-9, (kern, slot, r[slot])
     assert rep["projection"]["converter_busy"] > 0 and rep["backprojection"]["epilogue_busy"] > 0
+    if rep["spectral"]["cycles"]:
+        assert abs(sum(rep["spectral"][k] for k in nat.SPECTRAL_PHASES[1:6]) - 1.0) < 1e-6
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
@@ -81,7 +83,19 @@ def test_batch_counters_cover_the_grouped_kernels():
         p.close()
 
 
-def test_counters_are_refused_on_cuda_core_plans():
-    plan = fd.fdetd_plan(64, 16, 0, 4, 1 / 16, 1 / 4, 1 / 16, precision="fp32")
-    with pytest.raises(fd.FdetdError):
-        plan.pipeline_waits()
+def test_cuda_core_plans_count_only_the_spectral_phases():
+    Nz, Nr = 256, 48
+    F, J = _inputs(Nz, Nr, 2, 5)
+    plan = fd.fdetd_plan(Nz, Nr, 1, 8, 1 / 16, 1 / 4, 1 / 16, precision="fp32")
+    f = torch.from_numpy(F).to(torch.complex64).cuda()
+    j = torch.from_numpy(J).to(torch.complex64).cuda()
+    plan.set_profiling(True)
+    fd.fdetd_step(plan, f, j, 2)
+    rep = plan.pipeline_waits()
+    plan.set_profiling(False)
+    plan.status()
+    assert rep["projection"]["cycles"] == 0 and rep["backprojection"]["cycles"] == 0
+    sp = rep["spectral"]
+    assert sp["blocks"] == 2 * 2 * 2 * Nr          # steps x modes x families x j
+    shares = [sp[k] for k in nat.SPECTRAL_PHASES[1:6]]
+    assert all(0.0 <= x <= 1.0 for x in shares) and abs(sum(shares) - 1.0) < 1e-6
