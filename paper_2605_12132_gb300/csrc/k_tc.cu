@@ -664,8 +664,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
 
 template <int NP, int NACC, int NBUF, int TN>
 struct BG {
-  static constexpr uint32_t kA = 8192u;       // one piece of the Q tile: 128 r x 32 j (64-byte rows)
-  static constexpr uint32_t kBp = TN * 64u;   // one piece of the coefficient tile: 32 j x TN (z, part)
+  static constexpr uint32_t kA = 16384u;      // one piece of the Q tile: 128 r x 64 j
+  static constexpr uint32_t kBp = TN * 128u;  // one piece of the coefficient tile: 64 j x TN (z, part)
   static constexpr uint32_t kStage = NP * (kA + kBp);
   static constexpr int S0 = (int)((220u * 1024u) / kStage);
   static constexpr int S = S0 > 6 ? 6 : S0;
@@ -771,9 +771,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         int md, g, fb, bl[2];
         decode(tl, md, g, fb);
         const GInst& I = gp.inst[tl.x];
-        // K stages of 32 j; the coefficient pieces are stored in 64-j blocks (two 32-row halves of each
-        // 64-z N chunk), the Q pieces in 32-j blocks
-        const int ks = (I.n + 31) >> 5, kb64 = (I.n + 63) >> 6, nzb = I.Nz >> 6, nrb = (I.n + 127) >> 7;
+        const int ks = (I.n + 63) >> 6, nzb = I.Nz >> 6, nrb = (I.n + 127) >> 7;
         const int T = back_blocks(g, fb, bl) * ks;
         for (int t = 0; t < T; ++t, ++q) {
           const int s = q % S;
@@ -789,17 +787,12 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
           const int cb = bl[t / ks], kk = t % ks;
           mbar_expect_tx(&sb->fullB[s], (uint32_t)NP * (C::kA + C::kBp));
           for (int p = 0; p < NP; ++p) {
-            // Q block (md, g, piece, fb, cb, ks, rb): 128 r x 32 j, 8 KB
+            // Q block (md, g, piece, fb, cb, ks, rb): 128 r x 64 j, 16 KB
             const size_t qa = (((((size_t)(md * 2 + g) * NP + p) * 3 + fb) * 3 + cb) * ks + kk) * nrb + (tl.w >> 7);
-            bulk_g2s(stage_A(s) + p * C::kA, I.Q + qa * 8192, C::kA, &sb->fullB[s]);
-            // coefficient block (md, piece, c, j / 64, zb): [2 N chunks of 32 z][64 j][128 B]; this stage's 32
-            // j rows of each of the tile's TN / 64 N chunks, 4 KB apiece, packed 4 KB apart in the stage
-            const size_t sa = ((((size_t)md * NP + p) * 6 + g * 3 + cb) * kb64 + (kk >> 1)) * nzb + (tl.z >> 6);
-            const unsigned char* src = I.S + sa * 16384 + (size_t)(kk & 1) * 4096;
-#pragma unroll
-            for (int h = 0; h < TN / 64; ++h)
-              bulk_g2s(stage_B(s) + p * C::kBp + h * 4096, src + (size_t)(h >> 1) * 16384 + (h & 1) * 8192, 4096,
-                       &sb->fullB[s]);
+            bulk_g2s(stage_A(s) + p * C::kA, I.Q + qa * 16384, C::kA, &sb->fullB[s]);
+            // coefficient block (md, piece, c, ks, zb): 64 j x 64 z x re/im, 16 KB; TN/128 consecutive zb
+            const size_t sa = ((((size_t)md * NP + p) * 6 + g * 3 + cb) * ks + kk) * nzb + (tl.z >> 6);
+            bulk_g2s(stage_B(s) + p * C::kBp, I.S + sa * 16384, C::kBp, &sb->fullB[s]);
           }
         }
       }
@@ -825,7 +818,7 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
         int md, g, fb, bl[2];
         decode(tl, md, g, fb);
         const GInst& I = gp.inst[tl.x];
-        const int ks = (I.n + 31) >> 5;
+        const int ks = (I.n + 63) >> 6;
         const int T = back_blocks(g, fb, bl) * ks;
         const int b = NBUF == 2 ? (it & 1) : 0;
         const uint32_t use = (uint32_t)(NBUF == 2 ? (it >> 1) : it);
@@ -853,17 +846,16 @@ __global__ void __launch_bounds__(192, 1) tcg_backproject_kernel(const __grid_co
           unsigned char* As = stage_A(s);
           unsigned char* Bs = stage_B(s);
 #pragma unroll
-          for (int k16 = 0; k16 < 2; ++k16) {
+          for (int k16 = 0; k16 < 4; ++k16) {
 #pragma unroll
             for (int pr = 0; pr < (NP == 2 ? 3 : 6); ++pr) {
               int ia, ibp;
               product<NP>(pr, ia, ibp);
               const int acc = (NACC == 2 && pr > 0) ? 1 : 0;
               const bool first = t == 0 && k16 == 0 && (pr == 0 || (NACC == 2 && pr == 1));
-              // K-major A with 64-byte rows (32 j), as the projection's operands
-              const uint64_t ad = desc_sw64(As + ia * C::kA + k16 * 32);
-              // MN-major B: 64-element (128 B) rows along N, 16 K rows per MMA; N chunks 4 KB apart
-              const uint64_t bd = smem_desc(Bs + ibp * C::kBp + k16 * 16 * 128, 4096, 1024, 2);
+              const uint64_t ad = smem_desc(As + ia * C::kA + k16 * 32, 16, 1024, 2);
+              // MN-major B: 64-element (128 B) rows along N, 16 K rows per MMA; N chunks 8 KB apart
+              const uint64_t bd = smem_desc(Bs + ibp * C::kBp + k16 * 16 * 128, 8192, 1024, 2);
               mma_bf16(d0 + (uint32_t)(acc * TN), ad, bd, idesc, first ? 0u : 1u);
             }
           }
@@ -905,8 +897,7 @@ struct TcPlan {
   int Nz = 0, n = 0, nmodes = 0, np = 0;
   int njb = 0;  // projection: 128-row j blocks (n padded to 256)
   int nks = 0;  // projection: 32-wide r stages
-  int ksb = 0;  // coefficient pieces (spectral output): 64-row j blocks
-  int ksq = 0;  // back-projection: 32-wide j stages
+  int ksb = 0;  // back-projection: 64-wide j stages
   int nrb = 0;  // back-projection: 128-row r blocks
   uint8_t* d_P = nullptr;
   uint8_t* d_Q = nullptr;
@@ -960,9 +951,9 @@ static std::vector<uint8_t> tile_P(const double* P, int nmodes, int n, int np, i
 
 // Q [nmodes][2][3n][3n] (rows: field block fb, r; columns: coefficient block cb, j) -> pieces in
 // 16 KB blocks (md, g, piece, fb, cb, ks, rb) of 128 r rows x 64 j, 128B-swizzled rows.
-static std::vector<uint8_t> tile_Q(const double* Q, int nmodes, int n, int np, int ksq, int nrb) {
+static std::vector<uint8_t> tile_Q(const double* Q, int nmodes, int n, int np, int ksb, int nrb) {
   const int N3 = 3 * n;
-  std::vector<uint8_t> out((size_t)nmodes * 2 * np * 9 * ksq * nrb * 8192, 0);
+  std::vector<uint8_t> out((size_t)nmodes * 2 * np * 9 * ksb * nrb * 16384, 0);
   uint16_t pcs[3];
   for (int md = 0; md < nmodes; ++md)
     for (int g = 0; g < 2; ++g) {
@@ -974,12 +965,11 @@ static std::vector<uint8_t> tile_Q(const double* Q, int nmodes, int n, int np, i
               const double v = src[(size_t)(fb * n + r) * N3 + cb * n + j];
               if (v == 0.0) continue;
               split_bf16(v, np, pcs);
-              // 128 r x 32 j blocks, K-major 64-byte rows with the 64-byte swizzle (as tile_P)
-              const int ks = j >> 5, jc = j & 31, rb = r >> 7, rr = r & 127;
-              const size_t off = (size_t)rr * 64 + (((jc >> 3) ^ ((rr >> 1) & 3)) << 4) + (jc & 7) * 2;
+              const int ks = j >> 6, jc = j & 63, rb = r >> 7, rr = r & 127;
+              const size_t off = (size_t)rr * 128 + (((jc >> 3) ^ (rr & 7)) << 4) + (jc & 7) * 2;
               for (int p = 0; p < np; ++p) {
-                const size_t blk = (((((size_t)(md * 2 + g) * np + p) * 3 + fb) * 3 + cb) * ksq + ks) * nrb + rb;
-                memcpy(&out[blk * 8192 + off], &pcs[p], 2);
+                const size_t blk = (((((size_t)(md * 2 + g) * np + p) * 3 + fb) * 3 + cb) * ksb + ks) * nrb + rb;
+                memcpy(&out[blk * 16384 + off], &pcs[p], 2);
               }
             }
     }
@@ -1075,7 +1065,7 @@ static cudaError_t build_tiles(TcGroup* G) {
     for (int md = 0; md < t->nmodes; ++md)
       for (int g = 0; g < 2; ++g)
         for (int fb = 0; fb < 3; ++fb) {
-          const int cost = (fb == 2 ? 1 : 2) * t->ksq;
+          const int cost = (fb == 2 ? 1 : 2) * t->ksb;
           for (int r0 = 0; r0 < t->n; r0 += 128)
             for (int z0 = 0; z0 < t->Nz; z0 += c.tn_b / 2)
               bt.push_back({cost, make_int4((int)k, md | g << 8 | fb << 12, z0, r0)});
@@ -1098,7 +1088,7 @@ bool tc_config_valid(const TcPlan* const* plans, int count, const TcConfig& c) {
   if (c.tn_b != 128 && c.tn_b != 256) return false;
   if (c.sched_p < 0 || c.sched_p > 1 || c.sched_b < 0 || c.sched_b > 1) return false;
   for (int k = 0; k < count; ++k) {
-    if (plans[k]->np == 3 && c.tn_b != 128) return false;  // two accumulators x two buffers x 256 > 512 columns
+    if (plans[k]->np == 3 && c.tn_b != 128) return false;  // 3 pieces of a 256-wide tile leave one stage
     if (plans[k]->Nz % (c.tn_b / 2)) return false;         // a back-projection tile spans tn_b / 2 z values
   }
   return true;
@@ -1209,11 +1199,10 @@ cudaError_t tc_create(TcPlan** outp, int Nz, int n, int nmodes, int np, const do
   t->njb = (n + 255) / 256 * 2;
   t->nks = (n + 31) / 32;
   t->ksb = (n + 63) / 64;
-  t->ksq = (n + 31) / 32;
   t->nrb = (n + 127) / 128;
   t->cfg = tc_default_config(np);
   std::vector<uint8_t> hp = tile_P(P, nmodes, n, np, t->nks, t->njb);
-  std::vector<uint8_t> hq = tile_Q(Q, nmodes, n, np, t->ksq, t->nrb);
+  std::vector<uint8_t> hq = tile_Q(Q, nmodes, n, np, t->ksb, t->nrb);
   const size_t split_bytes = (size_t)nmodes * np * 6 * t->ksb * (Nz / 64) * 16384;
   e = cudaMalloc(&t->d_P, hp.size());
   if (e == cudaSuccess) e = cudaMalloc(&t->d_Q, hq.size());

@@ -111,7 +111,7 @@ extern "C" size_t fdetd_request_device_bytes(const fdetd_request* r) {
   if (r->precision == FDETD_PREC_BF16X3 || r->precision == FDETD_PREC_BF16X6) {
     const size_t np = r->precision == FDETD_PREC_BF16X3 ? 2 : 3;
     const size_t nks = (n + 31) / 32, njb = (n + 255) / 256 * 2, ksb = (n + 63) / 64, nrb = (n + 127) / 128;
-    b += nm * 2 * np * 9 * nks * njb * 8192 + nm * 2 * np * 9 * nks * nrb * 8192;    // pre-tiled P, Q pieces
+    b += nm * 2 * np * 9 * nks * njb * 8192 + nm * 2 * np * 9 * ksb * nrb * 16384;   // pre-tiled P, Q pieces
     b += nm * np * 6 * ksb * (pad_up(Nz, 64) / 64) * 16384;                           // split coefficients
     b += 2 * 1024 * 1024;                                                               // tile tables
   } else {
