@@ -110,8 +110,6 @@ def replica_rate(units_per_rank, seconds, world):
     return units_per_rank * world / seconds
 
 
-HOST_PARTS = 4   # parts of the host-buffer batch step (the library's default)
-
 STAGE_SOURCE = {"projection": "k_tc.cu", "spectral": "k_spectral32.cu", "backprojection": "k_tc.cu"}
 
 
@@ -360,7 +358,7 @@ def run_batch(args, rank, world, dist):
 
     batch.set_host_pipeline(1)
     e2e_serial = replica_rate(cells * args.e2e_steps, time_host_steps(), world)
-    batch.set_host_pipeline(HOST_PARTS)
+    batch.set_host_pipeline(args.host_parts)
     e2e_s = time_host_steps()
     h2d = sum(t.numel() * t.element_size() for t in hf) + sum(t.numel() * t.element_size() for t in hj)
     d2h = sum(t.numel() * t.element_size() for t in hf)
@@ -426,7 +424,7 @@ def run_batch(args, rank, world, dist):
                 "latency": {"unit": "ms per step (one graph replay)", "p50": float(np.percentile(lat, 50)),
                             "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "pipeline_parts": HOST_PARTS, "serial_value": e2e_serial,
+                        "pipeline_parts": args.host_parts, "serial_value": e2e_serial,
                         "api": "fdetd_batch_step_host"},
                 "gpu_launches": launches_per_step * args.steps, "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clk}
@@ -850,6 +848,7 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--drain", type=float, default=30.0)
     ap.add_argument("--prewarm", action="store_true", help="serve mode: radial tables of the pool computed first")
+    ap.add_argument("--host-parts", type=int, default=4, help="batch mode: parts of the host-buffer step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -250,7 +250,9 @@ __device__ __forceinline__ void add_waits(unsigned long long* w, int slot, long 
 // The projection's converter warps (0 .. kConvWarps-1) split the staged FP32 field tile (64 z x 32 complex =
 // 256 items of 8 radii) into bf16 pieces; with eight of them each thread converts one item per stage.
 constexpr int kConvWarps = 8, kConvThreads = 32 * kConvWarps, kConvItems = 256 / kConvThreads;
-constexpr int kProjThreads = 32 * (kConvWarps + 6);   // + 4 epilogue, 1 copy, 1 MMA warp
+// epilogue warps: two per TMEM lane quarter, each draining every other 32-column chunk
+constexpr int kEpiWarps = 8;
+constexpr int kProjThreads = 32 * (kConvWarps + kEpiWarps + 2);   // + 1 copy, 1 MMA warp
 
 // barrier + AND-reduction over the converter threads (named barrier 1)
 __device__ __forceinline__ bool bar_and_conv(bool v) {
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sb->tfull[b], 1);
-      mbar_init(&sb->tempty[b], 4);
+      mbar_init(&sb->tempty[b], kEpiWarps);
     }
     mbar_init(&sb->done, 1);
     sb->abort = 0;
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       add_waits(gp.waits, kWaitStaged, w_staged);
       add_waits(gp.waits, kBusyConv, busy);
     }
-  } else if (warp < kConvWarps + 4) {
+  } else if (warp < kConvWarps + kEpiWarps) {
     // ---- epilogue: TMEM -> coef[md][g*3+ob][j][2 Nz] (complex, re/im from adjacent rows); TMEM lane quarter
     // = warp mod 4
     const int quarter = warp & 3;
@@ -496,13 +498,14 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       // 32-column chunks that hold outputs j < n; NACC = 1 reads its single accumulator twice (the
       // second copy unused) so that both forms share one load instruction pair
       const int nch = (tile_n(TN, n, j0) + 31) >> 5;
+      const int half = (warp - kConvWarps) >> 2;  // which of the two warps of this lane quarter
       const uint32_t corr = NACC == 2 ? (uint32_t)TN : 0u;
       // lanes 4g .. 4g+3 hold four consecutive rows (contiguous in memory along z, re/im); a 4 x 4 transpose
       // over each such group leaves lane 4g + q with column q of the block, so that it stores the four rows
       // as one 16-byte vector: 8 vector stores per 32 columns instead of 32 scalar ones
       const int q = lane & 3;
       float* const out4 = I.coef + (size_t)(md * 9 + g * 3 + ob) * n * 2 * Nz + 2 * z0 + quarter * 32 + (lane & ~3);
-      for (int ch = 0; ch < nch; ++ch) {
+      for (int ch = half; ch < nch; ch += 2) {
         const int c0 = 32 * ch;
         uint32_t lead[32], cr[32];
         tmem_ld2x32(tbase + c0, tbase + corr + c0, lead, cr);  // both accumulators, one wait
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
       busy += clock64() - c1;
     }
     if (warp == kConvWarps && lane == 0) add_waits(gp.waits, kBusyEpi, busy);
-  } else if (warp == kConvWarps + 4) {
+  } else if (warp == kConvWarps + kEpiWarps) {
     // ---- producer: the FP32 field tile (TMA) and the pre-tiled P pieces (bulk copies)
     int q = 0;
     bool live = true;
