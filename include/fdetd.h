@@ -76,12 +76,17 @@ typedef struct fdetd_taylor_s* fdetd_taylor_t;
  * axis extensions of Eqs. spatialAM_derivativeS/A, the B_z axis value of
  * Sec. 2.4, taps beyond the outer radius dropped (Sec. 2.2), periodic z.
  * Nz = 64 k in 64..8192 with no prime factor above 7 (FDETD_ERR_UNSUPPORTED otherwise; FP64 takes
- * powers of two up to 4096 and other lengths while the five columns of a family fit in shared
- * memory, about 2500), Nr >= order/2 + 2, M >= 0.
+ * every power of two and other lengths while the five columns of a family fit in shared memory, about
+ * 2500), Nr >= order/2 + 2, M >= 0.  Powers of two whose three field columns do not fit in shared
+ * memory (FP64 at 8192) run the z transform in its column-split form: three launches (every column
+ * forward in place, the update of every (kz, j) point, every field column back), bitwise the results
+ * of the single-pass form; flags & FDETD_FLAG_SPECTRAL_COLUMNS selects that form at any power of two
+ * (FDETD_ERR_UNSUPPORTED for other lengths).
  * The radial eigen-decompositions, the omega table and the phase factors are
  * computed in FP64 on the host; device tables are allocated here and owned by
  * the plan.  Blocking; not stream-ordered.
  */
+#define FDETD_FLAG_SPECTRAL_COLUMNS 1ull
 int fdetd_plan(fdetd_plan_t* out, int Nz, int Nr, int M, int order, double dz, double dr, double dt,
                int precision, uint64_t flags);
 

@@ -226,6 +226,9 @@ class FdetdPlan:
             pass
 
 
+SPECTRAL_COLUMNS = 1   # plan flag: the z transform in its column-split form (FDETD_FLAG_SPECTRAL_COLUMNS)
+
+
 def fdetd_plan_modes(Nz, Nr, modes, order, dz, dr, dt, precision="fp64", flags=0):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * len(modes))(*modes)

@@ -33,6 +33,7 @@ static df to_df(double x) {
 
 struct fdetd_plan_s {
   int Nz = 0, Nr = 0, nmodes = 0, order = 0, precision = 0, logNz = 0, tw_count = 0;
+  bool columns = false;       // z transform in its column-split form (three launches)
   double dz = 0, dr = 0, dt = 0;
   std::vector<int> modes;
   void* d_P = nullptr;
@@ -106,7 +107,6 @@ static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* modes, int nmodes, int order,
                                 double dz, double dr, double dt, int precision, uint64_t flags) {
-  (void)flags;
   if (!out) return fail(FDETD_ERR_ARG, "out is null");
   *out = nullptr;
   if (!modes || nmodes < 1 || nmodes > 64) return fail(FDETD_ERR_ARG, "need 1..64 modes");
@@ -115,11 +115,17 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   if (Nz < 64 || Nz > 8192 || Nz % 64 || !spectral_radices(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, radices))
     return fail(FDETD_ERR_UNSUPPORTED, "the z transform needs Nz = 64 k in 64..8192 with no prime factor above 7");
   const bool hasJ_max = true;
-  if (is_pow2(Nz) ? spectral_smem_bytes(Nz, precision, hasJ_max) > 227 * 1024
-                  : spectral_mixed_smem_bytes(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, hasJ_max,
-                                              spectral_twiddles(Nz, precision == FDETD_PREC_FP64 ? 0 : 1, nullptr,
-                                                                nullptr)) > 227 * 1024)
-    return fail(FDETD_ERR_UNSUPPORTED, "Nz too long for the single-pass z transform at this precision");
+  const int prec01 = precision == FDETD_PREC_FP64 ? 0 : 1;
+  const bool fits = is_pow2(Nz) ? spectral_smem_bytes(Nz, precision, hasJ_max) <= 227 * 1024
+                                : spectral_mixed_smem_bytes(Nz, prec01, hasJ_max,
+                                                            spectral_twiddles(Nz, prec01, nullptr, nullptr)) <=
+                                      227 * 1024;
+  const bool force_cols = (flags & FDETD_FLAG_SPECTRAL_COLUMNS) != 0;
+  if (force_cols && !is_pow2(Nz))
+    return fail(FDETD_ERR_UNSUPPORTED, "the column-split z transform takes power-of-two lengths");
+  const bool columns = is_pow2(Nz) && (force_cols || !fits) && spectral_columns_supported(Nz, prec01);
+  if (!fits && !columns)
+    return fail(FDETD_ERR_UNSUPPORTED, "Nz too long for the z transform at this precision");
   HostPlan hp;
   std::string msg;
   int rc = build_host_plan(hp, Nz, Nr, modes, nmodes, order, dz, dr, dt, msg);
@@ -128,6 +134,7 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   fdetd_plan_s* p = new fdetd_plan_s();
   p->Nz = Nz;
   p->Nr = Nr;
+  p->columns = columns;
   p->nmodes = nmodes;
   p->order = order;
   p->precision = precision;
@@ -263,8 +270,8 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
     if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
     p->bytes += cbytes;
-    if (is_pow2(Nz) ? spectral_needs_source(Nz, prec_k, p->tw_count)
-                    : spectral_mixed_needs_source(Nz, prec_k, p->tw_count)) {
+    if (!p->columns && (is_pow2(Nz) ? spectral_needs_source(Nz, prec_k, p->tw_count)
+                                     : spectral_mixed_needs_source(Nz, prec_k, p->tw_count))) {
       const size_t sbytes = (size_t)nmodes * 2 * 3 * n * Nz * (fp64 ? 16 : 8);
       if ((e = cudaMalloc(&p->d_src, sbytes)) != cudaSuccess) goto cuda_fail;
       p->bytes += sbytes;
@@ -332,7 +339,9 @@ static int stage_spectral(fdetd_plan_s* p, bool hasJ, cudaStream_t st) {
   // FP32 data, Nz a power of two up to 4096: the kernel specialised on Nz; other powers of two: the general
   // power-of-two kernel; other 7-smooth lengths: the mixed-radix kernel
   cudaError_t e;
-  if (!is_pow2(p->Nz)) {
+  if (p->columns) {
+    e = launch_spectral_columns(sa, p->nmodes, prec, p->tc != nullptr, st);
+  } else if (!is_pow2(p->Nz)) {
     MixedRadices mr;
     mr.nst = spectral_radices(p->Nz, prec, mr.rad);
     e = launch_spectral_mixed(sa, mr, p->nmodes, prec, p->tc != nullptr, st);
@@ -634,7 +643,8 @@ extern "C" size_t fdetd_plan_device_bytes(fdetd_plan_t p) { return p ? p->bytes 
 
 extern "C" int fdetd_plan_launches_per_step(fdetd_plan_t p) {
   if (!p) return 0;
-  return (p->tc ? tc_launches_per_step(p->tc) : 2) + (p->d_src ? 2 : 1);  // + source kernel when split
+  // + the source kernel of the two-kernel form, or the three launches of the column-split form
+  return (p->tc ? tc_launches_per_step(p->tc) : 2) + (p->columns ? 3 : (p->d_src ? 2 : 1));
 }
 
 extern "C" int fdetd_plan_status(fdetd_plan_t p, void* stream) {

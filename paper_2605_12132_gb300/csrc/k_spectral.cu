@@ -216,13 +216,13 @@ __device__ __forceinline__ void stage_inplace(C* s, int Pc, int narr, int logN, 
 // The adjoint of stage 0 (one block, stride N / R) for the three field columns, writing the natural
 // order result z = n1 + L n2 to global memory (or its bf16 split pieces).  The column index is a
 // compile-time loop index, so the column descriptors stay in registers.
-template <int R, int NT, bool SPLIT_OUT, typename C>
+template <int R, int NT, bool SPLIT_OUT, typename C, int NCOL = 3>
 __device__ __forceinline__ void stage0_inv_to_global(const C* s, int Pc, int logN, const C* tw, C* const* dst,
                                                      const SplitColumn* sc) {
   constexpr int LR = Log2R<R>::v;
   const int logL = logN - LR, L = 1 << logL;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
+  for (int a = 0; a < NCOL; ++a) {
     // the bf16 split stores are kept rolled: unrolled, they push the kernel out of the instruction cache
 #pragma unroll 1
     for (int n1 = threadIdx.x; n1 < L; n1 += NT) {
@@ -536,6 +536,189 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) spectral_kernel(Spect
     stage0_inv_to_global<4, NT, SPLIT_OUT>(s, Pc, L, tw, dst, sc);
 }
 
+// ---------------------------------------------------------------- column-split form
+// For z lengths whose three field columns do not fit in shared memory (FP64 at Nz = 8192): the same
+// transform and update in three kernels over one column at a time.  (1) every coefficient column (fields
+// and current) is transformed forward in place, the last stage included, and left in global memory in
+// position order; (2) the update of every (kz, j) point reads the family's columns at that position;
+// (3) every field column is transformed back (the adjoints in reverse order) to natural order, or to the
+// back-projection's split pieces.  Same butterflies, tables and update arithmetic as the fused kernel, so
+// the results are bitwise those of the fused form.
+
+// stage schedule of a length-2^L transform with radix R: first-stage radix 2^LRF, S stages, last radix 2^LRL
+struct StageSchedule {
+  int S, LRF, LRL;
+  __device__ StageSchedule(int L, int LR) {
+    const int nfull = L / LR, rem = L % LR;
+    S = rem && nfull ? nfull + 1 : (nfull ? nfull : 1);
+    LRF = S == 1 ? L : (rem ? rem : LR);
+    LRL = S == 1 ? L : LR;
+  }
+};
+
+// the last stage (stride 1, no twiddles) of one column, forward or adjoint: runs of RL consecutive positions
+template <int RL, bool INV, int NT, typename C>
+__device__ __forceinline__ void stage_last_column(C* s, int N) {
+  for (int b = threadIdx.x; b < N / RL; b += NT) {
+    C v[RL];
+    load_run<RL>(s + pad16(b * RL), v);
+    dft_small<RL, INV>(v);
+    store_run<RL>(s + pad16(b * RL), v);
+  }
+  __syncthreads();
+}
+template <int R, bool INV, int NT, typename C>
+__device__ __forceinline__ void stage_last_any(C* s, int N, int LRL) {
+  if (LRL == 1)
+    stage_last_column<2, INV, NT>(s, N);
+  else if (LRL == 2)
+    stage_last_column<4, INV, NT>(s, N);
+  else if (LRL == 3)
+    stage_last_column<8, INV, NT>(s, N);
+  else
+    stage_last_column<R, INV, NT>(s, N);
+}
+
+template <typename C, int NT>
+__device__ __forceinline__ void load_column(C* s, const C* col, int L) {
+  constexpr int EPC = 16 / (int)sizeof(C);
+  const int per = 1 << (L - (EPC == 2 ? 1 : 0));
+  for (int i = threadIdx.x; i < per; i += NT) cp_async16(s + pad16(i * EPC), col + i * EPC);
+  cp_async_wait_all();
+  __syncthreads();
+}
+
+// (1) forward transform of coefficient column blockIdx.y (0 .. 8) of (mode blockIdx.z, j blockIdx.x), in place
+template <typename T, int R, int NT>
+__global__ void __launch_bounds__(NT, 1) spectral_fwd_column(SpectralArgs args) {
+  typedef typename cplx<T>::type C;
+  constexpr int LR = Log2R<R>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int Nz = args.Nz, L = args.logNz, n = args.n;
+  C* col = reinterpret_cast<C*>(args.coef) + ((size_t)(blockIdx.z * 9 + blockIdx.y) * n + blockIdx.x) * Nz;
+  const C* t = reinterpret_cast<const C*>(args.twiddle);
+  load_column<C, NT>(s, col, L);
+  const StageSchedule sc(L, LR);
+  const int Pc = pad16(Nz);
+  for (int st = 0; st < sc.S - 1; ++st) {
+    const int logLs = L - sc.LRF - LR * st;
+    if (st > 0 || sc.LRF == LR) {
+      stage_inplace<R, false, NT>(s, Pc, 1, L, logLs, t);
+      t += (size_t)(R - 1) << logLs;
+    } else if (sc.LRF == 1) {
+      stage_inplace<2, false, NT>(s, Pc, 1, L, logLs, t);
+      t += (size_t)1 << logLs;
+    } else {
+      stage_inplace<4, false, NT>(s, Pc, 1, L, logLs, t);
+      t += (size_t)3 << logLs;
+    }
+  }
+  stage_last_any<R, false, NT>(s, Nz, sc.LRL);
+  for (int z = threadIdx.x; z < Nz; z += NT) col[z] = s[pad16(z)];
+}
+
+// (2) the exact midpoint update of every (kz, j) point of (mode, family) = (blockIdx.z / 2, blockIdx.z % 2),
+// j = blockIdx.y, positions blockIdx.x * blockDim.x + threadIdx.x, scaled by 1 / Nz
+template <typename T, typename K, typename PH, typename ZS>
+__global__ void spectral_update_columns(SpectralArgs args, int RL) {
+  typedef typename cplx<T>::type C;
+  const int Nz = args.Nz, n = args.n, j = blockIdx.y, md = blockIdx.z >> 1, fam = blockIdx.z & 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Nz) return;
+  const int nb = Nz / RL, q = (p % RL) * nb + p / RL;  // table index of position p
+  C* coef = reinterpret_cast<C*>(args.coef);
+  auto at = [&](int c) { return coef + ((size_t)(md * 9 + c) * n + j) * Nz + p; };
+  // TM: e, a, b (columns 0, 1, 3), current eJ, aJ (6, 7); TE: c, d, f (2, 4, 5), current cJ (8)
+  C* x0 = at(fam == 0 ? 0 : 2);
+  C* x1 = at(fam == 0 ? 1 : 4);
+  C* x2 = at(fam == 0 ? 3 : 5);
+  const bool hasJ = args.hasJ;
+  const C zero = cmake<C>(0, 0);
+  const C j0 = hasJ ? *at(fam == 0 ? 6 : 8) : zero;
+  const C j1 = hasJ && fam == 0 ? *at(7) : zero;
+  K spr, spi, smr, smi, A1, A2;
+  T B1, B2;
+  zsym_unpack(reinterpret_cast<const ZS*>(args.zsym)[q], spr, spi, smr, smi);
+  phase_unpack(reinterpret_cast<const PH*>(args.phase)[((size_t)(md * 2 + fam) * n + j) * Nz + q], A1, A2, B1, B2);
+  const K lam = reinterpret_cast<const K*>(args.lam)[(md * 2 + fam) * n + j];
+  C v0 = *x0, v1 = *x1, v2 = *x2;
+  rotate_point<T, K, C>(v0, v1, v2, j0, j1, hasJ, fam, lam, spr, spi, smr, smi, A1, A2, B1, B2, (T)args.dt,
+                        (T)1 / (T)Nz);
+  *x0 = v0;
+  *x1 = v1;
+  *x2 = v2;
+}
+
+// (3) inverse transform of field coefficient column blockIdx.y (0 .. 5) of (mode blockIdx.z, j blockIdx.x)
+template <typename T, int R, int NT, bool SPLIT_OUT>
+__global__ void __launch_bounds__(NT, 1) spectral_inv_column(SpectralArgs args) {
+  typedef typename cplx<T>::type C;
+  constexpr int LR = Log2R<R>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int Nz = args.Nz, L = args.logNz, n = args.n, c = blockIdx.y, md = blockIdx.z, j = blockIdx.x;
+  C* col = reinterpret_cast<C*>(args.coef) + ((size_t)(md * 9 + c) * n + j) * Nz;
+  const C* tw = reinterpret_cast<const C*>(args.twiddle);
+  load_column<C, NT>(s, col, L);
+  const StageSchedule sc(L, LR);
+  const int Pc = pad16(Nz);
+  stage_last_any<R, true, NT>(s, Nz, sc.LRL);
+  // twiddles of stages 1 .. S-2 follow stage 0's
+  const C* t = tw + ((size_t)((1 << sc.LRF) - 1) << (L - sc.LRF));
+  for (int st = 1; st < sc.S - 1; ++st) t += (size_t)(R - 1) << (L - sc.LRF - LR * st);
+  for (int st = sc.S - 2; st >= 1; --st) {
+    const int logLs = L - sc.LRF - LR * st;
+    t -= (size_t)(R - 1) << logLs;
+    stage_inplace<R, true, NT>(s, Pc, 1, L, logLs, t);
+  }
+  SplitColumn spl[3];
+  C* dst[3] = {col, col, col};
+  if (SPLIT_OUT) spl[0] = split_column(args.split_out, args.npieces, md, c, j, args.split_kstages, Nz);
+  if (sc.S == 1) {
+    for (int z = threadIdx.x; z < Nz; z += NT) {
+      const C v = s[pad16(z)];
+      if (!SPLIT_OUT)
+        col[z] = v;
+      else
+        split_store(spl[0], z, (float)v.x, (float)v.y);
+    }
+  } else if (sc.LRF == LR) {
+    stage0_inv_to_global<R, NT, SPLIT_OUT, C, 1>(s, Pc, L, tw, dst, spl);
+  } else if (sc.LRF == 1) {
+    stage0_inv_to_global<2, NT, SPLIT_OUT, C, 1>(s, Pc, L, tw, dst, spl);
+  } else {
+    stage0_inv_to_global<4, NT, SPLIT_OUT, C, 1>(s, Pc, L, tw, dst, spl);
+  }
+}
+
+template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT>
+static cudaError_t launch_columns_nt(const SpectralArgs& a, int nmodes, cudaStream_t st) {
+  typedef typename cplx<T>::type C;
+  const size_t smem = (size_t)pad16(a.Nz) * sizeof(C);
+  auto kf = spectral_fwd_column<T, R, NT>;
+  auto ki = spectral_inv_column<T, R, NT, SPLIT>;
+  cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kf<<<dim3(a.n, a.hasJ ? 9 : 6, nmodes), NT, smem, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int LR = Log2R<R>::v, L = a.logNz;
+  const int RL = L <= LR ? a.Nz : R;  // radix of the last stage (the table order)
+  spectral_update_columns<T, K, PH, ZS><<<dim3((a.Nz + 255) / 256, a.n, 2 * nmodes), 256, 0, st>>>(a, RL);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ki<<<dim3(a.n, 6, nmodes), NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, typename K, typename PH, typename ZS, int R, bool SPLIT>
+static cudaError_t launch_columns(const SpectralArgs& a, int nmodes, cudaStream_t st) {
+  const int need = a.Nz / R;
+  if (need <= 128) return launch_columns_nt<T, K, PH, ZS, R, 128, SPLIT>(a, nmodes, st);
+  if (need <= 256) return launch_columns_nt<T, K, PH, ZS, R, 256, SPLIT>(a, nmodes, st);
+  return launch_columns_nt<T, K, PH, ZS, R, 512, SPLIT>(a, nmodes, st);
+}
+
 template <typename T, typename K, typename PH, typename ZS, int R, int NT, bool SPLIT, int MODE, bool TW_SMEM>
 static cudaError_t launch_one(const SpectralArgs& a, int nmodes, cudaStream_t st) {
   typedef typename cplx<T>::type C;
@@ -584,6 +767,18 @@ cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bo
   if (precision == 0) return launch_prec<double, double, PhaseD, ZSymD, 4, false>(a, nmodes, st);
   if (split_out) return launch_prec<float, df, PhaseF, ZSymF, 8, true>(a, nmodes, st);
   return launch_prec<float, df, PhaseF, ZSymF, 8, false>(a, nmodes, st);
+}
+
+cudaError_t launch_spectral_columns(const SpectralArgs& a, int nmodes, int precision, bool split_out,
+                                    cudaStream_t st) {
+  if (!spectral_columns_supported(a.Nz, precision)) return cudaErrorNotSupported;
+  if (precision == 0) return launch_columns<double, double, PhaseD, ZSymD, 4, false>(a, nmodes, st);
+  if (split_out) return launch_columns<float, df, PhaseF, ZSymF, 8, true>(a, nmodes, st);
+  return launch_columns<float, df, PhaseF, ZSymF, 8, false>(a, nmodes, st);
+}
+
+bool spectral_columns_supported(int Nz, int precision) {
+  return Nz >= 2 && (Nz & (Nz - 1)) == 0 && (size_t)pad16(Nz) * (precision == 0 ? 16 : 8) <= 227 * 1024;
 }
 
 bool spectral_needs_source(int Nz, int precision, int tw_count) {

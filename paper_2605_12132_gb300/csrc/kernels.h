@@ -33,6 +33,11 @@ struct SpectralArgs {
 };
 
 cudaError_t launch_spectral(const SpectralArgs& a, int nmodes, int precision, bool split_out, cudaStream_t st);
+// column-split form (three kernels, one column in shared memory at a time): power-of-two Nz whose single
+// padded column fits in shared memory; bitwise the results of the fused form
+cudaError_t launch_spectral_columns(const SpectralArgs& a, int nmodes, int precision, bool split_out,
+                                    cudaStream_t st);
+bool spectral_columns_supported(int Nz, int precision);
 size_t spectral_smem_bytes(int Nz, int precision, bool hasJ);
 int spectral_twiddles(int Nz, int precision, double* re, double* im);
 // kz index held at each position of the forward transform's output (the order of the phase and z tables)
