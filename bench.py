@@ -342,7 +342,7 @@ def run_batch(args, rank, world, dist):
         torch.cuda.empty_cache()
 
     # end to end through the host-buffer form of the batch: every step copies every instance's fields and
-    # current in from pinned host memory and the fields back out (the library's default: four parts whose
+    # current in from pinned host memory and the fields back out (the library's default: eight parts whose
     # copies overlap each other's compute; the serial form is timed beside it)
     hf = [torch.from_numpy(F).to(torch.complex64).pin_memory() for F, _ in host]
     hj = [torch.from_numpy(J).to(torch.complex64).pin_memory() for _, J in host]
@@ -848,7 +848,7 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--drain", type=float, default=30.0)
     ap.add_argument("--prewarm", action="store_true", help="serve mode: radial tables of the pool computed first")
-    ap.add_argument("--host-parts", type=int, default=4, help="batch mode: parts of the host-buffer step")
+    ap.add_argument("--host-parts", type=int, default=8, help="batch mode: parts of the host-buffer step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
