@@ -736,9 +736,11 @@ def run_step(args, w, prec, leg=False, dist=None, rank=0, world=1):
     value = replica_rate(cells * steps, ms / 1e3, world)
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in ktimes.items()}
 
-    # FP64 single-instance path on the same workload (where its z transform reaches: Nz <= 4096)
-    fp64_value = err = None
-    if not args.no_fp64 and prec != "fp64" and w.Nz <= 4096:
+    # FP64 single-instance path on the same workload: its rate, the error of one step from the same state, and
+    # (where FP64 steps take milliseconds, Nz <= 4096) the error after 100 steps, which shows the drift of the
+    # per-step error
+    fp64_value = err = err100 = None
+    if not args.no_fp64 and prec != "fp64":
         p64 = fd.fdetd_plan_modes(w.Nz, w.Nr, w.modes, w.order, w.dz, w.dr, w.dt, precision="fp64")
         f64 = torch.from_numpy(F).cuda()
         J64 = torch.from_numpy(J).cuda() if J is not None else None
@@ -753,12 +755,24 @@ def run_step(args, w, prec, leg=False, dist=None, rank=0, world=1):
         b.record(stream)
         barrier()
         fp64_value = cells * n64 / (a.elapsed_time(b) / 1e3)
+        if w.Nz <= 4096:
+            n_long = 100
+            fl = torch.from_numpy(F).to(cdt).cuda()
+            fd.fdetd_step(plan, fl, Jd, n_long)
+            f64 = torch.from_numpy(F).cuda()
+            fd.fdetd_step(p64, f64, J64, n_long)
+            barrier()
+            plan.status()
+            strong, weak = _field_error_stats(torch, fl, f64)
+            err100 = {"steps": n_long, "strong_fields_max": strong, "weak_fields_max": weak}
+            del fl
         p64.close()
         del f64, J64
 
     summary = {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "modes": w.modes, "order": w.order, "precision": prec,
                "steps": steps, "ms_per_step": ms / steps, "value": value, "stage_ms_per_step": stage_ms,
-               "fp64_value": fp64_value, "rel_err_vs_fp64_1step": err, "tiles": tiles, "pipeline": pipeline,
+               "fp64_value": fp64_value, "rel_err_vs_fp64_1step": err, "rel_err_vs_fp64_100steps": err100,
+               "tiles": tiles, "pipeline": pipeline,
                "l2": "flushed between timed steps (256 MiB write)"}
     launches = plan.launches_per_step * steps
     plan.close()
