@@ -392,12 +392,28 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         for (int it = 0; it < kConvItems; ++it) {
           const int item = threadIdx.x + it * kConvThreads;  // 64 z x 4 chunks of 8 r
           const int zl = item >> 2, c = item & 3;
-          // box c >> 1, row zl (128 B); its 16-byte chunk (c & 1) * 4 + k sits at that index XOR (zl & 7) (the
-          // TMA's 128-byte swizzle): a warp's 32 reads of one k fall evenly on the eight bank groups
-          const float4* rowp = reinterpret_cast<const float4*>(stg + (c >> 1) * 2048 + zl * 32);
+          const float4* src = reinterpret_cast<const float4*>(stg + zl * 64 + c * 16);
+          // read the four 16-byte pieces in an order rotated by rr = (c + zl): a warp's 32 reads then fall
+          // on all eight 16-byte bank groups (4 wavefronts) instead of two; t[k] is re-rotated after
+          const int rr = (c + zl) & 3;
           float4 t[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) t[k] = rowp[((c & 1) * 4 + k) ^ (zl & 7)];
+          for (int k = 0; k < 4; ++k) t[k] = src[(k + rr) & 3];
+          if (rr & 1) {
+            const float4 x = t[3];
+            t[3] = t[2];
+            t[2] = t[1];
+            t[1] = t[0];
+            t[0] = x;
+          }
+          if (rr & 2) {
+            float4 x = t[0];
+            t[0] = t[2];
+            t[2] = x;
+            x = t[1];
+            t[1] = t[3];
+            t[3] = x;
+          }
           // radii beyond Nr are zero-filled by the TMA box; masked here as well, on the last K stage only
           const bool full = r0 + 32 <= n;
 #pragma unroll
@@ -544,14 +560,12 @@ __global__ void __launch_bounds__(kProjThreads, 1) tcg_project_kernel(const __gr
         }
         const int ib = bl[t / nks], rs = t % nks, r0 = rs * 32;
         if (lane == 0) {
-          // FP32 field tile: 64 z rows x 32 complex as two 64 x 16-complex boxes, 128-byte swizzled, 8 KB apart
-          // (radii beyond Nr are zero-filled, a box wholly beyond them included)
+          // FP32 field tile: 64 z rows x 32 complex, one TMA box (radii beyond Nr are zero-filled); a single
+          // 16 KB box arrives sooner than two 128-byte-swizzled halves, whose conflict-free reads did not pay
           mbar_expect_tx(&sb->fullS[s], 64u * 256u);
           const CUtensorMap* map = g == 2 ? &gp.jmap[tl.x] : &gp.fmap[tl.x];
           const int field = g == 2 ? ib : ((g == 1) ? (ib == 0 ? 4 : (ib == 1 ? 3 : 5)) : ib);
-          const int row = (md * (g == 2 ? 3 : 6) + field) * Nz + z0;
-          tma_load_2d(stage_A(s), map, &sb->fullS[s], 2 * r0, row);
-          tma_load_2d(stage_A(s) + 8192, map, &sb->fullS[s], 2 * r0 + 32, row);
+          tma_load_2d(stage_A(s), map, &sb->fullS[s], 2 * r0, (md * (g == 2 ? 3 : 6) + field) * Nz + z0);
           mbar_expect_tx(&sb->fullB[s], (uint32_t)NP * bbytes);
         }
         __syncwarp();
@@ -985,11 +999,10 @@ static bool encode_rows(CUtensorMap* m, const void* ptr, int n, long rows) {
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)2 * n * 4};
-  // 64 rows x 32 floats (128 B) per box, 128-byte swizzle: a stage's 64 x 64-float tile is two boxes
-  cuuint32_t box[2] = {32, 64};
+  cuuint32_t box[2] = {64, 64};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
