@@ -1,8 +1,10 @@
 """Error of the FP32-state precisions against the FP64 oracle after 1, 100 and 1000 steps on the 8192 x 512
 three-mode current-driven workload (the full-size precision sweep), on sampled kz columns inside and outside
 the pulse band.  The oracle's columns are precomputed by tests/golden/make_sweep_8192x512.py (a dense 3069^2
-exponential per column takes minutes) and read from tests/golden/sweep_8192x512_ref.npz.  FP64 is absent: its
-single-pass z transform stops at Nz = 4096.
+exponential per column takes minutes) and read from tests/golden/sweep_8192x512_ref.npz.  FP64 is absent here:
+it runs at Nz = 8192 through the column-split z transform, checked against the oracle in
+tests/test_gpu_spectral_columns.py on a narrower radial grid, but its 1000 steps at Nr = 512 would take about ten
+GPU-minutes per run.
 
 Per mode and field: relative L2 with a floor of 1e-12 of the state's norm, and the element-wise error.  Fields
 carrying at least 10% of the state are checked against the strong bound, the others (the radial and
