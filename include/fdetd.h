@@ -309,7 +309,7 @@ int fdetd_taylor_host_bands(int Nr, int order, double dr, int m, double* bands, 
  * buffers, advances every instance by nlaunch times the captured steps, copies the fields back into
  * host_fields, and synchronizes `stream` before returning.  FDETD_ERR_ARG for a missing graph or
  * buffer.  Copies and compute overlap: the instances are split into up to
- * fdetd_batch_set_host_pipeline(batch, parts) contiguous parts of about equal bytes (default 8; 1
+ * fdetd_batch_set_host_pipeline(batch, parts) contiguous parts of about equal bytes (default 16; 1
  * gives the serial form: all copies in, the main graph, all copies out), each with a one-step graph
  * of its own (built at the first call with the main capture's tile shapes; results bitwise equal to
  * the main graph's); part p's inputs are copied in on an internal stream, its graph runs on `stream`

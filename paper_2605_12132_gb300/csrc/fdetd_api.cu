@@ -837,7 +837,7 @@ struct fdetd_batch_s {
     cudaEvent_t in = nullptr, done = nullptr;
   };
   std::vector<Part> parts;
-  int host_parts = 8;
+  int host_parts = 16;
   cudaStream_t s_in = nullptr, s_out = nullptr;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   std::vector<cudaEvent_t> stage_ev;
