@@ -87,6 +87,13 @@ typedef struct fdetd_taylor_s* fdetd_taylor_t;
  * the plan.  Blocking; not stream-ordered.
  */
 #define FDETD_FLAG_SPECTRAL_COLUMNS 1ull
+/* flags & FDETD_FLAG_J_ON_PRIMARY: fdetd_step takes J_rho deposited on the primary radial grid
+ * (rho_k = (k + 1/2) dr, like J_theta) and applies the downstagger S_rho^(-, mA) of Eq.
+ * spatialAM_staggerS (the J_rho stagger of Eq. spatialAM_filter_Jr, z filter the identity) into a
+ * plan-owned copy before the steps of each call: one more launch per call, J itself is not
+ * modified; the plan holds a second current-sized device buffer.  fdetd_batch_add refuses such a
+ * plan with a current (a batch takes J on the Yee locations; fdetd_current_correct gives them). */
+#define FDETD_FLAG_J_ON_PRIMARY 2ull
 int fdetd_plan(fdetd_plan_t* out, int Nz, int Nr, int M, int order, double dz, double dr, double dt,
                int precision, uint64_t flags);
 

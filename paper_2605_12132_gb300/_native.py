@@ -227,6 +227,7 @@ class FdetdPlan:
 
 
 SPECTRAL_COLUMNS = 1   # plan flag: the z transform in its column-split form (FDETD_FLAG_SPECTRAL_COLUMNS)
+J_ON_PRIMARY = 2       # plan flag: J_rho given on the primary radial grid, downstaggered by the step
 
 
 def fdetd_plan_modes(Nz, Nr, modes, order, dz, dr, dt, precision="fp64", flags=0):

@@ -34,6 +34,8 @@ static df to_df(double x) {
 struct fdetd_plan_s {
   int Nz = 0, Nr = 0, nmodes = 0, order = 0, precision = 0, logNz = 0, tw_count = 0;
   bool columns = false;       // z transform in its column-split form (three launches)
+  bool j_primary = false;     // J_rho handed to fdetd_step on the primary grid (FDETD_FLAG_J_ON_PRIMARY)
+  void* d_jstag = nullptr;    // its downstaggered copy, the J the step uses
   double dz = 0, dr = 0, dt = 0;
   std::vector<int> modes;
   void* d_P = nullptr;
@@ -89,7 +91,7 @@ static void plan_free(fdetd_plan_s* p) {
   if (!p) return;
   prof_collect(p);
   void* ptrs[] = {p->d_P,    p->d_Q,   p->d_phase,  p->d_zsym, p->d_zsymk, p->d_lam,
-                  p->d_tw,   p->d_coef, p->d_src,   p->d_hostio, p->d_err,  p->d_cur, p->d_waits};
+                  p->d_tw,   p->d_coef, p->d_src,   p->d_hostio, p->d_err,  p->d_cur, p->d_waits, p->d_jstag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->tc) tc_destroy(p->tc);
@@ -135,6 +137,7 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
   p->Nz = Nz;
   p->Nr = Nr;
   p->columns = columns;
+  p->j_primary = (flags & FDETD_FLAG_J_ON_PRIMARY) != 0;
   p->nmodes = nmodes;
   p->order = order;
   p->precision = precision;
@@ -270,6 +273,11 @@ extern "C" int fdetd_plan_modes(fdetd_plan_t* out, int Nz, int Nr, const int* mo
     const size_t cbytes = (size_t)nmodes * 9 * n * Nz * (fp64 ? 16 : 8);
     if ((e = cudaMalloc(&p->d_coef, cbytes)) != cudaSuccess) goto cuda_fail;
     p->bytes += cbytes;
+    if (p->j_primary) {
+      const size_t jbytes = (size_t)nmodes * 3 * n * Nz * (fp64 ? 16 : 8);
+      if ((e = cudaMalloc(&p->d_jstag, jbytes)) != cudaSuccess) goto cuda_fail;
+      p->bytes += jbytes;
+    }
     if (!p->columns && (is_pow2(Nz) ? spectral_needs_source(Nz, prec_k, p->tw_count)
                                      : spectral_mixed_needs_source(Nz, prec_k, p->tw_count))) {
       const size_t sbytes = (size_t)nmodes * 2 * 3 * n * Nz * (fp64 ? 16 : 8);
@@ -370,12 +378,20 @@ static int stage_backproject(fdetd_plan_s* p, void* fields, cudaStream_t st) {
   return FDETD_OK;
 }
 
+static int stagger_current(fdetd_plan_s* p, const void* J, cudaStream_t st);
+
 extern "C" int fdetd_step(fdetd_plan_t p, void* fields, const void* J, int nsteps, void* stream) {
   if (!p) return fail(FDETD_ERR_ARG, "plan is null");
   if (!fields) return fail(FDETD_ERR_ARG, "fields is null");
   if (nsteps < 0) return fail(FDETD_ERR_ARG, "nsteps < 0");
   if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
+  if (p->j_primary && J && nsteps > 0) {
+    // J_rho deposited on the primary grid: S_rho^(-, mA) into the plan's copy, which the steps then use
+    const int rc = stagger_current(p, J, st);
+    if (rc) return rc;
+    J = p->d_jstag;
+  }
   for (int s = 0; s < nsteps; ++s) {
     int rc = stage_project(p, fields, J, st);
     if (!rc) rc = stage_spectral(p, J != nullptr, st);
@@ -525,6 +541,39 @@ extern "C" int fdetd_destagger(fdetd_plan_t p, const void* fields, void* out, vo
   return FDETD_OK;
 }
 
+// Lagrange weights of the half point rho_k + dr / 2 on the 2 ND primary nodes k - ND + 1 .. k + ND (the
+// downstagger S_rho^(-, mA) of Eq. spatialAM_staggerS)
+static void half_point_weights(int ND, double* w) {
+  for (int i = -ND + 1; i <= ND; ++i) {
+    double num = 1.0, den = 1.0;
+    for (int l = -ND + 1; l <= ND; ++l)
+      if (l != i) {
+        num *= 0.5 - l;
+        den *= (double)(i - l);
+      }
+    w[i + ND - 1] = num / den;
+  }
+}
+
+// J with J_rho on the primary grid -> the plan's scratch with J_rho downstaggered (FDETD_FLAG_J_ON_PRIMARY)
+static int stagger_current(fdetd_plan_s* p, const void* J, cudaStream_t st) {
+  CurParams cp;
+  memset(&cp, 0, sizeof(cp));
+  cp.J = J;
+  cp.out = p->d_jstag;
+  cp.stagger_only = 1;
+  cp.dr = p->dr;
+  cp.Nz = p->Nz;
+  cp.n = p->Nr;
+  cp.ND = p->order / 2;
+  cp.nm = p->nmodes;
+  for (int i = 0; i < p->nmodes; ++i) cp.m[i] = p->modes[i];
+  half_point_weights(cp.ND, cp.w);
+  cudaError_t e = launch_current(cp, p->precision == FDETD_PREC_FP64, st);
+  if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("J_rho downstagger: ") + cudaGetErrorString(e));
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_current_correct(fdetd_plan_t p, const void* J, const void* rho_xy, void* J_out, void* stream) {
   if (!p || !J || !rho_xy || !J_out) return fail(FDETD_ERR_ARG, "null argument");
   const size_t elt = p->precision == FDETD_PREC_FP64 ? 16 : 8;
@@ -586,15 +635,7 @@ extern "C" int fdetd_current_correct(fdetd_plan_t p, const void* J, const void* 
   cp.ND = ND;
   cp.nm = p->nmodes;
   for (int i = 0; i < p->nmodes; ++i) cp.m[i] = p->modes[i];
-  for (int i = -ND + 1; i <= ND; ++i) {
-    double num = 1.0, den = 1.0;
-    for (int l = -ND + 1; l <= ND; ++l)
-      if (l != i) {
-        num *= 0.5 - l;
-        den *= (double)(i - l);
-      }
-    cp.w[i + ND - 1] = num / den;
-  }
+  half_point_weights(ND, cp.w);
   cudaError_t e = launch_current(cp, p->precision == FDETD_PREC_FP64, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(FDETD_ERR_CUDA, std::string("current correction: ") + cudaGetErrorString(e));
   return FDETD_OK;
@@ -889,6 +930,8 @@ extern "C" int fdetd_batch_add(fdetd_batch_t b, fdetd_plan_t plan, void* fields,
   if (((uintptr_t)fields & 15) || ((uintptr_t)J & 15)) return fail(FDETD_ERR_ARG, "pointers must be 16-byte aligned");
   for (auto& i : b->inst)
     if (i.plan == plan) return fail(FDETD_ERR_ARG, "a plan may appear once per batch (its scratch is not shared)");
+  if (plan->j_primary && J)
+    return fail(FDETD_ERR_ARG, "a J_ON_PRIMARY plan steps with fdetd_step (a batch takes J on the Yee locations)");
   cudaStream_t s;
   cudaEvent_t e;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(FDETD_ERR_CUDA, "stream");

@@ -98,6 +98,7 @@ struct CurArgs {
   const K* mri;     // [nm][n]: m / rho_k
   T w[32];          // half-point Lagrange weights, nodes t = -ND+1 .. ND
   int Nz, n, ND, R;
+  int stagger_only;      // 1: step 1 alone (J_rho downstaggered, J_theta and J_z copied), no correction
   signed char sign[64];  // mA extension sign per mode
 };
 
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(256) current_kernel(CurArgs<T> a) {
   C* raw = reinterpret_cast<C*>(ph);
   const size_t fs = (size_t)Nz * n, zq = (size_t)z0 * n;
   const C* J = a.J + (size_t)md * 3 * fs;
-  const C* rho = a.rho_xy + (size_t)md * fs;
+  const C* rho = a.stagger_only ? nullptr : a.rho_xy + (size_t)md * fs;
   C* O = a.out + (size_t)md * 3 * fs;
   const T sgn = (T)a.sign[md];
   const K* mr = a.mri + (size_t)md * n;
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(256) current_kernel(CurArgs<T> a) {
     js[i] = v;
     O[zq + i] = v;
   }
+  if (a.stagger_only) return;  // uniform over the block: nothing below runs
   __syncthreads();
 
   // 2. delta = rho_xy - Div^+ J_rho - (i sigma m / rho) J_theta, thread per radius over the rows
@@ -363,12 +365,16 @@ cudaError_t run_current(const CurParams& p, cudaStream_t st) {
   a.out = (typename cplx<T>::type*)p.out;
   const K* base = (const K*)p.bands;
   const size_t nm = p.nm, n = p.n, W = 2 * p.ND + 1;
-  a.divp = base;
-  a.dm = a.divp + nm * W * n;
-  a.lo = a.dm + nm * W * n;
-  a.up = a.lo + nm * n * p.ND;
-  a.ipiv = a.up + nm * n * p.ND;
-  a.mri = a.ipiv + nm * n;
+  a.stagger_only = p.stagger_only;
+  a.divp = a.dm = a.lo = a.up = a.ipiv = a.mri = nullptr;
+  if (base) {  // the correction's tables (absent in the stagger-only form)
+    a.divp = base;
+    a.dm = a.divp + nm * W * n;
+    a.lo = a.dm + nm * W * n;
+    a.up = a.lo + nm * n * p.ND;
+    a.ipiv = a.up + nm * n * p.ND;
+    a.mri = a.ipiv + nm * n;
+  }
   a.Nz = p.Nz;
   a.n = p.n;
   a.ND = p.ND;
@@ -398,6 +404,7 @@ cudaError_t run_current(const CurParams& p, cudaStream_t st) {
 
 cudaError_t launch_current(const CurParams& p, bool fp64, cudaStream_t st) {
   if (p.ND < 1 || p.ND > MAX_ND || p.nm < 1 || p.nm > 64) return cudaErrorInvalidValue;
+  if (!p.stagger_only && (!p.bands || !p.rho_xy)) return cudaErrorInvalidValue;
   return fp64 ? run_current<double>(p, st) : run_current<float>(p, st);
 }
 

@@ -195,6 +195,7 @@ struct CurParams {
   double dr;
   int Nz, n, ND, nm;
   int m[64];
+  int stagger_only;    // 1: the downstagger of J_rho alone (rho_xy and bands unused, may be null)
 };
 cudaError_t launch_current(const CurParams& p, bool fp64, cudaStream_t st);
 

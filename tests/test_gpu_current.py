@@ -58,3 +58,37 @@ def test_current_pipeline_rejects_aliasing():
     rho = torch.zeros((1, 64, 16), dtype=torch.complex64, device="cuda")
     with pytest.raises(fd.FdetdError):
         fd.fdetd_current_correct(plan, J, rho, J)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("bf16x6", 2e-6)])
+def test_j_on_primary_flag_downstaggers_j_rho(prec, tol):
+    # a plan with J_ON_PRIMARY stepping a current whose J_rho sits on the primary grid equals a plain plan
+    # stepping the oracle's downstaggered current (S_rho^(-, mA) of Eq. spatialAM_staggerS); J is left as given
+    from paper_2605_12132_gb300 import _native as nat
+    from tests.gpu_util import zero_axis
+    rng = np.random.default_rng(12)
+    Nz, Nr, modes, order = 64, 40, [0, 1, 2], 8
+    F = zero_axis(rng.standard_normal((3, 6, Nz, Nr)) + 1j * rng.standard_normal((3, 6, Nz, Nr)))
+    J = rng.standard_normal((3, 3, Nz, Nr)) + 1j * rng.standard_normal((3, 3, Nz, Nr))
+    Js = np.stack([np.stack([cur.s_rho_minus(J[i, 0], order, abs(m - 1) % 2 == 0), J[i, 1], J[i, 2]])
+                   for i, m in enumerate(modes)])
+    flagged = fd.fdetd_plan_modes(Nz, Nr, modes, order, 1 / 16, 1 / 4, 1 / 16, precision=prec,
+                                  flags=nat.J_ON_PRIMARY)
+    plain = fd.fdetd_plan_modes(Nz, Nr, modes, order, 1 / 16, 1 / 4, 1 / 16, precision=prec)
+    dt = plain.complex_dtype
+    j = torch.from_numpy(J).to(dt).cuda()
+    j0 = j.clone()
+    a = torch.from_numpy(F).to(dt).cuda()
+    fd.fdetd_step(flagged, a, j, 2)
+    flagged.status()
+    assert torch.equal(j, j0)
+    b = torch.from_numpy(F).to(dt).cuda()
+    fd.fdetd_step(plain, b, torch.from_numpy(Js).to(dt).cuda(), 2)
+    plain.status()
+    err = (torch.linalg.vector_norm(a.to(torch.complex128) - b) / torch.linalg.vector_norm(b.to(torch.complex128)))
+    assert float(err) < tol, float(err)
+    # a batch takes J on the Yee locations: the flagged plan with a current is refused there
+    batch = fd.FdetdBatch()
+    with pytest.raises(fd.FdetdError):
+        batch.add(flagged, a, j)
+    batch.close()
