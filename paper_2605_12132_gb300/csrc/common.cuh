@@ -53,4 +53,26 @@ struct ZSymK { df spr, spi, k2, pad; };
 
 __device__ __forceinline__ unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
 
+// 4 x 4 transpose over the four lanes 4g .. 4g+3 of a group (q = lane & 3; every lane of the warp takes part):
+// on entry x[c] is element (q, c) of the group's block, on exit element (c, q).  Two butterfly exchanges:
+// across lanes q ^ 1 the elements whose column's low bit differs from q's, then across q ^ 2 those whose
+// column's high bit differs.
+__device__ __forceinline__ void transpose4(float* x, int q) {
+  const bool lo = q & 1, hi = q & 2;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = lo ? x[2 * k] : x[2 * k + 1];
+    const float r = __shfl_xor_sync(0xffffffffu, send, 1);
+    if (lo) x[2 * k] = r;
+    else x[2 * k + 1] = r;
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = hi ? x[k] : x[k + 2];
+    const float r = __shfl_xor_sync(0xffffffffu, send, 2);
+    if (hi) x[k] = r;
+    else x[k + 2] = r;
+  }
+}
+
 }  // namespace fdetd

@@ -271,6 +271,9 @@ __device__ __forceinline__ void stage0_out(const float2* sm, const float2* tw, f
                                            const SplitColumn* sc) {
   typedef Shape<LOGN> SH;
   constexpr int R = SH::R(0), L = SH::L(0), PB = 8 / R, NT = SH::NT;
+  // split pieces from full warps with a radix of 4 or 8: a 4 x 4 transpose across each group of four lanes
+  // (consecutive n1) and four outputs r leaves every lane with four consecutive z, one 16-byte store per piece
+  constexpr bool VEC = SPLIT && NT >= 32 && (R == 4 || R == 8);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     // the split stores are kept rolled: unrolled, they push the kernel out of the instruction cache
@@ -284,13 +287,30 @@ __device__ __forceinline__ void stage0_out(const float2* sm, const float2* tw, f
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmulconj(v[r], tw[(r - 1) * L + n1]);
       dft_small<R, true>(v);
+      if constexpr (VEC) {
+        const int q = threadIdx.x & 3;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int z = n1 + r * L;
-        if (!SPLIT)
-          dst[a][z] = v[r];
-        else
-          split_store(sc[a], z, v[r].x, v[r].y);
+        for (int h = 0; h < R / 4; ++h) {
+          float xr[4], xi[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            xr[k] = v[4 * h + k].x;
+            xi[k] = v[4 * h + k].y;
+          }
+          transpose4(xr, q);
+          transpose4(xi, q);
+          // lane q now holds z = (n1 - q) + k + (4 h + q) L, k = 0 .. 3
+          split_store4(sc[a], (n1 & ~3) + (4 * h + q) * L, xr, xi);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int z = n1 + r * L;
+          if (!SPLIT)
+            dst[a][z] = v[r];
+          else
+            split_store(sc[a], z, v[r].x, v[r].y);
+        }
       }
     }
   }

@@ -102,6 +102,35 @@ __device__ __forceinline__ void split_store(const SplitColumn& d, int z, float v
   }
 }
 
+// split_store of four consecutive z (z0 a multiple of 4): their (re, im) pairs share one 16-byte chunk of the
+// swizzled row, so each piece is one 16-byte store
+__device__ __forceinline__ void split_store4(const SplitColumn& d, int z0, const float* vr, const float* vi) {
+  const int zl = z0 & 63;
+  const size_t off = (size_t)(z0 >> 6) * 16384 + (size_t)(zl >> 5) * 8192 + ((uint32_t)(((zl & 31) >> 2) ^ d.jr7) << 4);
+  unsigned char* q = d.base + off;
+  float r0[4], r1[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    r0[k] = vr[k];
+    r1[k] = vi[k];
+  }
+  for (int p = 0; p < d.npieces; ++p) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(r0[k]), h1 = __float2bfloat16_rn(r1[k]);
+      __nv_bfloat162 pr;
+      pr.x = h0;
+      pr.y = h1;
+      w[k] = *reinterpret_cast<const uint32_t*>(&pr);
+      r0[k] -= __bfloat162float(h0);
+      r1[k] -= __bfloat162float(h1);
+    }
+    *reinterpret_cast<uint4*>(q) = make_uint4(w[0], w[1], w[2], w[3]);
+    q += d.piece_stride;
+  }
+}
+
 // ---------------------------------------------------------------- CUDA-core projections
 struct ProjArgs {
   const void* fields;  // [nmodes][6][Nz][Nr] complex<T>
