@@ -233,7 +233,7 @@ def _build_plans(fd, cfgs, prec):
 
 
 def batch_gemm_flops(cfgs, hasJ=True):
-    """Algorithmic FLOPs of one step's radial transforms over the mix (the survey's count: per cell and
+    """Algorithmic FLOPs of one step's radial transforms over the mix (per cell and
     mode, 9 products of a real Nr x Nr matrix with a complex column forward including the current, 6 back,
     4 Nr flops each), and the dense-equivalent count the tensor-core kernels execute per bf16 product
     (15 / 10 nonzero Nr x Nr blocks of the folded projection / back-projection matrices)."""
@@ -380,8 +380,9 @@ def run_batch(args, rank, world, dist):
         pk = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": algo * products / tsec / 1e12, "peak": pk, "unit": "TFLOP/s",
                 "executed_tflops": execd * products / tsec / 1e12, "executed_frac": execd * products / tsec / 1e12 / pk,
-                "note": f"achieved = the survey's algorithmic flops x {products} bf16 products per FP32-accurate "
-                        "product; executed = the folded dense blocks the kernel multiplies"}
+                "note": f"achieved = the algorithmic flops (9 forward and 6 back Nr x Nr real products per cell and "
+                        f"mode) x {products} bf16 products per FP32-accurate product; executed = the folded dense "
+                        "blocks the kernel multiplies"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = recorded_traffic(dom, f"uneven_mix_{len(cfgs)}", prec)
     roof["algorithmic"] = algo
