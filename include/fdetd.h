@@ -334,6 +334,11 @@ int fdetd_batch_collect_stage_times(fdetd_batch_t batch);
 int fdetd_batch_pipeline_waits(fdetd_batch_t batch, unsigned long long* out);
 int fdetd_batch_stage_times(fdetd_batch_t batch, double* ms, long* steps);
 int fdetd_batch_set_host_pipeline(fdetd_batch_t batch, int parts);
+/* Host only: the split the host-buffer step uses.  n items of bytes[k] into at most `parts` contiguous
+ * parts: part p closes at the first item where the running size reaches (p + 1) / P of the total, P =
+ * min(parts, n), the last part takes the rest.  part_of[k] = part of item k; returns the number of
+ * parts, or -FDETD_ERR_ARG. */
+int fdetd_host_split_parts(const size_t* bytes, int n, int parts, int* part_of);
 int fdetd_batch_step_host(fdetd_batch_t batch, void* const* host_fields, const void* const* host_J, int nlaunch,
                           void* stream);
 int fdetd_batch_destroy(fdetd_batch_t batch);

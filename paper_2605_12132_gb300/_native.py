@@ -90,6 +90,7 @@ def lib():
     L.fdetd_batch_stage_times.argtypes = [c_vp, dp, ctypes.POINTER(ctypes.c_long)]
     L.fdetd_batch_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fdetd_batch_set_host_pipeline.argtypes = [c_vp, c_int]
+    L.fdetd_host_split_parts.argtypes = [ctypes.POINTER(ctypes.c_size_t), c_int, c_int, ctypes.POINTER(c_int)]
     L.fdetd_plan_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fdetd_batch_step_host.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
@@ -433,6 +434,17 @@ def fdetd_plan_cache_stats():
     _check(lib().fdetd_plan_cache_stats(ctypes.byref(b), ctypes.byref(lim), ctypes.byref(n), ctypes.byref(h),
                                         ctypes.byref(m)))
     return {"bytes": b.value, "limit": lim.value, "entries": n.value, "hits": h.value, "misses": m.value}
+
+
+def fdetd_host_split_parts(sizes, parts):
+    """Host only: the part of each item in the host-buffer batch step's split of `sizes` into `parts`."""
+    n = len(sizes)
+    b = (ctypes.c_size_t * max(n, 1))(*[int(x) for x in sizes])
+    out = (ctypes.c_int * max(n, 1))()
+    r = lib().fdetd_host_split_parts(b, n, int(parts), out)
+    if r < 0:
+        _check(-r)
+    return [out[k] for k in range(n)], r
 
 
 def fdetd_host_coeffs(kind, order):

@@ -1184,24 +1184,37 @@ static size_t inst_field_bytes(const fdetd_plan_s* p) {
 
 // Splits the instances into at most host_parts contiguous parts of about equal bytes and captures a one-step
 // graph for each (groups with the tile shapes the main capture chose).
+// Contiguous split of n items of the given sizes into at most `parts` parts: part p closes at the first item
+// where the running size reaches (p + 1) / P of the total (P = min(parts, n)), the last part takes the rest.
+// part_of[k] = the part of item k; returns the number of parts.
+static int split_parts(const size_t* bytes, int n, int parts, int* part_of) {
+  const int P = std::max(1, std::min(parts, n));
+  size_t total = 0;
+  for (int k = 0; k < n; ++k) total += bytes[k];
+  size_t acc = 0;
+  int p = 0;
+  for (int k = 0; k < n; ++k) {
+    part_of[k] = p;
+    acc += bytes[k];
+    if (k < n - 1 && p < P - 1 && acc * P >= total * (size_t)(p + 1)) ++p;
+  }
+  return n ? p + 1 : 0;
+}
+
+extern "C" int fdetd_host_split_parts(const size_t* bytes, int n, int parts, int* part_of) {
+  if (n < 0 || parts < 1 || (n && (!bytes || !part_of))) return -FDETD_ERR_ARG;
+  return split_parts(bytes, n, parts, part_of);
+}
+
 static int build_parts(fdetd_batch_s* b, cudaStream_t st) {
   batch_release_parts(b);
   const int n = (int)b->inst.size();
-  const int P = std::max(1, std::min(b->host_parts, n));
-  size_t total = 0;
-  for (auto& i : b->inst) total += inst_field_bytes(i.plan);
-  std::vector<int> cur;
-  size_t acc = 0;
-  for (int k = 0; k < n; ++k) {
-    cur.push_back(k);
-    acc += inst_field_bytes(b->inst[k].plan);
-    const bool last = k == n - 1;
-    if (last || (acc * P >= total * (b->parts.size() + 1) && (int)b->parts.size() < P - 1)) {
-      b->parts.emplace_back();
-      b->parts.back().members = cur;
-      cur.clear();
-    }
-  }
+  std::vector<size_t> sizes(n);
+  std::vector<int> part_of(n);
+  for (int k = 0; k < n; ++k) sizes[k] = inst_field_bytes(b->inst[k].plan);
+  const int np = split_parts(sizes.data(), n, b->host_parts, part_of.data());
+  b->parts.resize(np);
+  for (int k = 0; k < n; ++k) b->parts[part_of[k]].members.push_back(k);
   if (!b->s_in && cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking) != cudaSuccess)
     return fail(FDETD_ERR_CUDA, "stream");
   if (!b->s_out && cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking) != cudaSuccess)

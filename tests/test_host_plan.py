@@ -253,3 +253,32 @@ def test_radial_table_cache_returns_the_same_tables_and_honours_its_limit():
     for k in ("PE", "PB", "QE", "QB", "lam", "mu"):
         assert np.array_equal(a[k], c[k]), k
     native.fdetd_plan_cache_set_limit(4 << 30)
+
+
+def test_host_step_split_is_contiguous_ordered_and_balanced():
+    # the split of the host-buffer batch step: contiguous parts in instance order, none empty, at most
+    # min(parts, n), each closing at the first item that reaches its share of the total bytes
+    _lib_or_skip()
+    rng = np.random.default_rng(5)
+    cases = [[1000] * 64, list(rng.integers(1, 10 ** 6, 37)), [5, 10 ** 9, 3, 4, 7], [42], list(rng.integers(1, 100, 8))]
+    for sizes in cases:
+        for parts in (1, 2, 3, 8, 16, 100):
+            part_of, nparts = native.fdetd_host_split_parts(sizes, parts)
+            n = len(sizes)
+            P = min(parts, n)
+            assert 1 <= nparts <= P
+            assert part_of[0] == 0 and part_of[-1] == nparts - 1
+            assert all(b - a in (0, 1) for a, b in zip(part_of, part_of[1:]))      # contiguous, ordered
+            total = sum(sizes)
+            csum = np.cumsum(sizes)
+            for p in range(nparts - 1):
+                last = max(k for k in range(n) if part_of[k] == p)
+                assert csum[last] * P >= total * (p + 1)                          # reached its share
+                first = min(k for k in range(n) if part_of[k] == p)
+                if first > 0 and last > first:
+                    assert csum[last - 1] * P < total * (p + 1)                   # and closed at the first such item
+    part_of, nparts = native.fdetd_host_split_parts([1000] * 64, 16)
+    assert nparts == 16 and all(part_of.count(p) == 4 for p in range(16))
+    assert native.fdetd_host_split_parts([], 4) == ([], 0)
+    with pytest.raises(native.FdetdError):
+        native.fdetd_host_split_parts([1, 2], 0)
