@@ -26,8 +26,10 @@
 // Both kernels are persistent: one CTA per SM walks a tile table (tiles of several instances in
 // one launch), the pipeline stages run on across tile boundaries, and with NBUF = 2 the TMEM
 // accumulators are double-buffered so the epilogue of one tile overlaps the MMAs of the next.
-// Warp roles, projection: 0-7 convert, 8-11 epilogue (TMEM -> registers -> global), 12 issues the
-// bulk copies, 13 issues tcgen05.mma (one thread).  Back-projection: 0-3 epilogue, 4 copies, 5 MMA.
+// Warp roles, projection: 0-7 convert, 8-15 epilogue (TMEM -> registers -> global; two warps per TMEM lane
+// quarter, alternate 32-column chunks), 16 issues the TMA and bulk copies, 17 issues tcgen05.mma (one thread).
+// Back-projection: 0-3 epilogue, 4 copies, 5 MMA.  With NBUF = 1 (BF16x6 at TN = 256: the leading and
+// correction accumulators fill the 512 TMEM columns) the MMAs of the next tile wait for the drain.
 // Every mbarrier wait is bounded; on timeout the kernel records an error code in the instance's
 // flag, tells the other roles to stop through a shared abort flag, drains its own copies and
 // MMAs, and frees TMEM before returning.
