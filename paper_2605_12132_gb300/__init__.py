@@ -11,6 +11,13 @@ in the library's CUDA kernels.  PyTorch supplies device memory and streams.
 The library is loaded lazily on first use; importing this package does not need a GPU.
 """
 from ._native import (  # noqa: F401
+    J_ON_PRIMARY,
+    SPECTRAL_COLUMNS,
+    fdetd_host_split_parts,
+    fdetd_plan_cache_set_limit,
+    fdetd_plan_cache_stats,
+    fdetd_plan_cache_warm,
+    pipeline_report,
     PRECISIONS,
     EnvelopePlan,
     FdetdBatch,
