@@ -15,20 +15,20 @@ import numpy as np
 from .maxwell import TAU, Radial, dz_minus, dz_plus
 
 
-def div_E(F, rad, order, dz):
+def div_E(F, rad, order, dz, truncated=False):
     Er, Et, Ez = F[0], F[1], F[2]
     div_r = ((rad.rhom[None, :] * Er) @ rad.Dp.T) / rad.rho
-    return div_r + TAU * rad.m * Et / rad.rho + dz_plus(Ez, order, dz)
+    return div_r + TAU * rad.m * Et / rad.rho + dz_plus(Ez, order, dz, truncated=truncated)
 
 
-def div_J(J, rad, order, dz):
-    return div_E(np.concatenate([J, np.zeros_like(J)]), rad, order, dz)
+def div_J(J, rad, order, dz, truncated=False):
+    return div_E(np.concatenate([J, np.zeros_like(J)]), rad, order, dz, truncated)
 
 
-def div_B(F, rad, order, dz):
+def div_B(F, rad, order, dz, truncated=False):
     Br, Bt, Bz = F[3], F[4], F[5]
     div_r = ((rad.rho[None, :] * Br) @ rad.Dm.T)[:, 1:] / rad.rhom[1:]
-    return div_r + TAU * rad.m * Bt[:, 1:] / rad.rhom[1:] + dz_minus(Bz, order, dz)[:, 1:]
+    return div_r + TAU * rad.m * Bt[:, 1:] / rad.rhom[1:] + dz_minus(Bz, order, dz, truncated=truncated)[:, 1:]
 
 
 def energy(F, rad, dz):

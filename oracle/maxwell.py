@@ -16,7 +16,9 @@ Follows Sec. 2 of the paper:
 * the B_z axis value of the m = 0 mode extrapolated with the coefficients of
   Sec. 2.4, zero for m >= 1;
 * the discrete Ampere / Faraday equations Eqs. spatialAM_maxwell_Er ... _Bz, and
-  periodic z, where the same staggered stencil acts along z;
+  periodic z, where the same staggered stencil acts along z; the real-space evaluators (ii) and (iii) also
+  take the paper's own z boundary (Sec. 2.2, after Eq. bandedmatricesAM_Az: taps beyond the ends dropped,
+  truncated=True), which the spectral evaluator (i) and the GPU path do not;
 * the midpoint exponential step of Eq. maxwellAM_solution2, read with the Delta t
   factor that the integral of Eq. maxwellAM_solution implies:
         Psi(t+dt) = exp(dt H) Psi(t) - dt * exp(dt H / 2) J.
@@ -136,24 +138,38 @@ class Radial:
 
 
 # --------------------------------------------------------------------------
-# z stencils (periodic) and their discrete Fourier symbols
+# z stencils (periodic, or truncated at the ends) and their discrete Fourier symbols
 # --------------------------------------------------------------------------
 
-def dz_minus(f, order, dz, axis=0):
-    """(D_z^- f)_i = dz^-1 sum_n c_n (f_{i+n-1} - f_{i-n}), periodic; integer -> half points."""
+def _shift(f, s, axis, truncated):
+    """g_i = f_{i+s}: periodic (wrapped), or truncated (zero where i + s falls outside 0 .. Nz-1)."""
+    g = np.roll(f, -s, axis=axis)
+    if truncated and s != 0:
+        Nz = f.shape[axis]
+        idx = np.arange(Nz) + s
+        outside = (idx < 0) | (idx >= Nz)
+        shape = [1] * f.ndim
+        shape[axis] = Nz
+        g = np.where(outside.reshape(shape), 0, g)
+    return g
+
+
+def dz_minus(f, order, dz, axis=0, truncated=False):
+    """(D_z^- f)_i = dz^-1 sum_n c_n (f_{i+n-1} - f_{i-n}); integer -> half points; periodic, or with the
+    taps beyond the ends dropped (Sec. 2.2)."""
     c = staggered_coeffs(order)
     out = np.zeros_like(f)
     for n in range(1, len(c) + 1):
-        out += c[n - 1] * (np.roll(f, -(n - 1), axis=axis) - np.roll(f, n, axis=axis))
+        out += c[n - 1] * (_shift(f, n - 1, axis, truncated) - _shift(f, -n, axis, truncated))
     return out / dz
 
 
-def dz_plus(g, order, dz, axis=0):
-    """(D_z^+ g)_i = dz^-1 sum_n c_n (g_{i+n} - g_{i-n+1}), periodic; half points -> integer."""
+def dz_plus(g, order, dz, axis=0, truncated=False):
+    """(D_z^+ g)_i = dz^-1 sum_n c_n (g_{i+n} - g_{i-n+1}); half points -> integer; periodic, or truncated."""
     c = staggered_coeffs(order)
     out = np.zeros_like(g)
     for n in range(1, len(c) + 1):
-        out += c[n - 1] * (np.roll(g, -n, axis=axis) - np.roll(g, n - 1, axis=axis))
+        out += c[n - 1] * (_shift(g, n, axis, truncated) - _shift(g, -(n - 1), axis, truncated))
     return out / dz
 
 
@@ -320,11 +336,11 @@ def kz_spectrum(Nz, Nr, m, order, dz, dr, q):
 # Real-space operator application (used by evaluators (ii) and (iii))
 # --------------------------------------------------------------------------
 
-def apply_H(F, rad, order, dz):
+def apply_H(F, rad, order, dz, truncated=False):
     """dPsi/dt = H Psi in real space, Eqs. spatialAM_maxwell_Er ... _Bz (J excluded).
 
     F: [6][Nz][Nr]; slot 0 of staggered-grid fields is ignored on input and zero on output.
-    Radial operators act along the last axis (f @ D^T), z stencils are periodic.
+    Radial operators act along the last axis (f @ D^T); z stencils periodic, or truncated at the ends.
     """
     m = rad.m
     Er, Et, Ez, Br, Bt, Bz = F
@@ -332,11 +348,11 @@ def apply_H(F, rad, order, dz):
     out = np.zeros_like(F)
     bz_full = Bz[:, 1:] @ rad.X0.T                       # Bz with its axis value
     rhom_bt = rhom[None, :] * Bt                          # slot 0 multiplied by rho_(-),0 = 0
-    out[0, :, 1:] = (-dz_plus(Bt, order, dz) + TAU * m * Bz / np.where(rhom > 0, rhom, 1.0))[:, 1:]
-    out[1] = dz_plus(Br, order, dz) - bz_full @ rad.Dp.T
+    out[0, :, 1:] = (-dz_plus(Bt, order, dz, truncated=truncated) + TAU * m * Bz / np.where(rhom > 0, rhom, 1.0))[:, 1:]
+    out[1] = dz_plus(Br, order, dz, truncated=truncated) - bz_full @ rad.Dp.T
     out[2] = -TAU * m * Br / rho + (rhom_bt @ rad.Dp.T) / rho
-    out[3] = dz_minus(Et, order, dz) - TAU * m * Ez / rho
-    out[4, :, 1:] = (-dz_minus(Er, order, dz) + Ez @ rad.Dm.T)[:, 1:]
+    out[3] = dz_minus(Et, order, dz, truncated=truncated) - TAU * m * Ez / rho
+    out[4, :, 1:] = (-dz_minus(Er, order, dz, truncated=truncated) + Ez @ rad.Dm.T)[:, 1:]
     rho_et = (rho[None, :] * Et) @ rad.Dm.T
     out[5, :, 1:] = (TAU * m * Er[:, 1:] / rhom[1:] - rho_et[:, 1:] / rhom[1:])
     return out
@@ -360,7 +376,7 @@ def _J_state(J):
 # Evaluator (ii): brute-force expm of the whole real-space operator (tiny grids)
 # --------------------------------------------------------------------------
 
-def realspace_matrix(Nz, Nr, m, order, dz, dr):
+def realspace_matrix(Nz, Nr, m, order, dz, dr, truncated=False):
     """Dense matrix of apply_H on the unknowns (all z, interior staggered slots), column by column."""
     rad = Radial(Nr, order, dr, m)
     sizes = _sizes(Nr)
@@ -370,7 +386,7 @@ def realspace_matrix(Nz, Nr, m, order, dz, dr):
     for col in range(dim):
         x = np.zeros(dim, complex)
         x[col] = 1.0
-        A[:, col] = _flatten(apply_H(_unflatten(x, Nz, Nr), rad, order, dz))
+        A[:, col] = _flatten(apply_H(_unflatten(x, Nz, Nr), rad, order, dz, truncated))
     return A
 
 
@@ -384,10 +400,11 @@ def _unflatten(x, Nz, Nr):
     return np.stack([scatter(x[i * nun:(i + 1) * nun], Nr) for i in range(Nz)], axis=1)
 
 
-def step_expm_realspace(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1):
-    """Evaluator (ii): Eq. maxwellAM_solution2 with scipy's scaling-and-squaring expm of the full operator."""
+def step_expm_realspace(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, truncated=False):
+    """Evaluator (ii): Eq. maxwellAM_solution2 with scipy's scaling-and-squaring expm of the full operator
+    (periodic z, or truncated=True: the taps beyond the z ends dropped)."""
     rad = Radial(Nr, order, dr, m)
-    A = realspace_matrix(Nz, Nr, m, order, dz, dr)
+    A = realspace_matrix(Nz, Nr, m, order, dz, dr, truncated)
     Eh = scipy.linalg.expm(A * (dt / 2))
     E1 = Eh @ Eh
     x = _flatten(F)
@@ -408,7 +425,7 @@ def h_bound(rad, order, dz):
     return 2 * csum / dz + radial + 2 * rad.m / rad.dr
 
 
-def taylor_exp(F, rad, order, dz, t, taylor_order, substeps):
+def taylor_exp(F, rad, order, dz, t, taylor_order, substeps, truncated=False):
     """exp(t H) F by `substeps` repeated Taylor polynomials sum_{n<=N} (h H)^n / n! (Sec. 2.5 summary)."""
     h = t / substeps
     x = _zero_axis_slots(F)
@@ -416,13 +433,13 @@ def taylor_exp(F, rad, order, dz, t, taylor_order, substeps):
         term = x
         acc = x.copy()
         for n in range(1, taylor_order + 1):
-            term = apply_H(term, rad, order, dz) * (h / n)
+            term = apply_H(term, rad, order, dz, truncated) * (h / n)
             acc = acc + term
         x = acc
     return x
 
 
-def step_taylor(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, taylor_order=None, substeps=None):
+def step_taylor(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, taylor_order=None, substeps=None, truncated=False):
     """Evaluator (iii): Eq. maxwellAM_solution2 with the paper's Taylor-expanded exponentials.
 
     By default the Taylor order and substep count are chosen so that the
@@ -438,9 +455,9 @@ def step_taylor(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, taylor_order=None,
     x = _zero_axis_slots(F)
     src = None
     if J is not None:
-        src = dt * taylor_exp(_J_state(J), rad, order, dz, dt / 2, taylor_order, max(1, substeps // 2))
+        src = dt * taylor_exp(_J_state(J), rad, order, dz, dt / 2, taylor_order, max(1, substeps // 2), truncated)
     for _ in range(nsteps):
-        x = taylor_exp(x, rad, order, dz, dt, taylor_order, substeps)
+        x = taylor_exp(x, rad, order, dz, dt, taylor_order, substeps, truncated)
         if src is not None:
             x = x - src
     return fill_axis(x, rad)

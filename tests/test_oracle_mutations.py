@@ -18,6 +18,7 @@ from tests import test_oracle_current as PC
 from tests import test_oracle_destagger as PD
 from tests import test_oracle_envelope as PE
 from tests import test_oracle_pins as P
+from tests import test_oracle_truncated_z as PT
 
 
 def _c2_sign_flipped(mp):
@@ -179,9 +180,9 @@ def _realspace_faraday_sign(mp):
     # dB_theta/dt = +D_z^- E_rho + D^- E_z instead of -D_z^- E_rho + D^- E_z in the real-space operator
     orig = mx.apply_H
 
-    def bad(F, rad, order, dz):
-        out = orig(F, rad, order, dz)
-        out[4, :, 1:] += 2 * mx.dz_minus(F[0], order, dz)[:, 1:]
+    def bad(F, rad, order, dz, truncated=False):
+        out = orig(F, rad, order, dz, truncated)
+        out[4, :, 1:] += 2 * mx.dz_minus(F[0], order, dz, truncated=truncated)[:, 1:]
         return out
     mp.setattr(mx, "apply_H", bad)
 
@@ -195,6 +196,20 @@ def _absorbing_damping_once(mp):
             a, at = ev.envelope_step(a, at, chi + sigma ** 2, order, taylor_order, dz, dr, dt, 1, k0, m)
         return a, at
     mp.setattr(ev, "envelope_step_absorbing", bad)
+
+
+def _truncation_at_one_end(mp):
+    # the truncated z stencils drop the taps below the first point but wrap those past the last one
+    def bad(f, s, axis, truncated):
+        g = np.roll(f, -s, axis=axis)
+        if truncated and s < 0:
+            Nz = f.shape[axis]
+            idx = np.arange(Nz) + s
+            shape = [1] * f.ndim
+            shape[axis] = Nz
+            g = np.where((idx < 0).reshape(shape), 0, g)
+        return g
+    mp.setattr(mx, "_shift", bad)
 
 
 CASES = [
@@ -221,6 +236,8 @@ CASES = [
     ("Faraday sign in the real-space operator", _realspace_faraday_sign, lambda: P.test_three_evaluators_agree(0)),
     ("absorbing-layer damping on one side only", _absorbing_damping_once,
      lambda: PE.test_absorbing_step_with_a_uniform_layer_factorises()),
+    ("truncated z stencil wraps at one end", _truncation_at_one_end,
+     lambda: PT.test_truncated_z_differences_are_negative_transposes(4)),
 ]
 
 
