@@ -281,8 +281,22 @@ def _propagators(H, dt, method):
     return Eh @ Eh, Eh
 
 
-def step_spectral(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, method="eig", kz_subset=None):
+def _exact_current_source(H, j, dt):
+    """phi_1(dt H) dt j = int_0^dt exp(s H) j ds, from the exponential of the augmented matrix [[H, j], [0, 0]]
+    (its upper-right block is that integral)."""
+    n = H.shape[0]
+    A = np.zeros((n + 1, n + 1), complex)
+    A[:n, :n] = H
+    A[:n, n] = j
+    return scipy.linalg.expm(A * dt)[:n, n]
+
+
+def step_spectral(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, method="eig", kz_subset=None, current="midpoint"):
     """Evaluator (i): advance one mode by nsteps midpoint exponential steps (Eq. maxwellAM_solution2).
+
+    current="exact" replaces the midpoint current term -dt exp(dt H / 2) J by the exact integral of a current
+    held constant over the step, -int_0^dt exp(s H) J ds = -phi_1(dt H) dt J (the alternative reading of the
+    current term; the hot path computes the midpoint form).
 
     F: [6][Nz][Nr] complex128, J: [3][Nz][Nr] or None.  The z-DFT diagonalises the
     periodic z stencils; each kz column is advanced with the dense exponential of
@@ -307,7 +321,12 @@ def step_spectral(F, J, Nz, Nr, m, order, dz, dr, dt, nsteps=1, method="eig", kz
         H = kz_operator(rad, sp[q], sm[q])
         E1, Eh = _propagators(H, dt, method)
         x = gather(Fh[:, q, :])
-        src = dt * (Eh @ gather_J(Jh[:, q, :], Nr)) if Jh is not None else 0.0
+        if Jh is None:
+            src = 0.0
+        elif current == "exact":
+            src = _exact_current_source(H, gather_J(Jh[:, q, :], Nr), dt)
+        else:
+            src = dt * (Eh @ gather_J(Jh[:, q, :], Nr))
         done = 0
         for i, n in enumerate(counts):
             for _ in range(n - done):

@@ -8,6 +8,7 @@ from fractions import Fraction
 
 import numpy as np
 import pytest
+import scipy.linalg
 
 from oracle import current as cur
 from oracle import destagger as ds
@@ -212,6 +213,13 @@ def _truncation_at_one_end(mp):
     mp.setattr(mx, "_shift", bad)
 
 
+def _exact_current_left_endpoint(mp):
+    # the constant-current integral replaced by dt exp(dt H) J (the current taken at the start of the step)
+    def bad(H, j, dt):
+        return dt * (scipy.linalg.expm(H * dt) @ j)
+    mp.setattr(mx, "_exact_current_source", bad)
+
+
 CASES = [
     ("staggered c_2 sign", _c2_sign_flipped, lambda: P.test_staggered_textbook_values()),
     ("D- mirror sign ignored", _dminus_parity_ignored, lambda: P.test_radial_derivative_convergence_near_axis(1, 4)),
@@ -238,6 +246,8 @@ CASES = [
      lambda: PE.test_absorbing_step_with_a_uniform_layer_factorises()),
     ("truncated z stencil wraps at one end", _truncation_at_one_end,
      lambda: PT.test_truncated_z_differences_are_negative_transposes(4)),
+    ("constant-current integral taken at the left end", _exact_current_left_endpoint,
+     lambda: P.test_exact_current_variant_integrates_the_ode(1)),
 ]
 
 
