@@ -139,3 +139,39 @@ def test_absorbing_layer_absorbs_an_outgoing_pulse():
     absorbed = np.linalg.norm(x[0]) / np.linalg.norm(a)
     # >= 50x in amplitude, >= 2500x in energy (a stronger layer reflects more of the pulse)
     assert kept > 0.5 and absorbed < 0.02 * kept, (kept, absorbed)
+
+
+def _centroid_delay(w0, chi0, dz=1 / 16, Nz=320, T=4.0):
+    # 1 - v_g of a forward Gaussian envelope (a~ = -D_z a) in a uniform plasma chi0, from its |a|^2 centroid
+    dr, Nr, order, NT = 0.25, 56, 8, 4
+    dt = dz / 4
+    z = np.arange(Nz) * dz
+    rho = (np.arange(Nr) + 0.5) * dr
+    zc = Nz * dz / 2 - T / 2 - 1
+    a = np.exp(-(z[:, None] - zc) ** 2 / 4.0) * np.exp(-rho[None, :] ** 2 / w0 ** 2) + 0j
+    at = -ev.d1_z(a, order, dz)
+
+    def centroid(x):
+        w = np.abs(x) ** 2 * rho[None, :]
+        return (w.sum(axis=1) @ z) / w.sum()
+    n = int(round(T / dt))
+    a1, _ = ev.envelope_step(a, at, np.full((Nz, Nr), chi0), order, NT, dz, dr, dt, nsteps=n)
+    return 1 - (centroid(a1) - centroid(a)) / (n * dt)
+
+
+def test_envelope_group_velocity_in_a_uniform_plasma():
+    # 1 - v_g = n0 / (2 n_c) + (lambda / 2 pi w0)^2 (Sec. 5.2, Eq. test_am_plasma_vg; the paper notes the formula is
+    # analytical but not exact): chi0 = k0^2 n0 / n_c, so n0 / (2 n_c) = chi0 / (2 k0^2); centroid as in
+    # Eq. test_am_vacuum_Z, of |a|^2 weighted by rho
+    k0 = ev.K0
+    runs = {(3.0, 0.01): None, (3.0, 0.02): None, (4.0, 0.01): None}
+    for w0, dens in runs:
+        runs[(w0, dens)] = _centroid_delay(w0, k0 ** 2 * dens)
+    for (w0, dens), d in runs.items():
+        pred = dens / 2 + 1 / (k0 * w0) ** 2
+        assert abs(d / pred - 1) < 0.03, (w0, dens, d, pred)
+    # the density and waist dependences separately
+    dd = runs[(3.0, 0.02)] - runs[(3.0, 0.01)]
+    assert abs(dd / 0.005 - 1) < 0.02, dd
+    dw = runs[(3.0, 0.01)] - runs[(4.0, 0.01)]
+    assert abs(dw / (1 / (k0 * 3.0) ** 2 - 1 / (k0 * 4.0) ** 2) - 1) < 0.02, dw

@@ -220,6 +220,15 @@ def _exact_current_left_endpoint(mp):
     mp.setattr(mx, "_exact_current_source", bad)
 
 
+def _envelope_chi_sign(mp):
+    # the susceptibility entering with the wrong sign, (L - chi) a -> (L + chi) a
+    orig = ev.apply_Ha
+
+    def bad(a, at, chi, Lr, order, dz, k0=ev.K0):
+        return orig(a, at, -chi, Lr, order, dz, k0)
+    mp.setattr(ev, "apply_Ha", bad)
+
+
 CASES = [
     ("staggered c_2 sign", _c2_sign_flipped, lambda: P.test_staggered_textbook_values()),
     ("D- mirror sign ignored", _dminus_parity_ignored, lambda: P.test_radial_derivative_convergence_near_axis(1, 4)),
@@ -248,6 +257,7 @@ CASES = [
      lambda: PT.test_truncated_z_differences_are_negative_transposes(4)),
     ("constant-current integral taken at the left end", _exact_current_left_endpoint,
      lambda: P.test_exact_current_variant_integrates_the_ode(1)),
+    ("envelope susceptibility sign", _envelope_chi_sign, lambda: PE.test_envelope_group_velocity_in_a_uniform_plasma()),
 ]
 
 
