@@ -142,7 +142,8 @@ class Radial:
 # --------------------------------------------------------------------------
 
 def _shift(f, s, axis, truncated):
-    """g_i = f_{i+s}: periodic (wrapped), or truncated (zero where i + s falls outside 0 .. Nz-1)."""
+    """g_i = f_{i+s}: periodic (wrapped), or truncated (zero where i + s falls outside 0 .. Nz-1: the taps beyond
+    the ends that Sec. 2.2 drops)."""
     g = np.roll(f, -s, axis=axis)
     if truncated and s != 0:
         Nz = f.shape[axis]
@@ -282,8 +283,9 @@ def _propagators(H, dt, method):
 
 
 def _exact_current_source(H, j, dt):
-    """phi_1(dt H) dt j = int_0^dt exp(s H) j ds, from the exponential of the augmented matrix [[H, j], [0, 0]]
-    (its upper-right block is that integral)."""
+    """phi_1(dt H) dt j = int_0^dt exp(s H) j ds: the source integral of Eq. maxwellAM_solution for a current held
+    constant over the step, from the exponential of the augmented matrix [[H, j], [0, 0]] (its upper-right block is
+    that integral; Van Loan's block form)."""
     n = H.shape[0]
     A = np.zeros((n + 1, n + 1), complex)
     A[:n, :n] = H
