@@ -282,3 +282,11 @@ def test_host_step_split_is_contiguous_ordered_and_balanced():
     assert native.fdetd_host_split_parts([], 4) == ([], 0)
     with pytest.raises(native.FdetdError):
         native.fdetd_host_split_parts([1, 2], 0)
+
+
+def test_python_flag_and_precision_constants_match_the_header():
+    hdr = open(os.path.join(ROOT, "include", "fdetd.h")).read()
+    flags = dict((k, int(v)) for k, v in re.findall(r"#define (FDETD_FLAG_\w+) (\d+)ull", hdr))
+    assert flags == {"FDETD_FLAG_SPECTRAL_COLUMNS": native.SPECTRAL_COLUMNS, "FDETD_FLAG_J_ON_PRIMARY": native.J_ON_PRIMARY}
+    prec = dict((k.lower(), int(v)) for k, v in re.findall(r"FDETD_PREC_(\w+) = (\d+)", hdr))
+    assert prec == native.PRECISIONS
