@@ -458,6 +458,13 @@ int fdetd_plan_cache_set_limit(size_t bytes);
 int fdetd_plan_cache_warm(int Nr, int order, double dr, const int* modes, int nmodes);
 int fdetd_plan_cache_stats(size_t* bytes, size_t* limit, int* entries, uint64_t* hits, uint64_t* misses);
 
+/* Host only: builds the host tables of a multi-mode plan (the modes' radial eigenbases in parallel, as a plan
+ * does) and writes per mode the left-to-right sums of PE, PB, QE, QB, lambda and mu to digest[6 i .. 6 i + 5],
+ * for checking the parallel build against single-mode fdetd_host_tables.  FDETD_ERR_ARG / FDETD_ERR_EIG as
+ * fdetd_plan. */
+int fdetd_host_plan_digest(int Nz, int Nr, const int* modes, int nmodes, int order, double dz, double dr, double dt,
+                           double* digest);
+
 /* Host-only: staggered (kind 0), centred first (1), centred second (2, e0 first) derivative
  * coefficients of `order`, or axis coefficients (3, N = order/2); returns the count written. */
 int fdetd_host_coeffs(int kind, int order, double* out);

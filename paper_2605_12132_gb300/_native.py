@@ -91,6 +91,7 @@ def lib():
     L.fdetd_batch_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fdetd_batch_set_host_pipeline.argtypes = [c_vp, c_int]
     L.fdetd_host_split_parts.argtypes = [ctypes.POINTER(ctypes.c_size_t), c_int, c_int, ctypes.POINTER(c_int)]
+    L.fdetd_host_plan_digest.argtypes = [c_int, c_int, ctypes.POINTER(c_int), c_int, c_int, c_dbl, c_dbl, c_dbl, dp]
     L.fdetd_plan_pipeline_waits.argtypes = [c_vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fdetd_batch_step_host.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]
     L.fdetd_batch_destroy.argtypes = [c_vp]
@@ -434,6 +435,14 @@ def fdetd_plan_cache_stats():
     _check(lib().fdetd_plan_cache_stats(ctypes.byref(b), ctypes.byref(lim), ctypes.byref(n), ctypes.byref(h),
                                         ctypes.byref(m)))
     return {"bytes": b.value, "limit": lim.value, "entries": n.value, "hits": h.value, "misses": m.value}
+
+
+def fdetd_host_plan_digest(Nz, Nr, modes, order, dz, dr, dt):
+    """Host only: per-mode left-to-right sums (PE, PB, QE, QB, lambda, mu) of a multi-mode plan's host tables."""
+    m = (ctypes.c_int * len(modes))(*modes)
+    out = np.zeros(6 * len(modes))
+    _check(lib().fdetd_host_plan_digest(Nz, Nr, m, len(modes), order, dz, dr, dt, _dptr(out)))
+    return out.reshape(len(modes), 6)
 
 
 def fdetd_host_split_parts(sizes, parts):

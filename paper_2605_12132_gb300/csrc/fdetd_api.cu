@@ -824,6 +824,31 @@ extern "C" int fdetd_plan_cache_stats(size_t* bytes, size_t* limit, int* entries
   return FDETD_OK;
 }
 
+extern "C" int fdetd_host_plan_digest(int Nz, int Nr, const int* modes, int nmodes, int order, double dz, double dr,
+                                      double dt, double* digest) {
+  if (!modes || nmodes < 1 || !digest) return fail(FDETD_ERR_ARG, "null modes or digest");
+  HostPlan hp;
+  std::string msg;
+  const int rc = build_host_plan(hp, Nz, Nr, modes, nmodes, order, dz, dr, dt, msg);
+  if (rc) return fail(rc == 4 ? FDETD_ERR_EIG : FDETD_ERR_ARG, msg);
+  auto sum = [](const std::vector<double>& v) {
+    double a = 0.0;
+    for (double x : v) a += x;  // left to right
+    return a;
+  };
+  for (int i = 0; i < nmodes; ++i) {
+    const ModePlan& mp = hp.mp[i];
+    double* d = digest + 6 * i;
+    d[0] = sum(mp.PE);
+    d[1] = sum(mp.PB);
+    d[2] = sum(mp.QE);
+    d[3] = sum(mp.QB);
+    d[4] = sum(mp.lam);
+    d[5] = sum(mp.mu);
+  }
+  return FDETD_OK;
+}
+
 extern "C" int fdetd_host_coeffs(int kind, int order, double* out) {
   if (order < 2 || order > 32 || (order & 1) || !out) return fail(FDETD_ERR_ARG, "bad order or null out");
   std::vector<double> v;

@@ -5,9 +5,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <future>
 #include <list>
 #include <memory>
 #include <mutex>
+#include <thread>
 
 #include "eig.h"
 
@@ -263,6 +265,16 @@ void phase_coeffs(double w, double t, double* A1, double* A2) {
   }
 }
 
+// f on another thread (std::async), or deferred to get() where no thread can be started
+template <typename F>
+static auto run_async(F f) -> std::future<decltype(f())> {
+  try {
+    return std::async(std::launch::async, f);
+  } catch (...) {
+    return std::async(std::launch::deferred, f);
+  }
+}
+
 static int build_mode(ModePlan& P, int n, int order, double dr, int m, std::string& msg) {
   P.m = m;
   P.n = n;
@@ -300,12 +312,20 @@ static int build_mode(ModePlan& P, int n, int order, double dr, int m, std::stri
   std::vector<double> w0, w2;
   Mat U, Psi, Ui, Psii;
   double im0 = 0, im2 = 0;
-  if (eig_real(L0, w0, U, 1e-8, &im0) != 0 || eig_real(L2, w2, Psi, 1e-8, &im2) != 0) {
+  // the TM (L0) and TE (L2) eigenbases are independent: the TE one is computed on a second thread
+  // (1 = eigen-decomposition failed, 2 = singular basis)
+  auto te = run_async([&]() -> int {
+    if (eig_real(L2, w2, Psi, 1e-8, &im2) != 0) return 1;
+    return invert(Psi, Psii) != 0 ? 2 : 0;
+  });
+  const int rc0 = eig_real(L0, w0, U, 1e-8, &im0) != 0 ? 1 : (invert(U, Ui) != 0 ? 2 : 0);
+  const int rc2 = te.get();
+  if (rc0 == 1 || rc2 == 1) {
     msg = "radial eigen-decomposition failed (complex or non-convergent spectrum) for mode " + std::to_string(m);
     return 4;
   }
   P.max_imag = std::max(im0, im2);
-  if (invert(U, Ui) != 0 || invert(Psi, Psii) != 0) {
+  if (rc0 == 2 || rc2 == 2) {
     msg = "singular radial eigenbasis for mode " + std::to_string(m);
     return 4;
   }
@@ -347,8 +367,12 @@ static int build_mode(ModePlan& P, int n, int order, double dr, int m, std::stri
                             dd_div_d(dd_div_d(two_prod(-m2, x[k - 1]), rhom[k]), rhom[k]));
       }
     };
+    auto te_refine = run_async([&]() -> int {
+      refine_eigs(w2, Psi, Psii, apply_L2);
+      return 0;
+    });
     refine_eigs(w0, U, Ui, apply_L0);
-    refine_eigs(w2, Psi, Psii, apply_L2);
+    te_refine.get();
   }
   P.lam.assign(n, 0.0);
   P.mu.assign(n, 0.0);
@@ -726,13 +750,30 @@ int build_host_plan(HostPlan& hp, int Nz, int Nr, const int* modes, int nmodes, 
   hp.dt = dt;
   hp.modes.assign(modes, modes + nmodes);
   hp.mp.resize(nmodes);
-  for (int i = 0; i < nmodes; ++i) {
+  for (int i = 0; i < nmodes; ++i)
     if (modes[i] < 0 || modes[i] > 64) {
       msg = "mode numbers must be 0..64";
       return 1;
     }
-    int rc = cached_mode(hp.mp[i], Nr, order, dr, modes[i], msg);
-    if (rc) return rc;
+  // modes are independent: W workers take modes w, w + W, ...; the first failing mode (in mode order) reports
+  {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int W = std::max(1, std::min(nmodes, (int)std::max(1u, hw / 2)));
+    std::vector<int> rcs(nmodes, 0);
+    std::vector<std::string> msgs(nmodes);
+    auto work = [&](int w) -> int {
+      for (int i = w; i < nmodes; i += W) rcs[i] = cached_mode(hp.mp[i], Nr, order, dr, modes[i], msgs[i]);
+      return 0;
+    };
+    std::vector<std::future<int>> fs;
+    for (int w = 1; w < W; ++w) fs.push_back(run_async([&work, w]() { return work(w); }));
+    work(0);
+    for (auto& f : fs) f.get();
+    for (int i = 0; i < nmodes; ++i)
+      if (rcs[i]) {
+        msg = msgs[i];
+        return rcs[i];
+      }
   }
   // z symbols of the periodic staggered stencil: s+ = i kappa e^{+i th/2}, s- = i kappa e^{-i th/2},
   // kappa = (2/dz) sum_n c_n sin((2n-1) th / 2), th = 2 pi q / Nz.

@@ -290,3 +290,29 @@ def test_python_flag_and_precision_constants_match_the_header():
     assert flags == {"FDETD_FLAG_SPECTRAL_COLUMNS": native.SPECTRAL_COLUMNS, "FDETD_FLAG_J_ON_PRIMARY": native.J_ON_PRIMARY}
     prec = dict((k.lower(), int(v)) for k, v in re.findall(r"FDETD_PREC_(\w+) = (\d+)", hdr))
     assert prec == native.PRECISIONS
+
+
+def test_parallel_multi_mode_build_equals_single_mode_builds():
+    # a plan builds its modes' radial eigenbases on parallel threads (and each mode's TM and TE bases on two):
+    # every mode's tables must be bitwise those of a single-mode build, with the radial-table cache off (every
+    # table built in the threads) and on
+    _lib_or_skip()
+    Nz, Nr, order, dz, dr, dt = 32, 40, 8, 1 / 16, 1 / 4, 1 / 16
+    modes = [0, 1, 2, 3, 5]
+
+    def seq_sum(x):
+        return float(np.cumsum(np.asarray(x, dtype=np.float64).ravel())[-1])
+    native.fdetd_plan_cache_set_limit(0)
+    ref = []
+    for m in modes:
+        T = native.fdetd_host_tables(Nz, Nr, m, order, dz, dr, dt)
+        ref.append([seq_sum(T[k]) for k in ("PE", "PB", "QE", "QB", "lam", "mu")])
+    ref = np.array(ref)
+    for limit in (0, 1 << 30):
+        native.fdetd_plan_cache_set_limit(limit)
+        for _ in range(2):
+            got = native.fdetd_host_plan_digest(Nz, Nr, modes, order, dz, dr, dt)
+            assert np.array_equal(got, ref), (limit, np.abs(got - ref).max())
+    native.fdetd_plan_cache_set_limit(4 << 30)
+    with pytest.raises(native.FdetdError):
+        native.fdetd_host_plan_digest(Nz, Nr, [0, 70], order, dz, dr, dt)
